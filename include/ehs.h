@@ -1,0 +1,168 @@
+/*
+ * ehs.h - C ABI of the GB300 elastic Helmholtz shifted-Laplacian solver.
+ *
+ * The library solves the mixed (displacement / pressure) staggered-grid
+ * discretisation of the elastic Helmholtz equation,
+ *
+ *     K [u; p] = [q; 0],   K = [[L_mu - w^2 M,  G           ],
+ *                               [G^T,          -D(1/(l+mu))]]
+ *
+ * (Treister & Yovel, Sec. 2.1 eq. elasticHelmSystem and eq.
+ * elasticHelmMass, Sec. 3 eq. pressure and eq.
+ * elasticHelmReformulatedSystem), with a flexible GMRES preconditioned by a
+ * multigrid cycle of the shifted operator K_s = K + i alpha w^2 diag(A_f(rho), 0)
+ * (Sec. 2.2 eq. shift; Sec. 3 zero-padded shift), red-black cell-wise
+ * (Vanka) relaxation (Sec. 3), Galerkin coarse operators (Sec. 2.2 eq.
+ * coarseGridMatrix) and an exact FP64 coarsest solve; optionally wrapped in
+ * the multicolour overlapping domain decomposition of Sec. 2.3 Algorithm DD
+ * (DD-MG of Sec. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: n[0] x n[1] x n[2] cells (x fastest; n[2] = 1 in 2D), spacing h.
+ * Media: cell-centred lambda, mu, rho, double, [nmedia][n_z][n_y][n_x].
+ * Vector ("slot layout"): per item, d+1 component arrays of ncell complex
+ *   numbers (interleaved re, im): u_1 .. u_d, p.  u_k[c] lives on the low
+ *   face of cell c in direction k; slots with index 0 along k are Dirichlet
+ *   boundary faces and must be zero on input (they are zero on output).
+ *   A batch of items is stacked on the slowest axis; item b uses medium
+ *   b / nrhs.  Double-precision vectors hold complex128, single-precision
+ *   vectors complex64.
+ * Pointers: vector arguments of ehs_op_apply, ehs_smooth, ehs_vcycle and
+ *   ehs_dd_precond are device pointers; ehs_fgmres_solve and
+ *   ehs_adjoint_solve accept host or device pointers (host buffers are
+ *   copied in and out by the call).  The caller owns every buffer it passes;
+ *   the context owns its hierarchy and workspaces.
+ * Streams: every call is ordered on the stream given to ehs_create; only the
+ *   solves synchronise it (they read residual norms on the host).
+ * Errors: no call throws; a failed call returns a non-zero ehs_status,
+ *   ehs_last_error() describes it, outputs are unspecified except for
+ *   EHS_ERR_NOCONV / EHS_ERR_BREAKDOWN, which return the best iterate.
+ *   Arguments are validated before any launch.
+ */
+#ifndef EHS_H
+#define EHS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EHS_OK = 0,
+  EHS_ERR_ARG = 1,        /* invalid argument (sizes, divisibility, media) */
+  EHS_ERR_CUDA = 2,       /* a CUDA call failed */
+  EHS_ERR_OOM = 3,        /* device allocation failed */
+  EHS_ERR_NOCONV = 4,     /* maxit reached before tol */
+  EHS_ERR_BREAKDOWN = 5,  /* Arnoldi breakdown before tol */
+  EHS_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+  EHS_ERR_NONFINITE = 7,  /* NaN / Inf in a residual norm or a pivot */
+  EHS_ERR_UNSUPPORTED = 8 /* option combination not built */
+} ehs_status;
+
+typedef enum { EHS_C128 = 0, EHS_C64 = 1 } ehs_prec;
+typedef enum { EHS_PRECOND_MG = 0, EHS_PRECOND_DD = 1 } ehs_precond;
+
+typedef struct ehs_ctx ehs_ctx; /* opaque, owned by the library */
+
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int n[3];              /* cells along x, y, z */
+  double h;              /* grid spacing */
+  double omega;          /* angular frequency (all media) */
+  const double* omegas;  /* optional host array [nmedia] of per-medium frequencies; NULL = omega */
+  int nmedia;            /* independent media (coefficient sets), >= 1 */
+  const double* lambda;  /* [nmedia][ncell], host or device, read during ehs_create only */
+  const double* mu;
+  const double* rho;
+  int abl_cells;         /* absorbing layer width on every side (cells) */
+  double abl_max;        /* gamma/omega reached at the outer edge (eq. elasticHelmMass) */
+  double gamma_add;      /* constant attenuation added everywhere (0.01 pi in Sec. 6) */
+} ehs_problem;
+
+typedef struct {
+  int levels;            /* multigrid levels >= 2; every n[k] divisible by 2^(levels-1) */
+  double alpha;          /* shift (Sec. 2.2 eq. shift) */
+  double w[8];           /* Vanka damping of level l (Sec. 6: 0.75, 0.5, 0.25) */
+  double wp_ratio;       /* w_p = w_l * wp_ratio (Sec. 5.4 component damping); 1 = same */
+  int nu_pre, nu_post;   /* relaxation sweeps (one sweep = red + black) */
+  int cycle;             /* 1 = V-cycle, 2 = W-cycle */
+  int restart;           /* FGMRES restart length m (1..11) */
+  int maxit;             /* max preconditioner applications per solve */
+  double tol;            /* relative residual of the mixed system */
+  int precond;           /* ehs_precond */
+  int prec;              /* ehs_prec of the preconditioner (the Krylov solve is FP64) */
+  int nrhs;              /* right-hand sides per medium; items = nmedia * nrhs */
+  int dd[3];             /* subdomains per axis (DD only) */
+  int dd_overlap;        /* overlap in cells (DD only) */
+  int dd_pad;            /* absorbing padding in cells on interface sides (DD only) */
+  double dd_abl_max;     /* gamma/omega at the outer edge of the padding (DD only) */
+} ehs_opts;
+
+typedef struct {
+  int iters;             /* preconditioner applications */
+  double relres;         /* true ||q - K u|| / ||q|| at exit */
+  int converged;         /* 1 if relres <= tol */
+} ehs_solve_info;
+
+/* Fill *o with the defaults of Sec. 6 (3 levels, alpha 0.2, w 0.75/0.5/0.25,
+ * V(1,1), FGMRES(10), tol 1e-6, MG preconditioner in complex64). */
+void ehs_default_opts(ehs_opts* o);
+
+/* Build the hierarchy (coefficients, Galerkin operators, coarsest inverse,
+ * and the DD subdomain hierarchies when opts->precond is DD) for every
+ * medium.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Returns EHS_ERR_ARG for invalid sizes or media (rho <= 0, mu < 0,
+ * lambda + mu <= 0, non-finite omega, n not divisible). */
+ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* stream, ehs_ctx** out);
+ehs_status ehs_destroy(ehs_ctx* ctx);
+
+/* y = K_l x for all items.  level 0: the fine operator, unshifted
+ * (shifted = 0, the Krylov operator K) or shifted (K_s); level l >= 1: the
+ * Galerkin operator P^T K_{l-1} P (always shifted).  prec selects complex128
+ * or complex64 vectors and arithmetic.  Device pointers, slot layout of the
+ * level's grid. */
+ehs_status ehs_op_apply(ehs_ctx* ctx, int level, int shifted, int prec, const void* x, void* y);
+
+/* nsweeps red-black cell-wise relaxation sweeps of level l on K_l x = b
+ * (Sec. 3, economic block of eq. RelaxationMatrix, damping w_l); x is
+ * updated in place.  Device pointers. */
+ehs_status ehs_smooth(ehs_ctx* ctx, int level, int nsweeps, int prec, const void* b, void* x);
+
+/* x := one multigrid cycle (Algorithm TwoCycle, recursive) for K_s x = b
+ * from a zero initial guess.  Device pointers, fine-grid slot layout. */
+ehs_status ehs_vcycle(ehs_ctx* ctx, int prec, const void* b, void* x);
+
+/* z := one sweep of Algorithm DD on K z = r (global residual recomputed
+ * before each colour, subdomain corrections by one multigrid cycle of the
+ * shifted subdomain operator).  Requires a context created with
+ * precond = EHS_PRECOND_DD.  Device pointers. */
+ehs_status ehs_dd_precond(ehs_ctx* ctx, int prec, const void* r, void* z);
+
+/* Solve K u = q for every item with right-preconditioned FGMRES(m) from a
+ * zero initial guess (Sec. 6).  q, u: complex128, host or device.
+ * info: host array of nmedia*nrhs entries (may be NULL). */
+ehs_status ehs_fgmres_solve(ehs_ctx* ctx, const void* q, void* u, ehs_solve_info* info);
+
+/* Solve K^H w = g (adjoint state).  K is complex symmetric (K = K^T), so
+ * K^H = conj(K) and w = conj(K^{-1} conj(g)); the same preconditioner is
+ * used.  Same argument conventions as ehs_fgmres_solve. */
+ehs_status ehs_adjoint_solve(ehs_ctx* ctx, const void* g, void* w, ehs_solve_info* info);
+
+/* Sizes: items of a vector batch, complex values per item at level l. */
+int ehs_items(const ehs_ctx* ctx);
+long long ehs_level_len(const ehs_ctx* ctx, int level);
+int ehs_level_dims(const ehs_ctx* ctx, int level, int n[3]);
+
+/* Wait for all work issued on the context's stream. */
+ehs_status ehs_sync(ehs_ctx* ctx);
+
+/* Number of kernels this library has launched since load (diagnostics). */
+long long ehs_kernel_launches(void);
+
+/* Message of the last failed call of ctx (or of ehs_create when ctx is NULL). */
+const char* ehs_last_error(const ehs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EHS_H */

@@ -9,9 +9,10 @@ Sec. 2.3 and Sec. 4 of the paper.  Readings of what the paper leaves open:
   absorbing layer, gamma += omega * dd_abl_max * (depth / pad)^2 (the
   interface absorbing layer of Sec. 2.3); the padded extent is rounded up
   (more padding) to a multiple of 2^(levels-1);
-* 2^d colours by the parity of the subdomain index along each axis; the
-  colours are visited in order and the global residual is recomputed before
-  each colour (Algorithm DD, step 1);
+* 2^d colours by the parity of the subdomain index along each axis,
+  c = sum_k 2^k (i_k mod 2) with k = 0 for x; colours are visited in
+  increasing c and the global residual is recomputed before each colour
+  (Algorithm DD, step 1);
 * the local correction solves the local operator H_i, and in the hybrid
   DD-MG form (Sec. 4) this solve is one multigrid cycle of the shifted local
   operator; the correction is added on the DOFs that lie inside Omega_i (cells
@@ -57,7 +58,8 @@ class Subdomain:
     def __init__(self, shape, sub_index, splits, overlap, pad, align):
         d = len(shape)
         self.index = sub_index                        # per numpy axis
-        self.colour = sum((sub_index[a] % 2) << a for a in range(d))
+        # colour c = sum_k 2^k (index along direction k mod 2), k = 0 for x
+        self.colour = sum((sub_index[a] % 2) << (d - 1 - a) for a in range(d))
         self.om_lo, self.om_hi, self.pad_lo, self.pad_hi = [], [], [], []
         for a in range(d):
             e = splits[a]

@@ -1,0 +1,697 @@
+// Host side of the GB300 elastic Helmholtz library: hierarchy setup, the
+// multigrid cycle, the multicolour DD sweep and the FGMRES driver, behind the
+// C ABI of include/ehs.h.  Every arithmetic step runs in the kernels of this
+// directory; the host only sequences launches and runs the (m+1) x m
+// Hessenberg least-squares update of FGMRES.
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "ehs.h"
+#include "kernels.h"
+
+namespace ehs {
+std::atomic<long long> g_launches{0};
+}
+
+using namespace ehs;
+typedef std::complex<double> zc;
+
+namespace {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct ArgError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw CudaError(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+inline void cnt(long long k = 1) { g_launches += k; }
+inline void post() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
+struct Level {
+  Grid g{};
+  StencilLayout L{};
+  double2* tab64 = nullptr;   // Galerkin levels and coarsest: [nsets][nslot][ncell]
+  float2* tab32 = nullptr;
+  double2* inv = nullptr;     // coarsest: [nsets][N][N]
+  void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
+  double w = 0.5;
+};
+
+struct Hier {
+  Grid g0{};
+  int nlev = 0, nsets = 0, nrhs = 1, items = 0;
+  double h = 1, alpha = 0;
+  double wp_ratio = 1;
+  int nu1 = 1, nu2 = 1, cyc = 1;
+  Coef4<double>* cf64 = nullptr;
+  Coef4<float>* cf32 = nullptr;
+  std::vector<Level> lv;
+};
+
+struct DDGroup {          // subdomains of one colour that share one shape
+  Hier H;
+  int nsub = 0;
+  std::vector<int> subs;  // global subdomain ids
+  int* d_map = nullptr;   // [nsub][ncell_local] -> global cell index or -1 (outside Omega_i)
+  int* d_origin = nullptr;
+};
+
+}  // namespace
+
+struct ehs_ctx {
+  cudaStream_t s = nullptr;
+  ehs_problem prob{};
+  ehs_opts opt{};
+  int d = 2;
+  long long n0 = 0;       // complex values per item at the fine level
+  Hier H;
+  std::vector<DDGroup> dd[8];
+  std::vector<void*> allocs;
+  // Krylov workspace
+  double2 *V = nullptr, *Z = nullptr, *w = nullptr, *part = nullptr, *hd = nullptr, *y = nullptr;
+  double2 *qd = nullptr, *ud = nullptr, *rd = nullptr;
+  double *npart = nullptr, *nrm = nullptr;
+  int* kused = nullptr;
+  float2 *f_in = nullptr, *f_out = nullptr;
+  double2* dd_x = nullptr;   // DD accumulated correction (c128 or c64 view)
+  double2* dd_r = nullptr;
+  int nblk = 1;
+  double* hpin = nullptr;    // pinned host scratch
+  std::string err;
+};
+
+static std::string g_create_err;
+
+namespace {
+
+template <typename P> P* dalloc(ehs_ctx* c, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(P));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw std::bad_alloc();
+  }
+  c->allocs.push_back(p);
+  CK(cudaMemsetAsync(p, 0, count * sizeof(P), c->s));
+  return (P*)p;
+}
+void dfree(ehs_ctx* c, void* p) {
+  if (!p) return;
+  for (auto& q : c->allocs)
+    if (q == p) { cudaFree(p); q = nullptr; return; }
+}
+
+Grid mkgrid(int d, int nx, int ny, int nz) {
+  Grid g;
+  g.d = d; g.n[0] = nx; g.n[1] = ny; g.n[2] = d == 3 ? nz : 1;
+  g.ncell = (long long)g.n[0] * g.n[1] * g.n[2];
+  return g;
+}
+
+// ------------------------------------------------------------ hierarchy
+void build_hier(ehs_ctx* c, Hier& H) {
+  const int d = H.g0.d;
+  H.cf32 = dalloc<Coef4<float>>(c, (size_t)H.nsets * H.g0.ncell);
+  launch_coef_cast<float>((long long)H.nsets * H.g0.ncell, H.cf64, H.cf32, c->s); cnt(); post();
+  H.lv.resize(H.nlev);
+  Grid g = H.g0;
+  for (int l = 0; l < H.nlev; ++l) {
+    Level& L = H.lv[l];
+    L.g = g;
+    L.w = c->opt.w[l < 8 ? l : 7];
+    const long long nv = (long long)H.items * (d + 1) * g.ncell;
+    for (int k = 0; k < 4; ++k) {
+      L.ws[0][k] = dalloc<double2>(c, nv);
+      L.ws[1][k] = dalloc<float2>(c, nv);
+    }
+    if (l + 1 < H.nlev) g = mkgrid(d, g.n[0] / 2, g.n[1] / 2, g.n[2] / 2);
+  }
+  // level-0 table of K_s, then Galerkin products level by level
+  StencilLayout Lf;
+  fine_table_layout(d, &Lf);
+  double2* tf = dalloc<double2>(c, (size_t)H.nsets * Lf.nslot * H.g0.ncell);
+  launch_fine_table(H.g0, H.nsets, H.cf64, H.h, H.alpha, Lf, tf, c->s); cnt(); post();
+  int* derr = dalloc<int>(c, 1);
+  for (int l = 1; l < H.nlev; ++l) {
+    Level& L = H.lv[l];
+    coarse_layout(d, Lf, &L.L);
+    L.tab64 = dalloc<double2>(c, (size_t)H.nsets * L.L.nslot * L.g.ncell);
+    launch_galerkin(H.lv[l - 1].g, L.g, H.nsets, Lf, tf, L.L, L.tab64, derr, c->s); cnt(); post();
+    if (l > 1 || tf != nullptr) {
+      if (l == 1) dfree(c, tf);
+    }
+    const long long nt = (long long)H.nsets * L.L.nslot * L.g.ncell;
+    L.tab32 = dalloc<float2>(c, nt);
+    launch_table_cast<float>(nt, L.tab64, L.tab32, c->s); cnt(); post();
+    Lf = L.L;
+    tf = L.tab64;
+  }
+  // coarsest: dense FP64 inverse
+  Level& C = H.lv[H.nlev - 1];
+  const long long N = (long long)(d + 1) * C.g.ncell;
+  if (N > 16384) throw ArgError("coarsest grid too large for the dense FP64 inverse (use more levels)");
+  double2* M = dalloc<double2>(c, (size_t)H.nsets * N * 2 * N);
+  double2* fb = dalloc<double2>(c, (size_t)H.nsets * (N + 1));
+  int* pv = dalloc<int>(c, H.nsets);
+  launch_dense_assemble(C.g, H.nsets, C.L, C.tab64, M, c->s); cnt(); post();
+  C.inv = dalloc<double2>(c, (size_t)H.nsets * N * N);
+  dense_invert((int)N, H.nsets, M, C.inv, fb, pv, derr, c->s); cnt(4 * N + 1); post();
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  dfree(c, M); dfree(c, fb); dfree(c, pv); dfree(c, derr);
+  if (herr & EHS_DEVERR_BOX) throw CudaError("Galerkin stencil fell outside its box");
+  if (herr & EHS_DEVERR_SINGULAR) throw ArgError("coarsest Galerkin operator is singular");
+}
+
+template <typename T> struct PT;
+template <> struct PT<double> { static const int i = 0; };
+template <> struct PT<float> { static const int i = 1; };
+
+template <typename T> const Coef4<T>* cfp(const Hier& H);
+template <> const Coef4<double>* cfp<double>(const Hier& H) { return H.cf64; }
+template <> const Coef4<float>* cfp<float>(const Hier& H) { return H.cf32; }
+template <typename T> const typename CT<T>::type* tabp(const Level& L);
+template <> const double2* tabp<double>(const Level& L) { return L.tab64; }
+template <> const float2* tabp<float>(const Level& L) { return L.tab32; }
+
+template <typename T>
+void level_apply(ehs_ctx* c, const Hier& H, int l, double alpha, const typename CT<T>::type* x,
+                 const typename CT<T>::type* b, typename CT<T>::type* y, int mode) {
+  const Level& L = H.lv[l];
+  if (l == 0)
+    launch_fine_apply<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, alpha, x, b, y, mode, c->s);
+  else
+    launch_st_apply<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), x, b, y, mode, c->s);
+  cnt(); post();
+}
+
+// one red-black sweep on level l: x -> t -> x
+template <typename T>
+void level_sweep(ehs_ctx* c, const Hier& H, int l, const typename CT<T>::type* b,
+                 typename CT<T>::type* x, typename CT<T>::type* t) {
+  const Level& L = H.lv[l];
+  const T wu = (T)L.w, wp = (T)(L.w * H.wp_ratio);
+  if (l == 0) {
+    launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 0, b, x, t, c->s);
+    launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 1, b, t, x, c->s);
+  } else {
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 0, b, x, t, c->s);
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 1, b, t, x, c->s);
+  }
+  cnt(2); post();
+}
+
+template <typename T>
+void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typename CT<T>::type* x,
+               bool guess) {
+  typedef typename CT<T>::type C;
+  Level& L = H.lv[l];
+  const int p = PT<T>::i;
+  const long long nv = (long long)H.items * (L.g.d + 1) * L.g.ncell;
+  if (l == H.nlev - 1) {
+    launch_dense_apply<T>((int)((L.g.d + 1) * L.g.ncell), H.items, H.nrhs, L.inv, b, x, c->s);
+    cnt(); post();
+    return;
+  }
+  C* t = (C*)L.ws[p][2];
+  C* r = (C*)L.ws[p][3];
+  if (!guess) CK(cudaMemsetAsync(x, 0, nv * sizeof(C), c->s));
+  for (int s = 0; s < H.nu1; ++s) level_sweep<T>(c, H, l, b, x, t);
+  level_apply<T>(c, H, l, H.alpha, x, b, r, 1);
+  Level& Lc = H.lv[l + 1];
+  C* bc = (C*)Lc.ws[p][0];
+  C* xc = (C*)Lc.ws[p][1];
+  launch_restrict<T>(L.g, Lc.g, H.items, r, bc, c->s); cnt(); post();
+  const int reps = (l + 1 == H.nlev - 1) ? 1 : H.cyc;
+  for (int k = 0; k < reps; ++k) cycle_rec<T>(c, H, l + 1, bc, xc, k > 0);
+  launch_prolong_add<T>(L.g, Lc.g, H.items, xc, x, c->s); cnt(); post();
+  for (int s = 0; s < H.nu2; ++s) level_sweep<T>(c, H, l, b, x, t);
+}
+
+// ------------------------------------------------------------------ checks
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void validate(const ehs_problem* P, const ehs_opts* O) {
+  if (!P || !O) throw ArgError("null problem or options");
+  if (P->dim != 2 && P->dim != 3) throw ArgError("dim must be 2 or 3");
+  if (O->levels < 2 || O->levels > 8) throw ArgError("levels must be in [2, 8]");
+  const int f = 1 << (O->levels - 1);
+  for (int k = 0; k < P->dim; ++k)
+    if (P->n[k] < 2 * f || P->n[k] % f) throw ArgError("every n[k] must be a multiple of 2^(levels-1), at least twice it");
+  if (!(P->h > 0) || (!P->omegas && (!std::isfinite(P->omega) || !(P->omega > 0))))
+    throw ArgError("h and omega must be positive and finite");
+  if (P->nmedia < 1 || O->nrhs < 1) throw ArgError("nmedia and nrhs must be >= 1");
+  if (!P->lambda || !P->mu || !P->rho) throw ArgError("null media pointer");
+  if (O->restart < 1 || O->restart > 11) throw ArgError("restart must be in [1, 11]");
+  if (O->prec != EHS_C64 && O->prec != EHS_C128) throw ArgError("prec must be EHS_C64 or EHS_C128");
+  if (O->cycle != 1 && O->cycle != 2) throw ArgError("cycle must be 1 (V) or 2 (W)");
+  if (O->nu_pre < 0 || O->nu_post < 0) throw ArgError("negative sweep count");
+  if (!(O->tol > 0)) throw ArgError("tol must be positive");
+  if (P->abl_cells < 0 || 2 * P->abl_cells > P->n[0]) throw ArgError("bad abl_cells");
+  if (O->precond != EHS_PRECOND_MG && O->precond != EHS_PRECOND_DD) throw ArgError("bad precond");
+}
+
+void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* rho, long long n) {
+  std::vector<double> L(n), M(n), R(n);
+  CK(cudaMemcpy(L.data(), lam, n * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(M.data(), mu, n * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(R.data(), rho, n * sizeof(double), cudaMemcpyDefault));
+  for (long long i = 0; i < n; ++i) {
+    if (!std::isfinite(L[i]) || !std::isfinite(M[i]) || !std::isfinite(R[i])) throw ArgError("non-finite medium value");
+    if (!(R[i] > 0)) throw ArgError("rho must be positive");
+    if (M[i] < 0) throw ArgError("mu must be non-negative");
+    if (!(L[i] + M[i] > 0)) throw ArgError("lambda + mu must be positive");
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- DD
+#include "dd_impl.inc"
+
+// ------------------------------------------------------------------ FGMRES
+namespace {
+
+void precond_apply(ehs_ctx* c, const double2* v, double2* z);
+
+void givens(zc a, zc b, double* cs, zc* sn, zc* r) {
+  if (b == 0.0) { *cs = 1; *sn = 0; *r = a; return; }
+  if (a == 0.0) { *cs = 0; *sn = std::conj(b) / std::abs(b); *r = std::abs(b); return; }
+  const double t = std::abs(a), nr = std::hypot(t, std::abs(b));
+  *cs = t / nr;
+  *sn = (a / t) * std::conj(b) / nr;
+  *r = (a / t) * nr;
+}
+
+ehs_status fgmres(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info) {
+  const int items = c->H.items, m = c->opt.restart;
+  const long long n = c->n0;
+  const int nblk = c->nblk;
+  cudaStream_t s = c->s;
+  // ||q||
+  launch_norm_part(n, items, q, c->npart, nblk, s);
+  launch_reduce_norm(items, nblk, c->npart, c->nrm, s); cnt(2); post();
+  std::vector<double> bnorm(items), beta(items);
+  CK(cudaMemcpyAsync(c->hpin, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int b = 0; b < items; ++b) bnorm[b] = beta[b] = c->hpin[b];
+  CK(cudaMemsetAsync(u, 0, (size_t)items * n * sizeof(double2), s));
+  CK(cudaMemcpyAsync(c->rd, q, (size_t)items * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  std::vector<int> iters(items, 0), done(items, 0);
+  for (int b = 0; b < items; ++b) done[b] = !(bnorm[b] > 0) || (beta[b] / bnorm[b] <= c->opt.tol);
+  std::vector<zc> H((size_t)items * (m + 1) * m), g((size_t)items * (m + 1)), sn((size_t)items * m);
+  std::vector<double> cs((size_t)items * m);
+  std::vector<int> kused(items), active(items);
+  std::vector<double2> yh((size_t)items * m);
+  std::vector<double2> hh((size_t)items * (m + 1));
+  bool breakdown = false, nonfinite = false;
+  auto all_done = [&]() { for (int b = 0; b < items; ++b) if (!done[b]) return false; return true; };
+  while (!all_done()) {
+    bool maxed = true;
+    for (int b = 0; b < items; ++b) if (!done[b] && iters[b] < c->opt.maxit) maxed = false;
+    if (maxed) break;
+    // V_0 = r / beta
+    CK(cudaMemcpyAsync(c->nrm, beta.data(), items * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_inv(n, items, c->rd, c->nrm, c->V, s); cnt(); post();
+    std::fill(H.begin(), H.end(), zc(0));
+    std::fill(g.begin(), g.end(), zc(0));
+    for (int b = 0; b < items; ++b) {
+      g[(size_t)b * (m + 1)] = beta[b];
+      kused[b] = 0;
+      active[b] = !done[b] && iters[b] < c->opt.maxit;
+    }
+    for (int j = 0; j < m; ++j) {
+      double2* Vj = c->V + (size_t)j * items * n;
+      double2* Zj = c->Z + (size_t)j * items * n;
+      precond_apply(c, Vj, Zj);
+      launch_fine_apply<double>(c->H.g0, items, c->H.nrhs, c->H.cf64, c->H.h, 0.0, Zj,
+                                nullptr, c->w, 0, s);
+      cnt(); post();
+      const int nv = j + 1;
+      launch_mdot(n, items, nv, c->V, c->w, c->part, nblk, s);
+      launch_reduce_parts(items, nv, nblk, c->part, c->hd, 0, s);
+      launch_mupdate(n, items, nv, c->V, c->hd, c->w, c->part, nblk, 1, nullptr, s);
+      launch_reduce_parts(items, nv, nblk, c->part, c->y, 0, s);   // h2 into y scratch
+      launch_mupdate(n, items, nv, c->V, c->y, c->w, nullptr, nblk, 0, c->npart, s);
+      launch_reduce_norm(items, nblk, c->npart, c->nrm, s);
+      cnt(6); post();
+      CK(cudaMemcpyAsync(hh.data(), c->hd, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(yh.data(), c->y, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(c->hpin, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool any_active = false;
+      for (int b = 0; b < items; ++b) {
+        if (!active[b]) continue;
+        zc* Hb = &H[(size_t)b * (m + 1) * m];
+        zc* gb = &g[(size_t)b * (m + 1)];
+        for (int i = 0; i < nv; ++i)
+          Hb[i * m + j] = zc(hh[b * nv + i].x + yh[b * nv + i].x, hh[b * nv + i].y + yh[b * nv + i].y);
+        const double hn = c->hpin[b];
+        Hb[(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const zc t = cs[b * m + i] * Hb[i * m + j] + sn[b * m + i] * Hb[(i + 1) * m + j];
+          Hb[(i + 1) * m + j] = -std::conj(sn[b * m + i]) * Hb[i * m + j] + cs[b * m + i] * Hb[(i + 1) * m + j];
+          Hb[i * m + j] = t;
+        }
+        zc rr;
+        givens(Hb[j * m + j], Hb[(j + 1) * m + j], &cs[b * m + j], &sn[b * m + j], &rr);
+        Hb[j * m + j] = rr;
+        Hb[(j + 1) * m + j] = 0.0;
+        gb[j + 1] = -std::conj(sn[b * m + j]) * gb[j];
+        gb[j] = cs[b * m + j] * gb[j];
+        iters[b] += 1;
+        kused[b] = j + 1;
+        const double res = std::abs(gb[j + 1]) / bnorm[b];
+        if (!std::isfinite(res)) { nonfinite = true; active[b] = 0; continue; }
+        if (hn == 0.0) { active[b] = 0; if (res > c->opt.tol) breakdown = true; continue; }
+        if (res <= c->opt.tol || iters[b] >= c->opt.maxit) { active[b] = 0; continue; }
+        any_active = true;
+      }
+      if (!any_active) break;
+      launch_scale_inv(n, items, c->w, c->nrm, c->V + (size_t)(j + 1) * items * n, s); cnt(); post();
+    }
+    // y = R^{-1} g (back substitution) and x += Z y
+    for (int b = 0; b < items; ++b) {
+      const int k = kused[b];
+      const zc* Hb = &H[(size_t)b * (m + 1) * m];
+      const zc* gb = &g[(size_t)b * (m + 1)];
+      std::vector<zc> yv(k);
+      for (int i = k - 1; i >= 0; --i) {
+        zc acc = gb[i];
+        for (int l = i + 1; l < k; ++l) acc -= Hb[i * m + l] * yv[l];
+        yv[i] = acc / Hb[i * m + i];
+      }
+      for (int i = 0; i < m; ++i) yh[(size_t)b * m + i] = i < k ? make_double2(yv[i].real(), yv[i].imag()) : make_double2(0, 0);
+    }
+    CK(cudaMemcpyAsync(c->y, yh.data(), (size_t)items * m * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->kused, kused.data(), items * sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_xupdate<double2>(n, items, m, c->Z, c->y, c->kused, u, s); cnt(); post();
+    // true residual in FP64
+    launch_fine_apply<double>(c->H.g0, items, c->H.nrhs, c->H.cf64, c->H.h, 0.0, u, q,
+                              c->rd, 1, s);
+    launch_norm_part(n, items, c->rd, c->npart, nblk, s);
+    launch_reduce_norm(items, nblk, c->npart, c->nrm, s); cnt(3); post();
+    CK(cudaMemcpyAsync(c->hpin, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < items; ++b) {
+      beta[b] = c->hpin[b];
+      if (!std::isfinite(beta[b])) { nonfinite = true; done[b] = 1; }
+      if (!done[b] && beta[b] / bnorm[b] <= c->opt.tol) done[b] = 1;
+    }
+    if (nonfinite) break;
+    if (breakdown) break;
+  }
+  bool allconv = true;
+  for (int b = 0; b < items; ++b) {
+    const double rel = bnorm[b] > 0 ? beta[b] / bnorm[b] : 0.0;
+    const int conv = rel <= c->opt.tol;
+    allconv = allconv && conv;
+    if (info) { info[b].iters = iters[b]; info[b].relres = rel; info[b].converged = conv; }
+  }
+  if (nonfinite) { c->err = "non-finite residual norm"; return EHS_ERR_NONFINITE; }
+  if (!allconv && breakdown) { c->err = "Arnoldi breakdown before tol"; return EHS_ERR_BREAKDOWN; }
+  if (!allconv) { c->err = "maxit reached before tol"; return EHS_ERR_NOCONV; }
+  return EHS_OK;
+}
+
+void precond_apply(ehs_ctx* c, const double2* v, double2* z) {
+  const long long nv = (long long)c->H.items * c->n0;
+  if (c->opt.precond == EHS_PRECOND_DD) {
+    dd_apply(c, c->opt.prec, v, z);
+    return;
+  }
+  if (c->opt.prec == EHS_C64) {
+    launch_cast_c128_c64(nv, v, c->f_in, c->s); cnt(); post();
+    cycle_rec<float>(c, c->H, 0, c->f_in, c->f_out, false);
+    launch_cast_c64_c128(nv, c->f_out, z, c->s); cnt(); post();
+  } else {
+    cycle_rec<double>(c, c->H, 0, v, z, false);
+  }
+}
+
+__global__ void k_conj(long long n, double2* v) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) v[e].y = -v[e].y;
+}
+
+template <typename F> ehs_status guard(ehs_ctx* c, F f) {
+  try {
+    return f();
+  } catch (const ArgError& e) {
+    if (c) c->err = e.what();
+    return EHS_ERR_ARG;
+  } catch (const CudaError& e) {
+    if (c) c->err = e.what();
+    return EHS_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "device allocation failed";
+    return EHS_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    return EHS_ERR_CUDA;
+  }
+}
+
+ehs_status solve_common(ehs_ctx* c, const void* qin, void* uout, ehs_solve_info* info, bool adjoint) {
+  const size_t bytes = (size_t)c->H.items * c->n0 * sizeof(double2);
+  const bool qdev = is_device_ptr(qin), udev = is_device_ptr(uout);
+  const double2* q = (const double2*)qin;
+  double2* u = (double2*)uout;
+  if (!qdev || adjoint) {
+    CK(cudaMemcpyAsync(c->qd, qin, bytes, qdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+    q = c->qd;
+  }
+  if (!udev) u = c->ud;
+  const long long n = (long long)c->H.items * c->n0;
+  if (adjoint) { k_conj<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(n, c->qd); cnt(); post(); }
+  ehs_status st = fgmres(c, q, u, info);
+  if (adjoint) { k_conj<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(n, u); cnt(); post(); }
+  if (!udev) {
+    CK(cudaMemcpyAsync(uout, u, bytes, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+  }
+  return st;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void ehs_default_opts(ehs_opts* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->levels = 3;
+  o->alpha = 0.2;
+  const double w[8] = {0.75, 0.5, 0.25, 0.25, 0.25, 0.25, 0.25, 0.25};
+  for (int i = 0; i < 8; ++i) o->w[i] = w[i];
+  o->wp_ratio = 1.0;
+  o->nu_pre = o->nu_post = 1;
+  o->cycle = 1;
+  o->restart = 10;
+  o->maxit = 500;
+  o->tol = 1e-6;
+  o->precond = EHS_PRECOND_MG;
+  o->prec = EHS_C64;
+  o->nrhs = 1;
+  o->dd[0] = o->dd[1] = o->dd[2] = 1;
+  o->dd_overlap = 4;
+  o->dd_pad = 8;
+  o->dd_abl_max = 1.0;
+}
+
+ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* stream, ehs_ctx** out) {
+  if (!out) { g_create_err = "null output pointer"; return EHS_ERR_ARG; }
+  *out = nullptr;
+  ehs_ctx* c = new ehs_ctx();
+  ehs_status st = guard(c, [&]() -> ehs_status {
+    validate(prob, opts);
+    c->s = (cudaStream_t)stream;
+    c->prob = *prob;
+    c->opt = *opts;
+    c->d = prob->dim;
+    Hier& H = c->H;
+    H.g0 = mkgrid(prob->dim, prob->n[0], prob->n[1], prob->n[2]);
+    H.nlev = opts->levels;
+    H.nsets = prob->nmedia;
+    H.nrhs = opts->nrhs;
+    H.items = H.nsets * H.nrhs;
+    H.h = prob->h; H.alpha = opts->alpha;
+    H.wp_ratio = opts->wp_ratio > 0 ? opts->wp_ratio : 1.0;
+    H.nu1 = opts->nu_pre; H.nu2 = opts->nu_post; H.cyc = opts->cycle;
+    c->n0 = (long long)(c->d + 1) * H.g0.ncell;
+    const long long nc = (long long)H.nsets * H.g0.ncell;
+    check_media(c, prob->lambda, prob->mu, prob->rho, nc);
+    // media to the device (the caller's buffers are only read here)
+    double* dl = dalloc<double>(c, nc);
+    double* dm = dalloc<double>(c, nc);
+    double* dr = dalloc<double>(c, nc);
+    CK(cudaMemcpyAsync(dl, prob->lambda, nc * sizeof(double), cudaMemcpyDefault, c->s));
+    CK(cudaMemcpyAsync(dm, prob->mu, nc * sizeof(double), cudaMemcpyDefault, c->s));
+    CK(cudaMemcpyAsync(dr, prob->rho, nc * sizeof(double), cudaMemcpyDefault, c->s));
+    std::vector<double> om(H.nsets);
+    for (int m = 0; m < H.nsets; ++m) om[m] = prob->omegas ? prob->omegas[m] : prob->omega;
+    for (double w : om)
+      if (!std::isfinite(w) || !(w > 0)) throw ArgError("omega must be positive and finite");
+    double* dom = dalloc<double>(c, H.nsets);
+    CK(cudaMemcpyAsync(dom, om.data(), H.nsets * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    H.cf64 = dalloc<Coef4<double>>(c, nc);
+    launch_fine_coef<double>(H.g0, H.nsets, dl, dm, dr, dom, prob->abl_cells, prob->abl_max,
+                             prob->gamma_add, H.cf64, c->s);
+    cnt(); post();
+    CK(cudaStreamSynchronize(c->s));
+    dfree(c, dl); dfree(c, dm); dfree(c, dr); dfree(c, dom);
+    build_hier(c, H);
+    if (opts->precond == EHS_PRECOND_DD) dd_build(c);
+    // Krylov workspace
+    const int m = opts->restart, items = H.items;
+    const long long n = c->n0;
+    c->nblk = krylov_nblk(n);
+    c->V = dalloc<double2>(c, (size_t)(m + 1) * items * n);
+    c->Z = dalloc<double2>(c, (size_t)m * items * n);
+    c->w = dalloc<double2>(c, (size_t)items * n);
+    c->rd = dalloc<double2>(c, (size_t)items * n);
+    c->qd = dalloc<double2>(c, (size_t)items * n);
+    c->ud = dalloc<double2>(c, (size_t)items * n);
+    c->part = dalloc<double2>(c, (size_t)items * 12 * c->nblk);
+    c->hd = dalloc<double2>(c, (size_t)items * 12);
+    c->y = dalloc<double2>(c, (size_t)items * 12);
+    c->npart = dalloc<double>(c, (size_t)items * c->nblk);
+    c->nrm = dalloc<double>(c, items);
+    c->kused = dalloc<int>(c, items);
+    c->f_in = dalloc<float2>(c, (size_t)items * n);
+    c->f_out = dalloc<float2>(c, (size_t)items * n);
+    CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));
+    CK(cudaStreamSynchronize(c->s));
+    return EHS_OK;
+  });
+  if (st != EHS_OK) {
+    g_create_err = c->err;
+    ehs_destroy(c);
+    return st;
+  }
+  *out = c;
+  return EHS_OK;
+}
+
+ehs_status ehs_destroy(ehs_ctx* c) {
+  if (!c) return EHS_OK;
+  if (c->s) cudaStreamSynchronize(c->s);
+  for (void* p : c->allocs)
+    if (p) cudaFree(p);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  delete c;
+  return EHS_OK;
+}
+
+ehs_status ehs_op_apply(ehs_ctx* c, int level, int shifted, int prec, const void* x, void* y) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (level < 0 || level >= c->H.nlev) throw ArgError("level out of range");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!x || !y) throw ArgError("null vector");
+    const double alpha = (level == 0 && !shifted) ? 0.0 : c->H.alpha;
+    if (prec == EHS_C128) level_apply<double>(c, c->H, level, alpha, (const double2*)x, nullptr, (double2*)y, 0);
+    else level_apply<float>(c, c->H, level, alpha, (const float2*)x, nullptr, (float2*)y, 0);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_smooth(ehs_ctx* c, int level, int nsweeps, int prec, const void* b, void* x) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (level < 0 || level >= c->H.nlev - 1) throw ArgError("level out of range (the coarsest level is solved, not smoothed)");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!b || !x || nsweeps < 0) throw ArgError("bad argument");
+    for (int s = 0; s < nsweeps; ++s) {
+      if (prec == EHS_C128)
+        level_sweep<double>(c, c->H, level, (const double2*)b, (double2*)x, (double2*)c->H.lv[level].ws[0][2]);
+      else
+        level_sweep<float>(c, c->H, level, (const float2*)b, (float2*)x, (float2*)c->H.lv[level].ws[1][2]);
+    }
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_vcycle(ehs_ctx* c, int prec, const void* b, void* x) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!b || !x) throw ArgError("null vector");
+    if (prec == EHS_C128) cycle_rec<double>(c, c->H, 0, (const double2*)b, (double2*)x, false);
+    else cycle_rec<float>(c, c->H, 0, (const float2*)b, (float2*)x, false);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_dd_precond(ehs_ctx* c, int prec, const void* r, void* z) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (c->opt.precond != EHS_PRECOND_DD) throw ArgError("context was not created with the DD preconditioner");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!r || !z) throw ArgError("null vector");
+    dd_apply(c, prec, (const double2*)r, (double2*)z);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_fgmres_solve(ehs_ctx* c, const void* q, void* u, ehs_solve_info* info) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (!q || !u) throw ArgError("null vector");
+    return solve_common(c, q, u, info, false);
+  });
+}
+
+ehs_status ehs_adjoint_solve(ehs_ctx* c, const void* g, void* w, ehs_solve_info* info) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (!g || !w) throw ArgError("null vector");
+    return solve_common(c, g, w, info, true);
+  });
+}
+
+int ehs_items(const ehs_ctx* c) { return c ? c->H.items : 0; }
+long long ehs_level_len(const ehs_ctx* c, int level) {
+  if (!c || level < 0 || level >= c->H.nlev) return -1;
+  return (long long)(c->d + 1) * c->H.lv[level].g.ncell;
+}
+int ehs_level_dims(const ehs_ctx* c, int level, int n[3]) {
+  if (!c || level < 0 || level >= c->H.nlev) return -1;
+  for (int k = 0; k < 3; ++k) n[k] = c->H.lv[level].g.n[k];
+  return 0;
+}
+ehs_status ehs_sync(ehs_ctx* c) {
+  if (!c) return EHS_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->s);
+  if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return EHS_ERR_CUDA; }
+  return EHS_OK;
+}
+long long ehs_kernel_launches(void) { return g_launches.load(); }
+const char* ehs_last_error(const ehs_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

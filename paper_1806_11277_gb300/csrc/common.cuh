@@ -1,0 +1,134 @@
+// Shared device/host definitions of the GB300 elastic Helmholtz library.
+//
+// Layout of every vector (the "slot layout" of include/ehs.h): per batch
+// item, d+1 component arrays of ncell complex values each, [u_1, .., u_d, p];
+// x is the fastest index.  u_k[c] is the value on the low face of cell c in
+// direction k; the slot with i_k == 0 is a Dirichlet boundary face and is
+// always zero.  Complex numbers are interleaved (re, im).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define EHS_HD __host__ __device__ __forceinline__
+
+namespace ehs {
+
+template <typename T> struct CT;
+template <> struct CT<float> { typedef float2 type; };
+template <> struct CT<double> { typedef double2 type; };
+
+template <typename T> EHS_HD typename CT<T>::type mk(T re, T im) {
+  typename CT<T>::type z; z.x = re; z.y = im; return z;
+}
+EHS_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+EHS_HD double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+EHS_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+EHS_HD double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+EHS_HD float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+EHS_HD double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+EHS_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+EHS_HD double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// a + b * c
+EHS_HD float2 cfma(float2 b, float2 c, float2 a) {
+  return make_float2(fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x)), fmaf(b.x, c.y, fmaf(b.y, c.x, a.y)));
+}
+EHS_HD double2 cfma(double2 b, double2 c, double2 a) {
+  return make_double2(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
+}
+template <typename C> EHS_HD C czero() { C z; z.x = 0; z.y = 0; return z; }
+// 1 / z
+EHS_HD float2 cinv(float2 z) { float s = 1.0f / (z.x * z.x + z.y * z.y); return make_float2(z.x * s, -z.y * s); }
+EHS_HD double2 cinv(double2 z) { double s = 1.0 / (z.x * z.x + z.y * z.y); return make_double2(z.x * s, -z.y * s); }
+EHS_HD float2 to_c(float2 z, float) { return z; }
+EHS_HD float2 to_c(double2 z, float) { return make_float2((float)z.x, (float)z.y); }
+EHS_HD double2 to_c(float2 z, double) { return make_double2(z.x, z.y); }
+EHS_HD double2 to_c(double2 z, double) { return z; }
+
+// Grid of one multigrid level; n[0] = n_x, n[1] = n_y, n[2] = n_z (1 in 2D).
+struct Grid {
+  int d;
+  int n[3];
+  long long ncell;
+};
+
+EHS_HD void cell_coords(const Grid& g, long long c, int i[3]) {
+  i[0] = (int)(c % g.n[0]);
+  long long t = c / g.n[0];
+  i[1] = (int)(t % g.n[1]);
+  i[2] = (int)(t / g.n[1]);
+}
+EHS_HD long long cell_index(const Grid& g, const int i[3]) {
+  return ((long long)i[2] * g.n[1] + i[1]) * g.n[0] + i[0];
+}
+EHS_HD long long stride_of(const Grid& g, int k) {
+  return k == 0 ? 1 : (k == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
+}
+
+// Fine-level cell coefficients of the matrix-free operator: mu, 1/(lambda+mu),
+// mr = omega^2 rho and mi = omega rho gamma, so that the face mass term
+// -omega^2 A_f(rho (1 - i gamma/omega)) is -A_f(mr) + i A_f(mi) and each
+// coefficient set (medium) carries its own frequency.
+template <typename T> struct Coef4 { T mu, kap, mr, mi; };
+
+// ------------------------------------------------------------ stencil table
+// Stored operators of Galerkin levels: for each (row comp a, col comp b)
+// pair a box of offsets [lo, lo+ext) per direction.  Coefficients are stored
+// per coefficient set as [slot][cell] (cell fastest), slot = base + linear
+// offset index (x fastest).
+#define EHS_MAXPAIR 16
+struct PairBox {
+  int a, b;
+  int lo[3];
+  int ext[3];
+  int base;  // first slot of this pair
+};
+struct StencilLayout {
+  int npair;
+  int nslot;            // coefficients per cell
+  int row_first[5];     // pairs are sorted by row; pairs of row a: [row_first[a], row_first[a+1])
+  int pidx[4][4];       // pair index of (a, b), -1 if the pair is structurally zero
+  PairBox p[EHS_MAXPAIR];
+};
+
+// slot of coefficient (a, b, offset o) or -1 if outside the stored box
+EHS_HD int st_slot(const StencilLayout& L, int a, int b, int ox, int oy, int oz) {
+  int q = L.pidx[a][b];
+  if (q < 0) return -1;
+  const PairBox& P = L.p[q];
+  int ix = ox - P.lo[0], iy = oy - P.lo[1], iz = oz - P.lo[2];
+  if (ix < 0 || iy < 0 || iz < 0 || ix >= P.ext[0] || iy >= P.ext[1] || iz >= P.ext[2]) return -1;
+  return P.base + (iz * P.ext[1] + iy) * P.ext[0] + ix;
+}
+
+// Transfer weights (1D).  Kinds: 0 = vertex-like (u_k along k; interior faces
+// 1..n-1 are unknowns), 1 = cell-like with zero ghosts (u tangential),
+// 2 = cell-like with clamped ghosts (p).  pw(kind, j, J, nc) is the weight of
+// coarse index J in fine index j (fine grid has 2 nc cells).
+EHS_HD double pw(int kind, int j, int J, int nc) {
+  const int nf = 2 * nc;
+  if (kind == 0) {
+    if (j < 1 || j > nf - 1 || J < 1 || J > nc - 1) return 0.0;
+    if ((j & 1) == 0) return (j == 2 * J) ? 1.0 : 0.0;
+    return (J == (j - 1) / 2 || J == (j + 1) / 2) ? 0.5 : 0.0;
+  }
+  if (j < 0 || j > nf - 1 || J < 0 || J > nc - 1) return 0.0;
+  const int Jc = j >> 1;
+  const int nb = (j & 1) ? Jc + 1 : Jc - 1;
+  double w = 0.0;
+  if (J == Jc) w += 0.75;
+  if (nb >= 0 && nb < nc) {
+    if (J == nb) w += 0.25;
+  } else if (kind == 2 && J == Jc) {
+    w += 0.25;
+  }
+  return w;
+}
+// kind of component a along direction k
+EHS_HD int tkind(int a, int k, int d) { return a == d ? 2 : (a == k ? 0 : 1); }
+
+// a valid unknown slot?  (u_k at i_k == 0 is a boundary face)
+EHS_HD bool slot_valid(int a, int d, const int i[3]) { return a == d || i[a] >= 1; }
+
+enum { EHS_DEVERR_BOX = 1, EHS_DEVERR_SINGULAR = 2, EHS_DEVERR_NONFINITE = 4 };
+
+}  // namespace ehs

@@ -1,0 +1,452 @@
+// Fine-level (matrix-free) kernels of the mixed elastic Helmholtz operator.
+//
+// Operator (Sec. 2.1 eq. elasticHelmSystem / Sec. 3 eq.
+// elasticHelmReformulatedSystem, shifted per eq. shift with the zero-padded
+// shift matrix of Sec. 3):
+//   row u_k at face f (low face of cell c):
+//     sum_j [w+ (u_f - u_{f+e_j}) + w- (u_f - u_{f-e_j})] / h^2
+//     + (-mr_f + i (mi_f + alpha mr_f)) u_f + (p_c - p_{c-e_k}) / h
+//     with w = mu at the cell centre for j = k and the mean of the 4 cells
+//     around the edge for j != k (indices clamped); mr_f, mi_f are the face
+//     means of omega^2 rho and omega rho gamma;
+//   row p at cell c: sum_k (u_k(c) - u_k(c+e_k)) / h - p_c / (lambda+mu).
+// Outside the grid u is zero; the i_k == 0 slot of u_k is a boundary face.
+#include "kernels.h"
+
+namespace ehs {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ Coef4<T> ldcf(const Coef4<T>* p, long long c) {
+  Coef4<T> r;
+  if constexpr (sizeof(T) == 4) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p) + c);
+    r.mu = v.x; r.kap = v.y; r.mr = v.z; r.mi = v.w;
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p) + 2 * c;
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    r.mu = a.x; r.kap = a.y; r.mr = b.x; r.mi = b.y;
+  }
+  return r;
+}
+template <typename C> __device__ __forceinline__ C ldc(const C* p, long long i) { return __ldg(p + i); }
+
+template <typename T> struct FineP {
+  T h2inv, hinv, alpha;
+};
+
+// value and diagonal of row u_k at the face whose high cell is c (coords i)
+template <typename T, int D>
+__device__ __forceinline__ typename CT<T>::type row_u(
+    const Grid& g, int k, long long c, const int i[3], const Coef4<T>* cf,
+    const typename CT<T>::type* xk, const typename CT<T>::type* p, const FineP<T>& P,
+    typename CT<T>::type* diag) {
+  typedef typename CT<T>::type C;
+  const long long sk = stride_of(g, k);
+  const Coef4<T> c0 = ldcf(cf, c), c1 = ldcf(cf, c - sk);
+  const C xc = ldc(xk, c);
+  C xp = czero<C>(), xm = czero<C>();
+  if (i[k] + 1 < g.n[k]) xp = ldc(xk, c + sk);
+  if (i[k] - 1 >= 1) xm = ldc(xk, c - sk);
+  T wsum = c0.mu + c1.mu;
+  C nb = cadd(cscale(xp, c0.mu), cscale(xm, c1.mu));
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == k) continue;
+    const long long sj = stride_of(g, j);
+    const bool hp = i[j] + 1 < g.n[j], hm = i[j] - 1 >= 0;
+    const long long cp = hp ? c + sj : c, cm = hm ? c - sj : c;
+    const T base = c0.mu + c1.mu;
+    const T wp = T(0.25) * (base + ldcf(cf, cp).mu + ldcf(cf, cp - sk).mu);
+    const T wm = T(0.25) * (base + ldcf(cf, cm).mu + ldcf(cf, cm - sk).mu);
+    wsum += wp + wm;
+    if (hp) nb = cfma(mk<T>(wp, 0), ldc(xk, c + sj), nb);
+    if (hm) nb = cfma(mk<T>(wm, 0), ldc(xk, c - sj), nb);
+  }
+  const T rf = T(0.5) * (c0.mr + c1.mr), gf = T(0.5) * (c0.mi + c1.mi);
+  C dg = mk<T>(wsum * P.h2inv - rf, gf + P.alpha * rf);
+  *diag = dg;
+  C y = csub(cmul(dg, xc), cscale(nb, P.h2inv));
+  const C pc = ldc(p, c), pm = ldc(p, c - sk);
+  y = cadd(y, cscale(csub(pc, pm), P.hinv));
+  return y;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ typename CT<T>::type row_p(
+    const Grid& g, long long c, const int i[3], const Coef4<T>& c0,
+    const typename CT<T>::type* x, const FineP<T>& P) {
+  typedef typename CT<T>::type C;
+  const long long N = g.ncell;
+  C y = cscale(ldc(x + (long long)D * N, c), -c0.kap);
+  C s = czero<C>();
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const C* xk = x + (long long)k * N;
+    if (i[k] >= 1) s = cadd(s, ldc(xk, c));
+    if (i[k] + 1 < g.n[k]) s = csub(s, ldc(xk, c + stride_of(g, k)));
+  }
+  return cadd(y, cscale(s, P.hinv));
+}
+
+template <typename T, int D>
+__global__ void k_fine_apply(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, FineP<T> P,
+                             const typename CT<T>::type* __restrict__ x,
+                             const typename CT<T>::type* __restrict__ b,
+                             typename CT<T>::type* __restrict__ y, int mode) {
+  typedef typename CT<T>::type C;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int item = blockIdx.y;
+  const long long N = g.ncell;
+  const long long vo = (long long)item * (D + 1) * N;
+  const Coef4<T>* cs = cf + (long long)(item / nrhs) * N;
+  const C* xv = x + vo;
+  int i[3];
+  cell_coords(g, c, i);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    C r = czero<C>();
+    if (i[k] >= 1) {
+      C dg;
+      r = row_u<T, D>(g, k, c, i, cs, xv + (long long)k * N, xv + (long long)D * N, P, &dg);
+      if (mode) r = csub(ldc(b + vo + (long long)k * N, c), r);
+    }
+    y[vo + (long long)k * N + c] = r;
+  }
+  C r = row_p<T, D>(g, c, i, ldcf(cs, c), xv, P);
+  if (mode) r = csub(ldc(b + vo + (long long)D * N, c), r);
+  y[vo + (long long)D * N + c] = r;
+}
+
+// One colour of red-black economic Vanka.  Thread = pair of cells along x
+// (2t, 2t+1); the one of the requested colour is relaxed, the other one's p is
+// copied.  All u faces are written (each face belongs to exactly one cell of
+// each colour), so xo is a complete new iterate.
+template <typename T, int D>
+__global__ void k_fine_vanka(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, FineP<T> P,
+                             T wu, T wp, int colour, const typename CT<T>::type* __restrict__ b,
+                             const typename CT<T>::type* __restrict__ xi,
+                             typename CT<T>::type* __restrict__ xo) {
+  typedef typename CT<T>::type C;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long npair = g.ncell >> 1;
+  if (t >= npair) return;
+  const int item = blockIdx.y;
+  const long long N = g.ncell;
+  const long long vo = (long long)item * (D + 1) * N;
+  const Coef4<T>* cs = cf + (long long)(item / nrhs) * N;
+  const C* x = xi + vo;
+  const C* bb = b + vo;
+  C* xout = xo + vo;
+  long long c = 2 * t;
+  int i[3];
+  cell_coords(g, c, i);
+  if (((i[0] + i[1] + i[2]) & 1) != colour) { ++c; ++i[0]; }
+  const long long co = ((c & 1) ? c - 1 : c + 1);  // the other cell of the pair
+  xout[(long long)D * N + co] = ldc(x + (long long)D * N, co);
+
+  const Coef4<T> c0 = ldcf(cs, c);
+  C r[2 * D + 1], dg[2 * D], g_[2 * D];
+  bool ok[2 * D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const long long sk = stride_of(g, k);
+    const C* xk = x + (long long)k * N;
+    const C* pp = x + (long long)D * N;
+    ok[k] = i[k] >= 1;
+    if (ok[k]) {
+      r[k] = csub(ldc(bb + (long long)k * N, c), row_u<T, D>(g, k, c, i, cs, xk, pp, P, &dg[k]));
+    } else {
+      r[k] = czero<C>(); dg[k] = mk<T>(1, 0);
+    }
+    g_[k] = mk<T>(P.hinv, 0);            // K[u_k(c), p(c)] = +1/h
+    ok[D + k] = i[k] + 1 < g.n[k];
+    if (ok[D + k]) {
+      int ih[3] = {i[0], i[1], i[2]};
+      ih[k] += 1;
+      r[D + k] = csub(ldc(bb + (long long)k * N, c + sk),
+                      row_u<T, D>(g, k, c + sk, ih, cs, xk, pp, P, &dg[D + k]));
+    } else {
+      r[D + k] = czero<C>(); dg[D + k] = mk<T>(1, 0);
+    }
+    g_[D + k] = mk<T>(-P.hinv, 0);       // K[u_k(c+e_k), p(c)] = -1/h
+  }
+  r[2 * D] = csub(ldc(bb + (long long)D * N, c), row_p<T, D>(g, c, i, c0, x, P));
+  // arrowhead solve: B = [[diag(dg), g], [g^T, -kap]]
+  C sch = mk<T>(-c0.kap, 0);
+  C rp = r[2 * D];
+  C dinv[2 * D];
+#pragma unroll
+  for (int a = 0; a < 2 * D; ++a) {
+    if (!ok[a]) continue;
+    dinv[a] = cinv(dg[a]);
+    const C gd = cmul(g_[a], dinv[a]);
+    sch = csub(sch, cmul(gd, g_[a]));
+    rp = csub(rp, cmul(gd, r[a]));
+  }
+  const C dp = cmul(rp, cinv(sch));
+  xout[(long long)D * N + c] = cfma(mk<T>(wp, 0), dp, ldc(x + (long long)D * N, c));
+#pragma unroll
+  for (int a = 0; a < 2 * D; ++a) {
+    if (!ok[a]) continue;
+    const int k = a % D;
+    const long long idx = (long long)k * N + c + (a >= D ? stride_of(g, k) : 0);
+    const C du = cmul(csub(r[a], cmul(g_[a], dp)), dinv[a]);
+    xout[idx] = cfma(mk<T>(wu, 0), du, ldc(x, idx));
+  }
+}
+
+__device__ __forceinline__ double abl_ramp(const Grid& g, const int i[3], int L) {
+  if (L <= 0) return 0.0;
+  double r = 0.0;
+  for (int k = 0; k < g.d; ++k) {
+    int dep = max(max(L - i[k], i[k] - (g.n[k] - 1 - L)), 0);
+    double t = (double)dep / L;
+    r = fmax(r, t * t);
+  }
+  return r;
+}
+
+template <typename T>
+__global__ void k_fine_coef(Grid g, const double* lam, const double* mu, const double* rho,
+                            const double* omegas, int L, double abl_max, double gamma_add,
+                            Coef4<T>* out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const long long o = (long long)blockIdx.y * g.ncell + c;
+  const double omega = omegas[blockIdx.y];
+  int i[3];
+  cell_coords(g, c, i);
+  const double gam = gamma_add + omega * abl_max * abl_ramp(g, i, L);
+  Coef4<T> r;
+  r.mu = (T)mu[o];
+  r.kap = (T)(1.0 / (lam[o] + mu[o]));
+  r.mr = (T)(omega * omega * rho[o]);
+  r.mi = (T)(omega * rho[o] * gam);
+  out[o] = r;
+}
+
+template <typename T>
+__global__ void k_coef_cast(long long n, const Coef4<double>* in, Coef4<T>* out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  Coef4<double> v = in[c];
+  Coef4<T> r;
+  r.mu = (T)v.mu; r.kap = (T)v.kap; r.mr = (T)v.mr; r.mi = (T)v.mi;
+  out[c] = r;
+}
+
+// Subdomain coefficients (Algorithm DD, padded subdomains with an absorbing
+// layer in the padding).  blockIdx.y = subdomain-set index.
+template <typename T>
+__global__ void k_sub_coef(Grid gl, Grid gg, int nsub, const int* origin, const int* omlo,
+                           const int* omhi, const int* padlo, const int* padhi, const int* subset,
+                           const Coef4<double>* glob, double ddabl, Coef4<T>* out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= gl.ncell) return;
+  const int s = blockIdx.y;            // = set * nsub + sub
+  const int sub = s % nsub;
+  const int gset = subset[s];
+  int i[3], gi[3];
+  cell_coords(gl, c, i);
+  double ramp = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    int gk = origin[sub * 3 + k] + i[k];
+    gk = min(max(gk, omlo[sub * 3 + k]), omhi[sub * 3 + k] - 1);
+    gi[k] = gk;
+    if (k < gl.d) {
+      const int plo = padlo[sub * 3 + k], phi = padhi[sub * 3 + k];
+      const int ext = omhi[sub * 3 + k] - omlo[sub * 3 + k];
+      double dep = 0.0;
+      if (plo && i[k] < plo) dep = (double)(plo - i[k]) / plo;
+      if (phi && i[k] >= plo + ext) dep = (double)(i[k] - (plo + ext) + 1) / phi;
+      ramp = fmax(ramp, dep * dep);
+    }
+  }
+  Coef4<double> v = glob[(long long)gset * gg.ncell + cell_index(gg, gi)];
+  Coef4<T> r;
+  r.mu = (T)v.mu; r.kap = (T)v.kap; r.mr = (T)v.mr;
+  r.mi = (T)(v.mi + v.mr * ddabl * ramp);   // omega rho (gamma + omega*ddabl*ramp)
+  out[(long long)s * gl.ncell + c] = r;
+}
+
+// level-0 stencil table of K_s (double), layout from fine_table_layout
+template <int D>
+__global__ void k_fine_table(Grid g, const Coef4<double>* __restrict__ cf, FineP<double> P,
+                             StencilLayout L, double2* __restrict__ tab) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const long long N = g.ncell;
+  const int set = blockIdx.y;
+  const Coef4<double>* cs = cf + (long long)set * N;
+  double2* T0 = tab + (long long)set * L.nslot * N;
+  for (int q = 0; q < L.nslot; ++q) T0[(long long)q * N + c] = make_double2(0, 0);
+  int i[3];
+  cell_coords(g, c, i);
+  const Coef4<double> c0 = cs[c];
+  for (int k = 0; k < D; ++k) {
+    if (i[k] < 1) continue;
+    const long long sk = stride_of(g, k);
+    const Coef4<double> c1 = cs[c - sk];
+    int o[3] = {0, 0, 0};
+    double wsum = c0.mu + c1.mu;
+    // normal neighbours
+    if (i[k] + 1 < g.n[k]) { o[k] = 1; T0[(long long)st_slot(L, k, k, o[0], o[1], o[2]) * N + c].x = -c0.mu * P.h2inv; }
+    if (i[k] - 1 >= 1) { o[k] = -1; T0[(long long)st_slot(L, k, k, o[0], o[1], o[2]) * N + c].x = -c1.mu * P.h2inv; }
+    o[k] = 0;
+    for (int j = 0; j < D; ++j) {
+      if (j == k) continue;
+      const long long sj = stride_of(g, j);
+      const bool hp = i[j] + 1 < g.n[j], hm = i[j] - 1 >= 0;
+      const long long cp = hp ? c + sj : c, cm = hm ? c - sj : c;
+      const double base = c0.mu + c1.mu;
+      const double wp = 0.25 * (base + cs[cp].mu + cs[cp - sk].mu);
+      const double wm = 0.25 * (base + cs[cm].mu + cs[cm - sk].mu);
+      wsum += wp + wm;
+      if (hp) { o[j] = 1; T0[(long long)st_slot(L, k, k, o[0], o[1], o[2]) * N + c].x = -wp * P.h2inv; }
+      if (hm) { o[j] = -1; T0[(long long)st_slot(L, k, k, o[0], o[1], o[2]) * N + c].x = -wm * P.h2inv; }
+      o[j] = 0;
+    }
+    const double rf = 0.5 * (c0.mr + c1.mr), gf = 0.5 * (c0.mi + c1.mi);
+    T0[(long long)st_slot(L, k, k, 0, 0, 0) * N + c] =
+        make_double2(wsum * P.h2inv - rf, gf + P.alpha * rf);
+    T0[(long long)st_slot(L, k, D, 0, 0, 0) * N + c].x = P.hinv;
+    o[k] = -1;
+    T0[(long long)st_slot(L, k, D, o[0], o[1], o[2]) * N + c].x = -P.hinv;
+  }
+  for (int k = 0; k < D; ++k) {
+    if (i[k] >= 1) T0[(long long)st_slot(L, D, k, 0, 0, 0) * N + c].x = P.hinv;
+    if (i[k] + 1 < g.n[k]) {
+      int o[3] = {0, 0, 0};
+      o[k] = 1;
+      T0[(long long)st_slot(L, D, k, o[0], o[1], o[2]) * N + c].x = -P.hinv;
+    }
+  }
+  T0[(long long)st_slot(L, D, D, 0, 0, 0) * N + c].x = -c0.kap;
+}
+
+template <typename T> FineP<T> mkP(double h, double alpha) {
+  FineP<T> P;
+  P.h2inv = (T)(1.0 / (h * h));
+  P.hinv = (T)(1.0 / h);
+  P.alpha = (T)alpha;
+  return P;
+}
+
+inline dim3 grid1(long long n, int items, int bs) { return dim3((unsigned)((n + bs - 1) / bs), items, 1); }
+
+}  // namespace
+
+template <typename T>
+void launch_fine_coef(const Grid& g, int nsets, const double* lam, const double* mu,
+                      const double* rho, const double* omegas, int abl_cells, double abl_max,
+                      double gamma_add, Coef4<T>* out, cudaStream_t s) {
+  k_fine_coef<T><<<grid1(g.ncell, nsets, 256), 256, 0, s>>>(g, lam, mu, rho, omegas, abl_cells,
+                                                             abl_max, gamma_add, out);
+}
+
+template <typename T>
+void launch_sub_coef(const Grid& gl, const Grid& gg, int nsets_glob, int nsub, const int* d_origin,
+                     const int* d_omlo, const int* d_omhi, const int* d_padlo, const int* d_padhi,
+                     const int* d_subset, const Coef4<double>* glob, double ddabl,
+                     Coef4<T>* out, cudaStream_t s) {
+  k_sub_coef<T><<<grid1(gl.ncell, nsets_glob * nsub, 256), 256, 0, s>>>(
+      gl, gg, nsub, d_origin, d_omlo, d_omhi, d_padlo, d_padhi, d_subset, glob, ddabl, out);
+}
+
+template <typename T>
+void launch_coef_cast(long long n, const Coef4<double>* in, Coef4<T>* out, cudaStream_t s) {
+  k_coef_cast<T><<<grid1(n, 1, 256), 256, 0, s>>>(n, in, out);
+}
+
+template <typename T>
+void launch_fine_apply(const Grid& g, int items, int nrhs, const Coef4<T>* cf, double h,
+                       double alpha, const typename CT<T>::type* x,
+                       const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
+                       cudaStream_t s) {
+  const FineP<T> P = mkP<T>(h, alpha);
+  if (g.d == 2)
+    k_fine_apply<T, 2><<<grid1(g.ncell, items, 256), 256, 0, s>>>(g, nrhs, cf, P, x, b, y, mode);
+  else
+    k_fine_apply<T, 3><<<grid1(g.ncell, items, 256), 256, 0, s>>>(g, nrhs, cf, P, x, b, y, mode);
+}
+
+template <typename T>
+void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, double h,
+                       double alpha, T wu, T wp, int colour,
+                       const typename CT<T>::type* b, const typename CT<T>::type* xi,
+                       typename CT<T>::type* xo, cudaStream_t s) {
+  const FineP<T> P = mkP<T>(h, alpha);
+  const long long np = g.ncell / 2;
+  if (g.d == 2)
+    k_fine_vanka<T, 2><<<grid1(np, items, 128), 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo);
+  else
+    k_fine_vanka<T, 3><<<grid1(np, items, 128), 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo);
+}
+
+void fine_table_layout(int d, StencilLayout* L) {
+  *L = StencilLayout{};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) L->pidx[a][b] = -1;
+  int q = 0, base = 0;
+  auto add = [&](int a, int b, const int lo[3], const int ext[3]) {
+    PairBox& P = L->p[q];
+    P.a = a; P.b = b;
+    for (int k = 0; k < 3; ++k) { P.lo[k] = lo[k]; P.ext[k] = ext[k]; }
+    P.base = base;
+    base += ext[0] * ext[1] * ext[2];
+    L->pidx[a][b] = q++;
+  };
+  for (int a = 0; a <= d; ++a) {
+    L->row_first[a] = q;
+    if (a < d) {
+      int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+      for (int k = 0; k < d; ++k) { lo[k] = -1; ext[k] = 3; }
+      add(a, a, lo, ext);
+      int lo2[3] = {0, 0, 0}, ext2[3] = {1, 1, 1};
+      lo2[a] = -1; ext2[a] = 2;
+      add(a, d, lo2, ext2);
+    } else {
+      for (int b = 0; b < d; ++b) {
+        int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+        ext[b] = 2;
+        add(d, b, lo, ext);
+      }
+      int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+      add(d, d, lo, ext);
+    }
+  }
+  L->row_first[d + 1] = q;
+  L->npair = q;
+  L->nslot = base;
+}
+
+void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double h,
+                       double alpha, const StencilLayout& L, double2* tab, cudaStream_t s) {
+  const FineP<double> P = mkP<double>(h, alpha);
+  if (g.d == 2)
+    k_fine_table<2><<<grid1(g.ncell, nsets, 128), 128, 0, s>>>(g, cf, P, L, tab);
+  else
+    k_fine_table<3><<<grid1(g.ncell, nsets, 128), 128, 0, s>>>(g, cf, P, L, tab);
+}
+
+#define INST(T)                                                                                  \
+  template void launch_fine_coef<T>(const Grid&, int, const double*, const double*, const double*, \
+                                    const double*, int, double, double, Coef4<T>*, cudaStream_t);  \
+  template void launch_sub_coef<T>(const Grid&, const Grid&, int, int, const int*, const int*,     \
+                                   const int*, const int*, const int*, const int*,                 \
+                                   const Coef4<double>*, double, Coef4<T>*, cudaStream_t);         \
+  template void launch_coef_cast<T>(long long, const Coef4<double>*, Coef4<T>*, cudaStream_t);     \
+  template void launch_fine_apply<T>(const Grid&, int, int, const Coef4<T>*, double,              \
+                                     double, const CT<T>::type*, const CT<T>::type*,              \
+                                     CT<T>::type*, int, cudaStream_t);                             \
+  template void launch_fine_vanka<T>(const Grid&, int, int, const Coef4<T>*, double,              \
+                                     double, T, T, int, const CT<T>::type*, const CT<T>::type*,    \
+                                     CT<T>::type*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace ehs

@@ -1,0 +1,343 @@
+// Galerkin coarse operators K_c = P^T K P (Sec. 2.2 eq. coarseGridMatrix,
+// built on the shifted operator as Sec. 3 prescribes) stored as per-cell
+// stencil tables, and the kernels that apply and relax them.
+//
+// The table keeps, for every (row component a, column component b) pair, a
+// box of offsets; the coarse box of a pair follows from the fine box and the
+// 1D transfer supports, so the hierarchy never stores offsets it cannot use.
+#include <algorithm>
+#include <stdexcept>
+#include "kernels.h"
+
+namespace ehs {
+
+// ------------------------------------------------------------------ layout
+void coarse_layout(int d, const StencilLayout& F, StencilLayout* C) {
+  *C = StencilLayout{};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) C->pidx[a][b] = -1;
+  const int nc = 64, I = 32;
+  int base = 0;
+  for (int q = 0; q < F.npair; ++q) {
+    const PairBox& P = F.p[q];
+    PairBox& Q = C->p[q];
+    Q.a = P.a; Q.b = P.b;
+    for (int k = 0; k < 3; ++k) {
+      if (k >= d) { Q.lo[k] = 0; Q.ext[k] = 1; continue; }
+      const int ka = tkind(P.a, k, d), kb = tkind(P.b, k, d);
+      int mn = 1 << 30, mx = -(1 << 30);
+      for (int i = 2 * I - 4; i <= 2 * I + 5; ++i) {
+        if (pw(ka, i, I, nc) == 0.0) continue;
+        for (int o = P.lo[k]; o < P.lo[k] + P.ext[k]; ++o) {
+          const int j = i + o;
+          for (int J = j / 2 - 3; J <= j / 2 + 3; ++J) {
+            if (pw(kb, j, J, nc) == 0.0) continue;
+            mn = std::min(mn, J - I);
+            mx = std::max(mx, J - I);
+          }
+        }
+      }
+      Q.lo[k] = mn;
+      Q.ext[k] = mx - mn + 1;
+    }
+    Q.base = base;
+    base += Q.ext[0] * Q.ext[1] * Q.ext[2];
+    C->pidx[Q.a][Q.b] = q;
+  }
+  C->npair = F.npair;
+  C->nslot = base;
+  for (int a = 0; a < 5; ++a) C->row_first[a] = F.row_first[a];
+}
+
+namespace {
+
+#define EHS_MAXROW 512
+
+// 1D list of (fine index, weight) of coarse index I, and of (coarse index,
+// weight) of fine index j.
+__device__ __forceinline__ int fine_support(int kind, int I, int nc, int* idx, double* w) {
+  int n = 0;
+  for (int i = 2 * I - 2; i <= 2 * I + 3; ++i) {
+    const double v = pw(kind, i, I, nc);
+    if (v != 0.0) { idx[n] = i; w[n] = v; ++n; }
+  }
+  return n;
+}
+__device__ __forceinline__ int coarse_support(int kind, int j, int nc, int* idx, double* w) {
+  int n = 0;
+  for (int J = (j >> 1) - 1; J <= (j >> 1) + 1; ++J) {
+    const double v = pw(kind, j, J, nc);
+    if (v != 0.0) { idx[n] = J; w[n] = v; ++n; }
+  }
+  return n;
+}
+
+// one thread per (coarse cell, row component)
+template <int D>
+__global__ void k_galerkin(Grid gf, Grid gc, StencilLayout Lf, const double2* __restrict__ tf,
+                           StencilLayout Lc, double2* __restrict__ tc, int* err) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.ncell * (D + 1)) return;
+  const int a = (int)(t / gc.ncell);
+  const long long C = t % gc.ncell;
+  const int set = blockIdx.y;
+  const double2* TF = tf + (long long)set * Lf.nslot * gf.ncell;
+  double2* TC = tc + (long long)set * Lc.nslot * gc.ncell;
+  const int q0 = Lc.row_first[a], q1 = Lc.row_first[a + 1];
+  const int s0 = Lc.p[q0].base;
+  const int s1 = (q1 < Lc.npair) ? Lc.p[q1].base : Lc.nslot;
+  double2 acc[EHS_MAXROW];
+  for (int s = 0; s < s1 - s0; ++s) acc[s] = make_double2(0, 0);
+  int Ic[3];
+  cell_coords(gc, C, Ic);
+  if (slot_valid(a, D, Ic)) {
+    int fi[3][6];
+    double fw[3][6];
+    int nf[3] = {1, 1, 1};
+    for (int k = 0; k < 3; ++k) {
+      if (k < D) nf[k] = fine_support(tkind(a, k, D), Ic[k], gc.n[k], fi[k], fw[k]);
+      else { fi[k][0] = 0; fw[k][0] = 1.0; }
+    }
+    for (int az = 0; az < nf[2]; ++az)
+      for (int ay = 0; ay < nf[1]; ++ay)
+        for (int ax = 0; ax < nf[0]; ++ax) {
+          const int i[3] = {fi[0][ax], fi[1][ay], fi[2][az]};
+          if (!slot_valid(a, D, i)) continue;
+          const double wi = fw[0][ax] * fw[1][ay] * fw[2][az];
+          const long long ci = cell_index(gf, i);
+          for (int q = Lf.row_first[a]; q < Lf.row_first[a + 1]; ++q) {
+            const PairBox& P = Lf.p[q];
+            const int b = P.b;
+            const int qc = Lc.pidx[a][b];
+            const PairBox& Q = Lc.p[qc];
+            for (int oz = 0; oz < P.ext[2]; ++oz)
+              for (int oy = 0; oy < P.ext[1]; ++oy)
+                for (int ox = 0; ox < P.ext[0]; ++ox) {
+                  const int s = P.base + (oz * P.ext[1] + oy) * P.ext[0] + ox;
+                  const double2 kv = TF[(long long)s * gf.ncell + ci];
+                  if (kv.x == 0.0 && kv.y == 0.0) continue;
+                  const int j[3] = {i[0] + P.lo[0] + ox, i[1] + P.lo[1] + oy, i[2] + P.lo[2] + oz};
+                  bool in = true;
+                  for (int k = 0; k < D; ++k) in = in && j[k] >= 0 && j[k] < gf.n[k];
+                  if (!in || !slot_valid(b, D, j)) continue;
+                  int ci2[3][3];
+                  double cw[3][3];
+                  int nn[3] = {1, 1, 1};
+                  for (int k = 0; k < 3; ++k) {
+                    if (k < D) nn[k] = coarse_support(tkind(b, k, D), j[k], gc.n[k], ci2[k], cw[k]);
+                    else { ci2[k][0] = 0; cw[k][0] = 1.0; }
+                  }
+                  for (int bz = 0; bz < nn[2]; ++bz)
+                    for (int by = 0; by < nn[1]; ++by)
+                      for (int bx = 0; bx < nn[0]; ++bx) {
+                        const double w = wi * cw[0][bx] * cw[1][by] * cw[2][bz];
+                        const int O[3] = {ci2[0][bx] - Ic[0], ci2[1][by] - Ic[1], ci2[2][bz] - Ic[2]};
+                        const int lx = O[0] - Q.lo[0], ly = O[1] - Q.lo[1], lz = O[2] - Q.lo[2];
+                        if (lx < 0 || ly < 0 || lz < 0 || lx >= Q.ext[0] || ly >= Q.ext[1] ||
+                            lz >= Q.ext[2]) {
+                          atomicOr(err, EHS_DEVERR_BOX);
+                          continue;
+                        }
+                        const int sl = Q.base - s0 + (lz * Q.ext[1] + ly) * Q.ext[0] + lx;
+                        acc[sl].x += w * kv.x;
+                        acc[sl].y += w * kv.y;
+                      }
+                }
+          }
+        }
+  }
+  for (int s = 0; s < s1 - s0; ++s) TC[(long long)(s0 + s) * gc.ncell + C] = acc[s];
+}
+
+template <typename C>
+__global__ void k_table_cast(long long n, const double2* in, C* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = in[i];
+    C r; r.x = v.x; r.y = v.y;
+    out[i] = r;
+  }
+}
+
+// value of row a at cell c (coords i) of the stored operator
+template <typename T, int D>
+__device__ __forceinline__ typename CT<T>::type st_row(
+    const Grid& g, const StencilLayout& L, const typename CT<T>::type* tab, int a, long long c,
+    const int i[3], const typename CT<T>::type* x) {
+  typedef typename CT<T>::type Cx;
+  Cx y = czero<Cx>();
+  const long long N = g.ncell;
+  for (int q = L.row_first[a]; q < L.row_first[a + 1]; ++q) {
+    const PairBox& P = L.p[q];
+    const Cx* xb = x + (long long)P.b * N;
+    int s = P.base;
+    for (int oz = 0; oz < P.ext[2]; ++oz) {
+      const int jz = i[2] + P.lo[2] + oz;
+      for (int oy = 0; oy < P.ext[1]; ++oy) {
+        const int jy = i[1] + P.lo[1] + oy;
+        const bool rowin = jz >= 0 && jz < g.n[2] && jy >= 0 && jy < g.n[1];
+        for (int ox = 0; ox < P.ext[0]; ++ox, ++s) {
+          const int jx = i[0] + P.lo[0] + ox;
+          if (rowin && jx >= 0 && jx < g.n[0]) {
+            const long long cj = ((long long)jz * g.n[1] + jy) * g.n[0] + jx;
+            y = cfma(__ldg(tab + (long long)s * N + c), __ldg(xb + cj), y);
+          }
+        }
+      }
+    }
+  }
+  return y;
+}
+
+template <typename T, int D>
+__global__ void k_st_apply(Grid g, int nrhs, StencilLayout L, const typename CT<T>::type* __restrict__ tab,
+                           const typename CT<T>::type* __restrict__ x,
+                           const typename CT<T>::type* __restrict__ b,
+                           typename CT<T>::type* __restrict__ y, int mode) {
+  typedef typename CT<T>::type Cx;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int item = blockIdx.y;
+  const long long N = g.ncell;
+  const long long vo = (long long)item * (D + 1) * N;
+  const Cx* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  int i[3];
+  cell_coords(g, c, i);
+  for (int a = 0; a <= D; ++a) {
+    Cx r = czero<Cx>();
+    if (slot_valid(a, D, i)) {
+      r = st_row<T, D>(g, L, ts, a, c, i, x + vo);
+      if (mode) r = csub(__ldg(b + vo + (long long)a * N + c), r);
+    }
+    y[vo + (long long)a * N + c] = r;
+  }
+}
+
+template <typename T, int D>
+__global__ void k_st_vanka(Grid g, int nrhs, StencilLayout L, const typename CT<T>::type* __restrict__ tab,
+                           T wu, T wp, int colour, const typename CT<T>::type* __restrict__ b,
+                           const typename CT<T>::type* __restrict__ xi,
+                           typename CT<T>::type* __restrict__ xo) {
+  typedef typename CT<T>::type Cx;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long N = g.ncell;
+  if (t >= N / 2) return;
+  const int item = blockIdx.y;
+  const long long vo = (long long)item * (D + 1) * N;
+  const Cx* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  const Cx* x = xi + vo;
+  const Cx* bb = b + vo;
+  Cx* xout = xo + vo;
+  long long c = 2 * t;
+  int i[3];
+  cell_coords(g, c, i);
+  if (((i[0] + i[1] + i[2]) & 1) != colour) { ++c; ++i[0]; }
+  const long long co = (c & 1) ? c - 1 : c + 1;
+  xout[(long long)D * N + co] = __ldg(x + (long long)D * N + co);
+
+  Cx r[2 * D + 1], dg[2 * D], gr[2 * D], gc_[2 * D];
+  bool ok[2 * D];
+  for (int k = 0; k < D; ++k) {
+    const long long sk = stride_of(g, k);
+    int o[3] = {0, 0, 0};
+    ok[k] = i[k] >= 1;
+    if (ok[k]) {
+      r[k] = csub(__ldg(bb + (long long)k * N + c), st_row<T, D>(g, L, ts, k, c, i, x));
+      dg[k] = __ldg(ts + (long long)st_slot(L, k, k, 0, 0, 0) * N + c);
+      gr[k] = __ldg(ts + (long long)st_slot(L, k, D, 0, 0, 0) * N + c);   // K[u_k(c), p(c)]
+      gc_[k] = __ldg(ts + (long long)st_slot(L, D, k, 0, 0, 0) * N + c);  // K[p(c), u_k(c)]
+    }
+    ok[D + k] = i[k] + 1 < g.n[k];
+    if (ok[D + k]) {
+      int ih[3] = {i[0], i[1], i[2]};
+      ih[k] += 1;
+      r[D + k] = csub(__ldg(bb + (long long)k * N + c + sk), st_row<T, D>(g, L, ts, k, c + sk, ih, x));
+      dg[D + k] = __ldg(ts + (long long)st_slot(L, k, k, 0, 0, 0) * N + c + sk);
+      o[k] = -1;
+      gr[D + k] = __ldg(ts + (long long)st_slot(L, k, D, o[0], o[1], o[2]) * N + c + sk);
+      o[k] = 1;
+      gc_[D + k] = __ldg(ts + (long long)st_slot(L, D, k, o[0], o[1], o[2]) * N + c);
+    }
+  }
+  r[2 * D] = csub(__ldg(bb + (long long)D * N + c), st_row<T, D>(g, L, ts, D, c, i, x));
+  Cx sch = __ldg(ts + (long long)st_slot(L, D, D, 0, 0, 0) * N + c);
+  Cx rp = r[2 * D];
+  Cx dinv[2 * D];
+  for (int a = 0; a < 2 * D; ++a) {
+    if (!ok[a]) continue;
+    dinv[a] = cinv(dg[a]);
+    sch = csub(sch, cmul(cmul(gc_[a], dinv[a]), gr[a]));
+    rp = csub(rp, cmul(cmul(gc_[a], dinv[a]), r[a]));
+  }
+  const Cx dp = cmul(rp, cinv(sch));
+  xout[(long long)D * N + c] = cfma(mk<T>(wp, 0), dp, __ldg(x + (long long)D * N + c));
+  for (int a = 0; a < 2 * D; ++a) {
+    if (!ok[a]) continue;
+    const int k = a % D;
+    const long long idx = (long long)k * N + c + (a >= D ? stride_of(g, k) : 0);
+    const Cx du = cmul(csub(r[a], cmul(gr[a], dp)), dinv[a]);
+    xout[idx] = cfma(mk<T>(wu, 0), du, __ldg(x + idx));
+  }
+}
+
+inline dim3 grid1(long long n, int items, int bs) { return dim3((unsigned)((n + bs - 1) / bs), items, 1); }
+
+}  // namespace
+
+void launch_galerkin(const Grid& gf, const Grid& gc, int nsets, const StencilLayout& Lf,
+                     const double2* tf, const StencilLayout& Lc, double2* tc, int* err,
+                     cudaStream_t s) {
+  int mx = 0;
+  for (int a = 0; a <= gf.d; ++a) {
+    const int q0 = Lc.row_first[a], q1 = Lc.row_first[a + 1];
+    const int s1 = q1 < Lc.npair ? Lc.p[q1].base : Lc.nslot;
+    mx = std::max(mx, s1 - Lc.p[q0].base);
+  }
+  if (mx > EHS_MAXROW) throw std::runtime_error("coarse stencil row exceeds EHS_MAXROW");
+  const long long n = gc.ncell * (gf.d + 1);
+  if (gf.d == 2)
+    k_galerkin<2><<<grid1(n, nsets, 64), 64, 0, s>>>(gf, gc, Lf, tf, Lc, tc, err);
+  else
+    k_galerkin<3><<<grid1(n, nsets, 64), 64, 0, s>>>(gf, gc, Lf, tf, Lc, tc, err);
+}
+
+template <typename T>
+void launch_table_cast(long long n, const double2* in, typename CT<T>::type* out, cudaStream_t s) {
+  k_table_cast<typename CT<T>::type><<<grid1(n, 1, 256), 256, 0, s>>>(n, in, out);
+}
+
+template <typename T>
+void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
+                     const typename CT<T>::type* tab, const typename CT<T>::type* x,
+                     const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
+                     cudaStream_t s) {
+  if (g.d == 2)
+    k_st_apply<T, 2><<<grid1(g.ncell, items, 128), 128, 0, s>>>(g, nrhs, L, tab, x, b, y, mode);
+  else
+    k_st_apply<T, 3><<<grid1(g.ncell, items, 128), 128, 0, s>>>(g, nrhs, L, tab, x, b, y, mode);
+}
+
+template <typename T>
+void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
+                     const typename CT<T>::type* tab, T wu, T wp, int colour,
+                     const typename CT<T>::type* b, const typename CT<T>::type* xi,
+                     typename CT<T>::type* xo, cudaStream_t s) {
+  if (g.d == 2)
+    k_st_vanka<T, 2><<<grid1(g.ncell / 2, items, 128), 128, 0, s>>>(g, nrhs, L, tab, wu, wp, colour, b, xi, xo);
+  else
+    k_st_vanka<T, 3><<<grid1(g.ncell / 2, items, 128), 128, 0, s>>>(g, nrhs, L, tab, wu, wp, colour, b, xi, xo);
+}
+
+#define INST(T)                                                                                   \
+  template void launch_table_cast<T>(long long, const double2*, CT<T>::type*, cudaStream_t);       \
+  template void launch_st_apply<T>(const Grid&, int, int, const StencilLayout&, const CT<T>::type*, \
+                                   const CT<T>::type*, const CT<T>::type*, CT<T>::type*, int,       \
+                                   cudaStream_t);                                                   \
+  template void launch_st_vanka<T>(const Grid&, int, int, const StencilLayout&, const CT<T>::type*, \
+                                   T, T, int, const CT<T>::type*, const CT<T>::type*, CT<T>::type*, \
+                                   cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace ehs

@@ -1,0 +1,106 @@
+// Launchers of the device kernels (host side).  All launches are
+// asynchronous on the given stream; items = batch size of the vectors,
+// nrhs = items per coefficient set (item b uses coefficient set b / nrhs).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace ehs {
+
+// ---- fine level (matrix-free) -------------------------------------------
+// cell coefficients from lambda, mu, rho (double, one set per medium, device)
+// and the absorbing layer; gamma = gamma_add + omega*abl_max*max_k(depth_k/L)^2;
+// omegas: device array, one frequency per set
+template <typename T>
+void launch_fine_coef(const Grid& g, int nsets, const double* lam, const double* mu,
+                      const double* rho, const double* omegas, int abl_cells, double abl_max,
+                      double gamma_add, Coef4<T>* out, cudaStream_t s);
+// DD subdomain coefficients: clamped copy of a global coefficient set plus the
+// interface absorbing ramp; origin = global index of local cell 0 (may be
+// negative), om_lo/om_hi = Omega_i in global indices, pad = padding per side.
+template <typename T>
+void launch_sub_coef(const Grid& gl, const Grid& gg, int nsets_glob, int nsub,
+                     const int* d_origin /*[nsub*3]*/, const int* d_omlo, const int* d_omhi,
+                     const int* d_padlo, const int* d_padhi, const int* d_subset /*glob set of sub set*/,
+                     const Coef4<double>* glob, double dd_abl_max, Coef4<T>* out,
+                     cudaStream_t s);
+template <typename T>
+void launch_coef_cast(long long n, const Coef4<double>* in, Coef4<T>* out, cudaStream_t s);
+
+// y = K_s x (mode 0) or y = b - K_s x (mode 1), alpha = shift (0: unshifted)
+template <typename T>
+void launch_fine_apply(const Grid& g, int items, int nrhs, const Coef4<T>* cf, double h,
+                       double alpha, const typename CT<T>::type* x,
+                       const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
+                       cudaStream_t s);
+// one colour of red-black economic cell-wise relaxation: xo = xi + W B^{-1}(b - K_s xi)
+template <typename T>
+void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, double h,
+                       double alpha, T wu, T wp, int colour,
+                       const typename CT<T>::type* b, const typename CT<T>::type* xi,
+                       typename CT<T>::type* xo, cudaStream_t s);
+// level-0 stencil table (double) of K_s for the Galerkin setup
+void fine_table_layout(int d, StencilLayout* L);
+void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double h,
+                       double alpha, const StencilLayout& L, double2* tab, cudaStream_t s);
+
+// ---- stored stencils (Galerkin levels) ----------------------------------
+void coarse_layout(int d, const StencilLayout& fine, StencilLayout* coarse);
+void launch_galerkin(const Grid& gf, const Grid& gc, int nsets, const StencilLayout& Lf,
+                     const double2* tf, const StencilLayout& Lc, double2* tc, int* err,
+                     cudaStream_t s);
+template <typename T>
+void launch_table_cast(long long n, const double2* in, typename CT<T>::type* out, cudaStream_t s);
+template <typename T>
+void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
+                     const typename CT<T>::type* tab, const typename CT<T>::type* x,
+                     const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
+                     cudaStream_t s);
+template <typename T>
+void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
+                     const typename CT<T>::type* tab, T wu, T wp, int colour,
+                     const typename CT<T>::type* b, const typename CT<T>::type* xi,
+                     typename CT<T>::type* xo, cudaStream_t s);
+
+// ---- transfer -------------------------------------------------------------
+template <typename T>
+void launch_restrict(const Grid& gf, const Grid& gc, int items, const typename CT<T>::type* rf,
+                     typename CT<T>::type* rc, cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const Grid& gf, const Grid& gc, int items, const typename CT<T>::type* ec,
+                        typename CT<T>::type* xf, cudaStream_t s);
+
+// ---- coarsest level (dense FP64) ----------------------------------------
+void launch_dense_assemble(const Grid& g, int nsets, const StencilLayout& L, const double2* tab,
+                           double2* A /*[nsets][N][2N]*/, cudaStream_t s);
+void dense_invert(int N, int nsets, double2* M /*[nsets][N][2N] augmented*/, double2* inv /*[nsets][N][N]*/,
+                  double2* fbuf, int* pivbuf, int* err, cudaStream_t s);
+template <typename T>
+void launch_dense_apply(int N, int items, int nrhs, const double2* inv, const typename CT<T>::type* r,
+                        typename CT<T>::type* x, cudaStream_t s);
+
+// ---- Krylov (FP64) --------------------------------------------------------
+void launch_cast_c128_c64(long long n, const double2* in, float2* out, cudaStream_t s);
+void launch_cast_c64_c128(long long n, const float2* in, double2* out, cudaStream_t s);
+void launch_copy(long long nbytes, const void* in, void* out, cudaStream_t s);
+// partial dot products: part[item][i][blk] = sum conj(V_i) w over block blk
+// V: [m+1][items][n] (vector i of item b at V + (i*items + b)*n)
+int krylov_nblk(long long n);
+void launch_mdot(long long n, int items, int nv, const double2* V, const double2* w, double2* part,
+                 int nblk, cudaStream_t s);
+// w -= sum_i V_i h_i; if dot: partial dots of V with the new w; if nrm: partial |w|^2
+void launch_mupdate(long long n, int items, int nv, const double2* V, const double2* h, double2* w,
+                    double2* part, int nblk, int dot, double* nrm_part, cudaStream_t s);
+void launch_reduce_parts(int items, int nv, int nblk, const double2* part, double2* out, int accumulate,
+                         cudaStream_t s);
+void launch_norm_part(long long n, int items, const double2* w, double* part, int nblk, cudaStream_t s);
+void launch_reduce_norm(int items, int nblk, const double* part, double* out, cudaStream_t s);
+// v_out = w / nrm (per item)
+void launch_scale_inv(long long n, int items, const double2* w, const double* nrm, double2* out,
+                      cudaStream_t s);
+// x += sum_{i<k_b} Z_i y_i, Z: [m][items][n] of CZ
+template <typename CZ>
+void launch_xupdate(long long n, int items, int m, const CZ* Z, const double2* y /*[items][m]*/,
+                    const int* kused, double2* x, cudaStream_t s);
+
+}  // namespace ehs

@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/ehs.h; the binding declares the same set."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1806_11277_gb300 import build
+    try:
+        return build.build()
+    except FileNotFoundError:
+        pytest.skip("nvcc not available")
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ehs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ehs_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_path_entry_points():
+    names = _declared()
+    for n in ("ehs_op_apply", "ehs_smooth", "ehs_vcycle", "ehs_dd_precond", "ehs_fgmres_solve",
+              "ehs_adjoint_solve", "ehs_create", "ehs_destroy", "ehs_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (ehs_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_matches_header(lib_path):
+    from paper_1806_11277_gb300 import ehs
+    lib = ehs.load(lib_path)
+    assert sorted(ehs.EXPORTS) == _declared()
+    for n in _declared():
+        assert hasattr(lib, n)
+    o = ehs.default_opts()
+    assert o.levels == 3 and abs(o.alpha - 0.2) < 1e-15 and o.restart == 10
+    assert abs(o.w[0] - 0.75) < 1e-15 and abs(o.w[1] - 0.5) < 1e-15 and abs(o.tol - 1e-6) < 1e-20
+    assert lib.ehs_kernel_launches() >= 0
+
+
+def test_create_rejects_bad_arguments_before_any_launch(lib_path):
+    import ctypes as C
+    from paper_1806_11277_gb300 import ehs
+    lib = ehs.load(lib_path)
+    p = ehs.Problem()
+    p.dim = 4
+    o = ehs.default_opts()
+    ctx = C.c_void_p()
+    st = lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx))
+    assert st == 1 and not ctx.value
+    assert b"dim" in lib.ehs_last_error(None)

@@ -1,0 +1,288 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (relative, 2-norm over all items unless stated):
+* operator apply: 1e-12 in complex128, 1e-5 in complex64;
+* one relaxation sweep / one cycle: 1e-11 in complex128 (a few operator
+  applications deep), 1e-5 in complex64;
+* FGMRES: same iteration count as the oracle with the complex128
+  preconditioner (+-1 with complex64), true residual <= 1e-6 and solution
+  within 1e-5 of the oracle's solution.
+Grids span several multigrid tiles, odd numbers of interior faces and
+absorbing layers; 2D and 3D; batches of media and of right-hand sides.
+"""
+import numpy as np
+import pytest
+
+from oracle import dd as odd, krylov, multigrid as mg, operators as op
+from paper_1806_11277_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ehs():
+    from paper_1806_11277_gb300 import ehs
+    return ehs
+
+
+def _rand_slots(shape, items, seed, dtype=np.complex128):
+    rng = np.random.default_rng(seed)
+    d = len(shape)
+    v = rng.standard_normal((items, d + 1) + shape) + 1j * rng.standard_normal((items, d + 1) + shape)
+    for k in range(d):                           # Dirichlet slots are zero
+        sl = [slice(None)] * (d + 2)
+        sl[0] = slice(None); sl[1] = k; sl[2 + d - 1 - k] = 0
+        v[tuple(sl)] = 0
+    return v.astype(dtype)
+
+
+def _media_2d(n=64, nmed=2):
+    return [synth.random_2d(n=n, sigma=s, seed=i, corr=6.0, abl=8) for i, s in
+            zip(range(nmed), (0.3, 0.49, 0.45, 0.4))]
+
+
+def _media_3d(n=16, nmed=1):
+    return [synth.layered_3d(n=n, seed=i, corr=3.0, abl=3) for i in range(nmed)]
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _oracle_parts(med, alpha=0.0):
+    return op.assemble_mixed(op.parts_for(med), alpha)
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("shifted", [False, True])
+def test_op_apply_fine(case, shifted):
+    ehs = _ehs()
+    meds = _media_2d(48, 2) if case == "2d" else _media_3d(16, 1)
+    S = ehs.solver_for(meds, levels=3, alpha=0.2)
+    shape = meds[0].shape
+    x = _rand_slots(shape, S.items, 1)
+    for prec, dt, tol in ((ehs.EHS_C128, torch.complex128, 1e-12), (ehs.EHS_C64, torch.complex64, 1e-5)):
+        xd = torch.from_numpy(x).to("cuda", dt)
+        yd = torch.zeros_like(xd)
+        S.op_apply(xd, yd, level=0, shifted=shifted)
+        y = yd.cpu().numpy()
+        for b, med in enumerate(meds):
+            K = _oracle_parts(med, 0.2 if shifted else 0.0)
+            xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), shape)
+            ye = op.dofs_to_slots(K @ xe, shape)
+            assert _rel(y[b], ye) <= tol, (prec, b, _rel(y[b], ye))
+    S.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_galerkin_levels_match_oracle(case):
+    ehs = _ehs()
+    meds = _media_2d(64, 2) if case == "2d" else _media_3d(16, 1)
+    levels = 3
+    S = ehs.solver_for(meds, levels=levels, alpha=0.2)
+    for b, med in enumerate(meds):
+        H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels)
+        for l in range(1, levels):
+            shp = S.level_shape(l)
+            x = _rand_slots(tuple(shp[2:]), S.items, 10 + l)
+            for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+                xd = torch.from_numpy(x).to("cuda", dt)
+                yd = torch.zeros_like(xd)
+                S.op_apply(xd, yd, level=l)
+                xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), tuple(shp[2:]))
+                ye = op.dofs_to_slots(H.K[l] @ xe, tuple(shp[2:]))
+                assert _rel(yd[b].cpu().numpy(), ye) <= tol, (l, dt, _rel(yd[b].cpu().numpy(), ye))
+    S.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_smooth_matches_oracle(case):
+    ehs = _ehs()
+    meds = _media_2d(32, 2) if case == "2d" else _media_3d(16, 1)
+    levels = 3
+    S = ehs.solver_for(meds, levels=levels, alpha=0.2)
+    for l in range(levels - 1):
+        shp = S.level_shape(l)
+        gshape = tuple(shp[2:])
+        b_ = _rand_slots(gshape, S.items, 20 + l)
+        x_ = _rand_slots(gshape, S.items, 30 + l)
+        for dt, tol in ((torch.complex128, 1e-11), (torch.complex64, 2e-5)):
+            bd = torch.from_numpy(b_).to("cuda", dt)
+            xd = torch.from_numpy(x_).to("cuda", dt)
+            S.smooth(bd, xd, level=l, nsweeps=1)
+            for it, med in enumerate(meds):
+                H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels)
+                be = op.slots_to_dofs(bd[it].cpu().numpy().astype(np.complex128), gshape)
+                xe = op.slots_to_dofs(torch.from_numpy(x_[it]).to(dt).numpy().astype(np.complex128), gshape)
+                xr = op.dofs_to_slots(H.relax(l, be, xe), gshape)
+                got = xd[it].cpu().numpy()
+                assert _rel(got, xr) <= tol, (l, dt, it, _rel(got, xr))
+    S.close()
+
+
+@pytest.mark.parametrize("case,levels", [("2d", 3), ("2d", 4), ("3d", 3)])
+def test_vcycle_matches_oracle(case, levels):
+    ehs = _ehs()
+    meds = _media_2d(64, 2) if case == "2d" else _media_3d(16, 1)
+    S = ehs.solver_for(meds, levels=levels, alpha=0.2)
+    shape = meds[0].shape
+    b_ = _rand_slots(shape, S.items, 5)
+    for dt, tol in ((torch.complex128, 1e-10), (torch.complex64, 5e-5)):
+        bd = torch.from_numpy(b_).to("cuda", dt)
+        xd = torch.zeros_like(bd)
+        S.vcycle(bd, xd)
+        for it, med in enumerate(meds):
+            H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels,
+                             w=[0.75, 0.5, 0.25, 0.25, 0.25][:levels - 1])
+            xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape)), shape)
+            assert _rel(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _rel(xd[it].cpu().numpy(), xr))
+    S.close()
+
+
+def _solve_both(meds, levels, prec, nrhs=1, host=False, **kw):
+    ehs = _ehs()
+    S = ehs.solver_for(meds, levels=levels, prec=prec, nrhs=nrhs, **kw)
+    shape = meds[0].shape
+    qs = []
+    for med in meds:
+        srcs = med.sources * nrhs if len(med.sources) < nrhs else med.sources[:nrhs]
+        for r in range(nrhs):
+            k, idx = srcs[r]
+            idx = tuple(i + r for i in idx)
+            qs.append(synth.point_rhs(shape, [(k, idx)])[0])
+    q = np.stack(qs)
+    if host:
+        u = np.zeros_like(q)
+        info = S.fgmres_solve(q, u)
+    else:
+        qd = torch.from_numpy(q).cuda()
+        ud = torch.zeros_like(qd)
+        info = S.fgmres_solve(qd, ud)
+        u = ud.cpu().numpy()
+    S.close()
+    return q, u, info
+
+
+@pytest.mark.parametrize("prec_name", ["c128", "c64"])
+def test_fgmres_matches_oracle_2d(prec_name):
+    ehs = _ehs()
+    prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
+    meds = _media_2d(64, 4)
+    q, u, info = _solve_both(meds, 3, prec)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, 3)
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        res = np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo)
+        assert info[it]["converged"] and res <= 1e-6
+        if prec == ehs.EHS_C128:
+            assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
+        else:
+            assert abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_fgmres_config1_host_buffers():
+    """64 x 64 homogeneous Vp=2, Vs=1, 3 levels, alpha 0.2, FGMRES(10); host q/u."""
+    ehs = _ehs()
+    med = synth.homogeneous_2d()
+    q, u, info = _solve_both([med], 3, ehs.EHS_C128, host=True)
+    K = _oracle_parts(med)
+    H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, 3)
+    qo = op.slots_to_dofs(q[0], med.shape)
+    xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+    import scipy.sparse.linalg as spla
+    xe = spla.spsolve(K.tocsc(), qo)
+    ug = op.slots_to_dofs(u[0], med.shape)
+    assert info[0]["iters"] == io["iters"]
+    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+    assert np.linalg.norm(ug - xe) / np.linalg.norm(xe) <= 1e-5
+
+
+def test_fgmres_multi_rhs_3d():
+    ehs = _ehs()
+    meds = _media_3d(16, 1)
+    q, u, info = _solve_both(meds, 3, ehs.EHS_C64, nrhs=2)
+    K = _oracle_parts(meds[0])
+    for it in range(2):
+        qo = op.slots_to_dofs(q[it], meds[0].shape)
+        ug = op.slots_to_dofs(u[it], meds[0].shape)
+        assert np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo) <= 1e-6
+        assert info[it]["converged"]
+
+
+def test_adjoint_solve():
+    ehs = _ehs()
+    med = _media_2d(32, 1)[0]
+    S = ehs.solver_for(med, levels=3, prec=ehs.EHS_C64)
+    g = _rand_slots(med.shape, 1, 7)
+    gd = torch.from_numpy(g).cuda()
+    wd = torch.zeros_like(gd)
+    info = S.adjoint_solve(gd, wd)[0]
+    K = _oracle_parts(med)
+    go = op.slots_to_dofs(g[0], med.shape)
+    wo = op.slots_to_dofs(wd[0].cpu().numpy(), med.shape)
+    assert info["converged"]
+    assert np.linalg.norm(K.conj().T @ wo - go) / np.linalg.norm(go) <= 1e-6
+    S.close()
+
+
+@pytest.mark.parametrize("prec_name", ["c128", "c64"])
+def test_dd_precond_matches_oracle(prec_name):
+    ehs = _ehs()
+    prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
+    tol = 1e-10 if prec == ehs.EHS_C128 else 5e-5
+    med = synth.random_2d(n=64, sigma=0.4, seed=2, corr=6.0, abl=8)
+    S = ehs.solver_for(med, levels=3, precond=ehs.EHS_PRECOND_DD, dd=(2, 2, 1), dd_overlap=4,
+                       dd_pad=8, prec=prec)
+    D = odd.DD(med, (2, 2), 4, 8, 3, 0.2)
+    r = _rand_slots(med.shape, 1, 9)
+    rd = torch.from_numpy(r).cuda()
+    zd = torch.zeros_like(rd)
+    S.dd_precond(rd, zd, prec=prec)
+    zo = op.dofs_to_slots(D.apply(op.slots_to_dofs(r[0], med.shape)), med.shape)
+    assert _rel(zd[0].cpu().numpy(), zo) <= tol
+    S.close()
+
+
+def test_dd_fgmres_iterations_match_oracle():
+    ehs = _ehs()
+    med = synth.homogeneous_2d()
+    q, u, info = _solve_both([med], 3, ehs.EHS_C128, precond=ehs.EHS_PRECOND_DD, dd=(2, 2, 1),
+                             dd_overlap=4, dd_pad=8)
+    D = odd.DD(med, (2, 2), 4, 8, 3, 0.2)
+    qo = op.slots_to_dofs(q[0], med.shape)
+    xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
+    ug = op.slots_to_dofs(u[0], med.shape)
+    assert info[0]["iters"] == io["iters"]
+    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_invalid_arguments_rejected():
+    ehs = _ehs()
+    med = synth.homogeneous_2d(n=36)
+    with pytest.raises(ehs.EhsError, match="ERR_ARG"):
+        ehs.solver_for(med, levels=4)              # 36 not divisible by 8
+    bad = synth.homogeneous_2d(n=32)
+    bad.rho[3, 3] = -1.0
+    with pytest.raises(ehs.EhsError, match="ERR_ARG"):
+        ehs.solver_for(bad, levels=3)
+    bad = synth.homogeneous_2d(n=32)
+    bad.lam[1, 1] = np.nan
+    with pytest.raises(ehs.EhsError, match="ERR_ARG"):
+        ehs.solver_for(bad, levels=3)
+
+
+def test_noconv_reports_best_iterate():
+    ehs = _ehs()
+    med = synth.homogeneous_2d()
+    S = ehs.solver_for(med, levels=3, maxit=3)
+    q = synth.point_rhs(med.shape, med.sources)[0][None]
+    qd = torch.from_numpy(q).cuda()
+    ud = torch.zeros_like(qd)
+    info = S.fgmres_solve(qd, ud, raise_noconv=False)[0]
+    assert info["iters"] == 3 and not info["converged"]
+    assert 0 < info["relres"] < 1
+    S.close()
