@@ -1,0 +1,351 @@
+"""Benchmark: elastic Helmholtz solves/s to a 1e-6 residual on GB300.
+
+Workload (one step): four 512 x 512 heterogeneous media (smooth Gaussian
+random fields, correlation 20 cells, Vp in [1.5, 4.5], rho in [1, 2.5]) with
+Poisson ratios 0.25 / 0.4 / 0.45 / 0.49, 8 points per shortest S-wavelength,
+20-cell absorbing layer, one x-force each; a complex64 multigrid V-cycle
+preconditions an FP64 FGMRES(10) to 1e-6 relative residual.  The four media
+are one batched context, so one step is four solves.
+
+Timing: W warm-up steps, then K steps timed with CUDA events on the solver's
+stream, L2 flushed (a 512 MiB write) between steps outside the events;
+barrier + synchronize around the timed loop; max over ranks.  N > 1 ranks
+run independent replicas (weak scaling, no collective on the data path).
+
+Also reported: e2e (the same solves through the C ABI with host buffers,
+copies inside the timed region), the roofline of the dominant kernel timed
+live with CUDA events, SM clocks sampled during the timed region, and the
+CPU oracle timed on a bounded sample (``--impl reference`` times the oracle
+alone on this workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elastic Helmholtz solves/s to 1e-6 residual; stencil HBM GB/s vs peak"
+SIGMAS = (0.25, 0.4, 0.45, 0.49)
+N_GRID = 512
+LEVELS = 5
+ALPHA = 0.4
+W_LEVELS = (0.75, 0.5, 0.25, 0.25)
+WORKLOAD = ("2D heterogeneous media 512x512 (GRF corr 20, Vp 1.5-4.5, rho 1-2.5), Poisson "
+            "0.25/0.4/0.45/0.49, 8 points per S-wavelength, 20-cell ABL; complex64 V-cycle "
+            f"({LEVELS} levels, alpha {ALPHA}) inside FP64 FGMRES(10) to 1e-6")
+VANKA_BYTES_PER_CELL_C64 = 84     # read x 24 + read b 20 + coefficients 16 + write x 24
+
+
+def media(seed=0):
+    from paper_1806_11277_gb300 import synth
+    return [synth.random_2d(n=N_GRID, sigma=s, seed=seed) for s in SIGMAS]
+
+
+def rhs(meds):
+    from paper_1806_11277_gb300 import synth
+    return np.stack([synth.point_rhs(m.shape, m.sources)[0] for m in meds])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 3 + i and r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- oracle leg
+def oracle_sample(meds, iters_per_sample, which=0):
+    """Oracle (as it stands) FGMRES iterations on one medium; seconds per iteration."""
+    from oracle import krylov, multigrid as mg, operators as op
+    med = meds[which % len(meds)]
+    parts = op.parts_for(med)
+    K = op.assemble_mixed(parts)
+    H = mg.Hierarchy(op.assemble_mixed(parts, ALPHA), med.shape, LEVELS, w=list(W_LEVELS))
+    q = op.slots_to_dofs(rhs([med])[0], med.shape)
+    t = time.perf_counter()
+    _, info = krylov.fgmres(lambda v: K @ v, H.cycle, q, m=10, maxit=iters_per_sample, tol=1e-30)
+    dt = time.perf_counter() - t
+    return dt / max(1, info["iters"]), info["iters"]
+
+
+def oracle_iteration_counts():
+    p = os.path.join(ROOT, "tests", "golden", "c2_oracle_iters.json")
+    try:
+        with open(p) as f:
+            return json.load(f)["iters"]
+    except Exception:
+        return None
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        nt = [i.get("num_threads", 1) for i in threadpool_info()]
+        return max(nt) if nt else 1
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on this workload, per step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    meds = media()
+    iters = oracle_iteration_counts()
+    per = []
+    for s in range(args.warmup + args.steps):
+        t_it, n_it = oracle_sample(meds, args.ref_iters, which=s)
+        if s >= args.warmup:
+            per.append((s % len(meds), t_it))
+    mean_iters = float(np.mean(iters)) if iters else None
+    t_iter = float(np.mean([t for _, t in per]))
+    value = 1.0 / (t_iter * mean_iters) if mean_iters else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_iter * args.ref_iters * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "media": len(SIGMAS)},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": (f"{args.ref_iters} oracle FGMRES iterations per step on one medium "
+                                    f"(media cycled), seconds/iteration x the oracle's own mean iteration "
+                                    f"count per solve ({mean_iters}) from tests/golden/c2_oracle_iters.json")},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU leg
+def run_gpu(args):
+    import torch
+    from paper_1806_11277_gb300 import ehs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    meds = media()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        S = ehs.solver_for(meds, levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=ehs.EHS_C64,
+                           stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    q_host = rhs(meds)
+    qd = torch.from_numpy(q_host).to(dev)
+    ud = torch.zeros_like(qd)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        return S.fgmres_solve(qd, ud)
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    if args.profile_step:                 # one solve step between profiler start/stop
+        torch.cuda.cudart().cudaProfilerStart()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        S.close()
+        return 0
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    l0 = ehs.kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    launches = ehs.kernel_launches() - l0
+    clk = clocks.stop()
+    total = sum(times)
+    if dist:
+        t = torch.tensor([total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+        dist.barrier()
+    solves = len(SIGMAS) * args.steps * world
+    value = solves / total
+    its = [i["iters"] for i in info]
+    relres = [i["relres"] for i in info]
+
+    # e2e: same solves through the C ABI with host buffers (copies inside)
+    q_pin = torch.from_numpy(q_host).pin_memory().numpy()
+    u_pin = torch.zeros(q_host.shape, dtype=torch.complex128).pin_memory().numpy()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        S.fgmres_solve(q_pin, u_pin)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_val = len(SIGMAS) * world / (sum(e2e_t) / len(e2e_t))
+
+    # roofline of the fine-level Vanka half-sweep (dominant V-cycle kernel),
+    # one launch per sample, L2 flushed before each, events on the same stream
+    ncell = N_GRID * N_GRID * len(SIGMAS)
+    bd = torch.randn(qd.shape, dtype=torch.complex64, device=dev)
+    bd[:, 0, :, 0] = 0          # Dirichlet slots: u_x at i_x = 0, u_y at i_y = 0
+    bd[:, 1, 0, :] = 0
+    xd = torch.zeros_like(bd)
+    kt = []
+    for r in range(args.kernel_reps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            S.smooth(bd, xd, level=0, nsweeps=1)       # two Vanka launches (red, black)
+            e1.record(stream)
+        e1.synchronize()
+        kt.append(e0.elapsed_time(e1) / 1e3 / 2)
+    t_launch = statistics.median(kt)
+    peak, peak_kind = peaks()
+    alg = VANKA_BYTES_PER_CELL_C64 * ncell
+    achieved = alg / t_launch / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "media": len(SIGMAS),
+                   "sigmas": list(SIGMAS), "levels": LEVELS, "alpha": ALPHA, "cycle": "V(1,1)",
+                   "krylov": "FGMRES(10) FP64", "precond_dtype": "complex64",
+                   "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+        "iters": its, "relres": relres, "setup_s": setup_s,
+        "gridpoints_x_iters_per_s": float(N_GRID * N_GRID * sum(its) * args.steps * world / total),
+        "e2e": {"value": e2e_val, "unit": "solves/s",
+                "h2d_bytes_per_step": int(q_host.nbytes), "d2h_bytes_per_step": int(q_host.nbytes)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "k_fine_vanka<float,2> (one colour)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "traffic": args.traffic, "alg_bytes_per_launch": alg,
+                     "launch_us": t_launch * 1e6},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        iters_o = oracle_iteration_counts()
+        t_it = []
+        for s in range(len(SIGMAS)):
+            ti, _ = oracle_sample(meds, args.cpu_iters, which=s)
+            t_it.append(ti)
+        mean_iters = float(np.mean(iters_o)) if iters_o else float(np.mean(its))
+        src = "tests/golden/c2_oracle_iters.json" if iters_o else "this run's GPU counts"
+        cpu_val = 1.0 / (float(np.mean(t_it)) * mean_iters)
+        line["cpu_baseline"] = {
+            "value": cpu_val, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": (f"{args.cpu_iters} oracle FGMRES iterations on each of the 4 media; "
+                       f"seconds/iteration x mean iterations per solve ({mean_iters:.1f}, {src})")}
+    S.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ehs", choices=["ehs", "reference"])
+    ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--cpu-iters", type=int, default=4)
+    ap.add_argument("--ref-iters", type=int, default=4)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run warm-up, then one step between cudaProfilerStart/Stop and exit")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
