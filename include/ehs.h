@@ -148,6 +148,33 @@ ehs_status ehs_fgmres_solve(ehs_ctx* ctx, const void* q, void* u, ehs_solve_info
  * used.  Same argument conventions as ehs_fgmres_solve. */
 ehs_status ehs_adjoint_solve(ehs_ctx* ctx, const void* g, void* w, ehs_solve_info* info);
 
+/* Allocation-free fine-level smoothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they need it -- code inside a CUDA stream capture (cudaMalloc cannot be
+ * captured), host callbacks, or runtimes whose memory pool forbids extra
+ * device allocations -- and therefore cannot build a context with
+ * ehs_create.  It performs nsweeps red-black economic cell-wise relaxation
+ * sweeps of the shifted fine operator K_s (the same kernels and result as
+ * ehs_smooth on level 0 of a context built from the same problem) without any
+ * cudaMalloc / cudaFree or allocating library call.
+ *   prob: as for ehs_create, but lambda, mu, rho must be DEVICE pointers and
+ *     nmedia <= 32; every n[k] even.  nrhs: items per medium; items =
+ *     nmedia * nrhs.  alpha: shift; w, wp: damping of the u and p unknowns.
+ *   prec: EHS_C64 or EHS_C128; b, x: device vectors of that precision in the
+ *     slot layout (x is relaxed in place).  stream: a cudaStream_t or NULL.
+ * Scratch: the cell coefficients and the ping-pong vector live in one static
+ *   32 MiB device array per GPU, held from library load until process exit;
+ *   problems needing more return EHS_ERR_OOM.  Every call shares that array
+ *   (each call clears and rewrites what it uses), so calls whose GPU work can
+ *   overlap -- other streams or host threads -- race and must be serialised
+ *   by the caller.  The first call on each device looks up the array's device
+ *   address; make that first call before any stream capture begins.
+ * Returns EHS_ERR_ARG for invalid arguments or host pointers, EHS_ERR_OOM for
+ *   a problem larger than the scratch, EHS_ERR_CUDA if a launch fails. */
+ehs_status ehs_fine_smooth_noalloc(const ehs_problem* prob, int nrhs, double alpha, double w,
+                                   double wp, int nsweeps, int prec, const void* b, void* x,
+                                   void* stream);
+
 /* Sizes: items of a vector batch, complex values per item at level l. */
 int ehs_items(const ehs_ctx* ctx);
 long long ehs_level_len(const ehs_ctx* ctx, int level);

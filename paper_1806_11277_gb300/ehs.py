@@ -43,7 +43,8 @@ class SolveInfo(C.Structure):
 
 EXPORTS = ["ehs_default_opts", "ehs_create", "ehs_destroy", "ehs_op_apply", "ehs_smooth",
            "ehs_vcycle", "ehs_dd_precond", "ehs_fgmres_solve", "ehs_adjoint_solve", "ehs_items",
-           "ehs_level_len", "ehs_level_dims", "ehs_sync", "ehs_kernel_launches", "ehs_last_error"]
+           "ehs_level_len", "ehs_level_dims", "ehs_sync", "ehs_kernel_launches", "ehs_last_error",
+           "ehs_fine_smooth_noalloc"]
 
 _lib = None
 
@@ -77,6 +78,7 @@ def load(path=LIB_PATH):
     lib.ehs_kernel_launches.restype = C.c_longlong
     lib.ehs_last_error.argtypes = [vp]
     lib.ehs_last_error.restype = C.c_char_p
+    lib.ehs_fine_smooth_noalloc.argtypes = [C.POINTER(Problem), i, d, d, d, i, i, vp, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)
     _lib = lib
