@@ -4,6 +4,7 @@
 // directory; the host only sequences launches and runs the (m+1) x m
 // Hessenberg least-squares update of FGMRES.
 #include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -49,6 +50,7 @@ struct Level {
   double2* tab64 = nullptr;   // Galerkin levels and coarsest: [nsets][nslot][ncell]
   float2* tab32 = nullptr;
   double2* inv = nullptr;     // coarsest: [nsets][N][N]
+  float4* invdf = nullptr;    // coarsest inverse in complex df64 (used by the complex64 cycle)
   void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
   double w = 0.5;
 };
@@ -61,6 +63,7 @@ struct Hier {
   int nu1 = 1, nu2 = 1, cyc = 1;
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
+  void* cfdf = nullptr;        // df64 coefficients (outer-Krylov operator of the global problem)
   std::vector<Level> lv;
 };
 
@@ -89,10 +92,21 @@ struct ehs_ctx {
   double *npart = nullptr, *nrm = nullptr;
   int* kused = nullptr;
   float2 *f_in = nullptr, *f_out = nullptr;
+  // df64 Krylov workspace (complex64 preconditioner form)
+  float4 *Vq = nullptr, *wq = nullptr, *rq = nullptr, *qq = nullptr, *xq = nullptr, *partq = nullptr;
+  float4 *hq = nullptr, *h2q = nullptr, *yq = nullptr;
+  float2 *Zf = nullptr, *npq = nullptr, *invq = nullptr;
+  double2* hhost = nullptr;   // device double copies of h for the host
   double2* dd_x = nullptr;   // DD accumulated correction (c128 or c64 view)
   double2* dd_r = nullptr;
   int nblk = 1;
   double* hpin = nullptr;    // pinned host scratch
+  // CUDA graphs of the preconditioner application, one per Krylov direction j
+  // (the input/output pointers differ per j), captured on a private stream
+  bool use_graphs = true;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaGraphExec_t> pg;
+  std::vector<long long> pg_nodes;
   std::string err;
 };
 
@@ -154,9 +168,7 @@ void build_hier(ehs_ctx* c, Hier& H) {
     coarse_layout(d, Lf, &L.L);
     L.tab64 = dalloc<double2>(c, (size_t)H.nsets * L.L.nslot * L.g.ncell);
     launch_galerkin(H.lv[l - 1].g, L.g, H.nsets, Lf, tf, L.L, L.tab64, derr, c->s); cnt(); post();
-    if (l > 1 || tf != nullptr) {
-      if (l == 1) dfree(c, tf);
-    }
+    if (l == 1) dfree(c, tf);   // the level-0 table is only needed for the first product
     const long long nt = (long long)H.nsets * L.L.nslot * L.g.ncell;
     L.tab32 = dalloc<float2>(c, nt);
     launch_table_cast<float>(nt, L.tab64, L.tab32, c->s); cnt(); post();
@@ -173,6 +185,8 @@ void build_hier(ehs_ctx* c, Hier& H) {
   launch_dense_assemble(C.g, H.nsets, C.L, C.tab64, M, c->s); cnt(); post();
   C.inv = dalloc<double2>(c, (size_t)H.nsets * N * N);
   dense_invert((int)N, H.nsets, M, C.inv, fb, pv, derr, c->s); cnt(4 * N + 1); post();
+  C.invdf = dalloc<float4>(c, (size_t)H.nsets * N * N);
+  launch_d2_to_df((long long)H.nsets * N * N, C.inv, C.invdf, c->s); cnt(); post();
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
@@ -213,8 +227,11 @@ void level_sweep(ehs_ctx* c, const Hier& H, int l, const typename CT<T>::type* b
     launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 0, b, x, t, c->s);
     launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 1, b, t, x, c->s);
   } else {
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 0, b, x, t, c->s);
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 1, b, t, x, c->s);
+    typedef typename CT<T>::type C;
+    C* rb = (C*)L.ws[PT<T>::i][3];
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 0, b, x, t, rb, c->s);
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 1, b, t, x, rb, c->s);
+    cnt(2);
   }
   cnt(2); post();
 }
@@ -227,7 +244,11 @@ void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typena
   const int p = PT<T>::i;
   const long long nv = (long long)H.items * (L.g.d + 1) * L.g.ncell;
   if (l == H.nlev - 1) {
-    launch_dense_apply<T>((int)((L.g.d + 1) * L.g.ncell), H.items, H.nrhs, L.inv, b, x, c->s);
+    const int N = (int)((L.g.d + 1) * L.g.ncell);
+    if (p == 1)   // complex64 cycle: FP64-class (df64) inverse on the FP32 pipe
+      launch_dense_apply_df(N, H.items, H.nrhs, L.invdf, (const float2*)b, (float2*)x, c->s);
+    else
+      launch_dense_apply<T>(N, H.items, H.nrhs, L.inv, b, x, c->s);
     cnt(); post();
     return;
   }
@@ -297,8 +318,6 @@ void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* 
 // ------------------------------------------------------------------ FGMRES
 namespace {
 
-void precond_apply(ehs_ctx* c, const double2* v, double2* z);
-
 void givens(zc a, zc b, double* cs, zc* sn, zc* r) {
   if (b == 0.0) { *cs = 1; *sn = 0; *r = a; return; }
   if (a == 0.0) { *cs = 0; *sn = std::conj(b) / std::abs(b); *r = std::abs(b); return; }
@@ -308,94 +327,82 @@ void givens(zc a, zc b, double* cs, zc* sn, zc* r) {
   *r = (a / t) * nr;
 }
 
-ehs_status fgmres(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info) {
-  const int items = c->H.items, m = c->opt.restart;
-  const long long n = c->n0;
-  const int nblk = c->nblk;
-  cudaStream_t s = c->s;
-  // ||q||
-  launch_norm_part(n, items, q, c->npart, nblk, s);
-  launch_reduce_norm(items, nblk, c->npart, c->nrm, s); cnt(2); post();
-  std::vector<double> bnorm(items), beta(items);
-  CK(cudaMemcpyAsync(c->hpin, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  for (int b = 0; b < items; ++b) bnorm[b] = beta[b] = c->hpin[b];
-  CK(cudaMemsetAsync(u, 0, (size_t)items * n * sizeof(double2), s));
-  CK(cudaMemcpyAsync(c->rd, q, (size_t)items * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  std::vector<int> iters(items, 0), done(items, 0);
-  for (int b = 0; b < items; ++b) done[b] = !(bnorm[b] > 0) || (beta[b] / bnorm[b] <= c->opt.tol);
-  std::vector<zc> H((size_t)items * (m + 1) * m), g((size_t)items * (m + 1)), sn((size_t)items * m);
-  std::vector<double> cs((size_t)items * m);
-  std::vector<int> kused(items), active(items);
-  std::vector<double2> yh((size_t)items * m);
-  std::vector<double2> hh((size_t)items * (m + 1));
+// Host side of FGMRES(m) for every item: Hessenberg columns, complex Givens
+// rotations, residual estimates, per-item convergence and iteration counts.
+// The (m+1) x m least-squares problem is tiny; everything of length n runs in
+// the kernels.
+struct Arnoldi {
+  int items, m, maxit;
+  double tol;
+  std::vector<zc> H, g, sn;
+  std::vector<double> cs, bnorm, beta;
+  std::vector<int> iters, done, kused, active;
   bool breakdown = false, nonfinite = false;
-  auto all_done = [&]() { for (int b = 0; b < items; ++b) if (!done[b]) return false; return true; };
-  while (!all_done()) {
-    bool maxed = true;
-    for (int b = 0; b < items; ++b) if (!done[b] && iters[b] < c->opt.maxit) maxed = false;
-    if (maxed) break;
-    // V_0 = r / beta
-    CK(cudaMemcpyAsync(c->nrm, beta.data(), items * sizeof(double), cudaMemcpyHostToDevice, s));
-    launch_scale_inv(n, items, c->rd, c->nrm, c->V, s); cnt(); post();
+
+  Arnoldi(int items_, int m_, int maxit_, double tol_)
+      : items(items_), m(m_), maxit(maxit_), tol(tol_), H((size_t)items_ * (m_ + 1) * m_),
+        g((size_t)items_ * (m_ + 1)), sn((size_t)items_ * m_), cs((size_t)items_ * m_),
+        bnorm(items_), beta(items_), iters(items_, 0), done(items_, 0), kused(items_, 0),
+        active(items_, 0) {}
+
+  void set_b(const double* nrm) {
+    for (int b = 0; b < items; ++b) {
+      bnorm[b] = beta[b] = nrm[b];
+      done[b] = !(bnorm[b] > 0);
+    }
+  }
+  bool all_done() const {
+    for (int b = 0; b < items; ++b) if (!done[b]) return false;
+    return true;
+  }
+  bool maxed() const {
+    for (int b = 0; b < items; ++b) if (!done[b] && iters[b] < maxit) return false;
+    return true;
+  }
+  void start_cycle() {
     std::fill(H.begin(), H.end(), zc(0));
     std::fill(g.begin(), g.end(), zc(0));
     for (int b = 0; b < items; ++b) {
       g[(size_t)b * (m + 1)] = beta[b];
       kused[b] = 0;
-      active[b] = !done[b] && iters[b] < c->opt.maxit;
+      active[b] = !done[b] && iters[b] < maxit;
     }
-    for (int j = 0; j < m; ++j) {
-      double2* Vj = c->V + (size_t)j * items * n;
-      double2* Zj = c->Z + (size_t)j * items * n;
-      precond_apply(c, Vj, Zj);
-      launch_fine_apply<double>(c->H.g0, items, c->H.nrhs, c->H.cf64, c->H.h, 0.0, Zj,
-                                nullptr, c->w, 0, s);
-      cnt(); post();
-      const int nv = j + 1;
-      launch_mdot(n, items, nv, c->V, c->w, c->part, nblk, s);
-      launch_reduce_parts(items, nv, nblk, c->part, c->hd, 0, s);
-      launch_mupdate(n, items, nv, c->V, c->hd, c->w, c->part, nblk, 1, nullptr, s);
-      launch_reduce_parts(items, nv, nblk, c->part, c->y, 0, s);   // h2 into y scratch
-      launch_mupdate(n, items, nv, c->V, c->y, c->w, nullptr, nblk, 0, c->npart, s);
-      launch_reduce_norm(items, nblk, c->npart, c->nrm, s);
-      cnt(6); post();
-      CK(cudaMemcpyAsync(hh.data(), c->hd, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(yh.data(), c->y, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(c->hpin, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      bool any_active = false;
-      for (int b = 0; b < items; ++b) {
-        if (!active[b]) continue;
-        zc* Hb = &H[(size_t)b * (m + 1) * m];
-        zc* gb = &g[(size_t)b * (m + 1)];
-        for (int i = 0; i < nv; ++i)
-          Hb[i * m + j] = zc(hh[b * nv + i].x + yh[b * nv + i].x, hh[b * nv + i].y + yh[b * nv + i].y);
-        const double hn = c->hpin[b];
-        Hb[(j + 1) * m + j] = hn;
-        for (int i = 0; i < j; ++i) {
-          const zc t = cs[b * m + i] * Hb[i * m + j] + sn[b * m + i] * Hb[(i + 1) * m + j];
-          Hb[(i + 1) * m + j] = -std::conj(sn[b * m + i]) * Hb[i * m + j] + cs[b * m + i] * Hb[(i + 1) * m + j];
-          Hb[i * m + j] = t;
-        }
-        zc rr;
-        givens(Hb[j * m + j], Hb[(j + 1) * m + j], &cs[b * m + j], &sn[b * m + j], &rr);
-        Hb[j * m + j] = rr;
-        Hb[(j + 1) * m + j] = 0.0;
-        gb[j + 1] = -std::conj(sn[b * m + j]) * gb[j];
-        gb[j] = cs[b * m + j] * gb[j];
-        iters[b] += 1;
-        kused[b] = j + 1;
-        const double res = std::abs(gb[j + 1]) / bnorm[b];
-        if (!std::isfinite(res)) { nonfinite = true; active[b] = 0; continue; }
-        if (hn == 0.0) { active[b] = 0; if (res > c->opt.tol) breakdown = true; continue; }
-        if (res <= c->opt.tol || iters[b] >= c->opt.maxit) { active[b] = 0; continue; }
-        any_active = true;
+  }
+  // column j of H from h = h1 + h2 ([items][j+1]) and hn; true if an item is still active
+  bool step(int j, const double2* h1, const double2* h2, const double* hn) {
+    const int nv = j + 1;
+    bool any = false;
+    for (int b = 0; b < items; ++b) {
+      if (!active[b]) continue;
+      zc* Hb = &H[(size_t)b * (m + 1) * m];
+      zc* gb = &g[(size_t)b * (m + 1)];
+      for (int i = 0; i < nv; ++i)
+        Hb[i * m + j] = zc(h1[b * nv + i].x + h2[b * nv + i].x, h1[b * nv + i].y + h2[b * nv + i].y);
+      Hb[(j + 1) * m + j] = hn[b];
+      for (int i = 0; i < j; ++i) {
+        const zc t = cs[b * m + i] * Hb[i * m + j] + sn[b * m + i] * Hb[(i + 1) * m + j];
+        Hb[(i + 1) * m + j] = -std::conj(sn[b * m + i]) * Hb[i * m + j] + cs[b * m + i] * Hb[(i + 1) * m + j];
+        Hb[i * m + j] = t;
       }
-      if (!any_active) break;
-      launch_scale_inv(n, items, c->w, c->nrm, c->V + (size_t)(j + 1) * items * n, s); cnt(); post();
+      zc rr;
+      givens(Hb[j * m + j], Hb[(j + 1) * m + j], &cs[b * m + j], &sn[b * m + j], &rr);
+      Hb[j * m + j] = rr;
+      Hb[(j + 1) * m + j] = 0.0;
+      gb[j + 1] = -std::conj(sn[b * m + j]) * gb[j];
+      gb[j] = cs[b * m + j] * gb[j];
+      iters[b] += 1;
+      kused[b] = j + 1;
+      const double res = std::abs(gb[j + 1]) / bnorm[b];
+      if (!std::isfinite(res)) { nonfinite = true; active[b] = 0; continue; }
+      if (hn[b] == 0.0) { active[b] = 0; if (res > tol) breakdown = true; continue; }
+      if (res <= tol || iters[b] >= maxit) { active[b] = 0; continue; }
+      any = true;
     }
-    // y = R^{-1} g (back substitution) and x += Z y
+    return any;
+  }
+  // y = R^{-1} g per item, [items][m] (zero beyond kused)
+  void solve_y(std::vector<double2>& y) const {
+    y.assign((size_t)items * m, make_double2(0, 0));
     for (int b = 0; b < items; ++b) {
       const int k = kused[b];
       const zc* Hb = &H[(size_t)b * (m + 1) * m];
@@ -406,52 +413,185 @@ ehs_status fgmres(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info
         for (int l = i + 1; l < k; ++l) acc -= Hb[i * m + l] * yv[l];
         yv[i] = acc / Hb[i * m + i];
       }
-      for (int i = 0; i < m; ++i) yh[(size_t)b * m + i] = i < k ? make_double2(yv[i].real(), yv[i].imag()) : make_double2(0, 0);
+      for (int i = 0; i < k; ++i) y[(size_t)b * m + i] = make_double2(yv[i].real(), yv[i].imag());
     }
-    CK(cudaMemcpyAsync(c->y, yh.data(), (size_t)items * m * sizeof(double2), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c->kused, kused.data(), items * sizeof(int), cudaMemcpyHostToDevice, s));
-    launch_xupdate<double2>(n, items, m, c->Z, c->y, c->kused, u, s); cnt(); post();
-    // true residual in FP64
-    launch_fine_apply<double>(c->H.g0, items, c->H.nrhs, c->H.cf64, c->H.h, 0.0, u, q,
-                              c->rd, 1, s);
-    launch_norm_part(n, items, c->rd, c->npart, nblk, s);
-    launch_reduce_norm(items, nblk, c->npart, c->nrm, s); cnt(3); post();
-    CK(cudaMemcpyAsync(c->hpin, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+  }
+  void end_cycle(const double* rnorm) {
     for (int b = 0; b < items; ++b) {
-      beta[b] = c->hpin[b];
+      beta[b] = rnorm[b];
       if (!std::isfinite(beta[b])) { nonfinite = true; done[b] = 1; }
-      if (!done[b] && beta[b] / bnorm[b] <= c->opt.tol) done[b] = 1;
+      if (!done[b] && beta[b] / bnorm[b] <= tol) done[b] = 1;
     }
-    if (nonfinite) break;
-    if (breakdown) break;
   }
-  bool allconv = true;
-  for (int b = 0; b < items; ++b) {
-    const double rel = bnorm[b] > 0 ? beta[b] / bnorm[b] : 0.0;
-    const int conv = rel <= c->opt.tol;
-    allconv = allconv && conv;
-    if (info) { info[b].iters = iters[b]; info[b].relres = rel; info[b].converged = conv; }
+  ehs_status finish(ehs_ctx* c, ehs_solve_info* info) const {
+    bool allconv = true;
+    for (int b = 0; b < items; ++b) {
+      const double rel = bnorm[b] > 0 ? beta[b] / bnorm[b] : 0.0;
+      const int conv = rel <= tol;
+      allconv = allconv && conv;
+      if (info) { info[b].iters = iters[b]; info[b].relres = rel; info[b].converged = conv; }
+    }
+    if (nonfinite) { c->err = "non-finite residual norm"; return EHS_ERR_NONFINITE; }
+    if (!allconv && breakdown) { c->err = "Arnoldi breakdown before tol"; return EHS_ERR_BREAKDOWN; }
+    if (!allconv) { c->err = "maxit reached before tol"; return EHS_ERR_NOCONV; }
+    return EHS_OK;
   }
-  if (nonfinite) { c->err = "non-finite residual norm"; return EHS_ERR_NONFINITE; }
-  if (!allconv && breakdown) { c->err = "Arnoldi breakdown before tol"; return EHS_ERR_BREAKDOWN; }
-  if (!allconv) { c->err = "maxit reached before tol"; return EHS_ERR_NOCONV; }
-  return EHS_OK;
+};
+
+void sync_read(ehs_ctx* c, void* host, const void* dev, size_t bytes) {
+  CK(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
 }
 
-void precond_apply(ehs_ctx* c, const double2* v, double2* z) {
-  const long long nv = (long long)c->H.items * c->n0;
-  if (c->opt.precond == EHS_PRECOND_DD) {
-    dd_apply(c, c->opt.prec, v, z);
-    return;
+// Runs body() (a fixed sequence of launches on c->s) directly, or replays it
+// from a CUDA graph captured on the first call for slot j.
+template <typename F> void graphed(ehs_ctx* c, int j, F body) {
+  if (!c->use_graphs) { body(); return; }
+  if (!c->pg[j]) {
+    cudaStream_t user = c->s;
+    const long long l0 = g_launches.load();
+    c->s = c->cap;
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(c->cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      c->s = user;
+      throw;
+    }
+    c->s = user;
+    CK(cudaStreamEndCapture(c->cap, &graph));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    c->pg[j] = ex;
+    c->pg_nodes[j] = g_launches.load() - l0;
+    g_launches -= c->pg_nodes[j];          // counted when replayed
   }
-  if (c->opt.prec == EHS_C64) {
-    launch_cast_c128_c64(nv, v, c->f_in, c->s); cnt(); post();
-    cycle_rec<float>(c, c->H, 0, c->f_in, c->f_out, false);
-    launch_cast_c64_c128(nv, c->f_out, z, c->s); cnt(); post();
-  } else {
-    cycle_rec<double>(c, c->H, 0, v, z, false);
+  CK(cudaGraphLaunch(c->pg[j], c->s));
+  g_launches += c->pg_nodes[j];
+}
+
+// ---- plain FP64 form: complex128 vectors, FP64 kernels, FP64 cycle -------
+ehs_status fgmres_c128(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info) {
+  const int items = c->H.items, m = c->opt.restart, nblk = c->nblk;
+  const long long n = c->n0;
+  cudaStream_t s = c->s;
+  Arnoldi A(items, m, c->opt.maxit, c->opt.tol);
+  launch_norm_part(n, items, q, c->npart, nblk, s);
+  launch_reduce_norm(items, nblk, c->npart, c->nrm, s); cnt(2); post();
+  sync_read(c, c->hpin, c->nrm, items * sizeof(double));
+  A.set_b(c->hpin);
+  CK(cudaMemsetAsync(u, 0, (size_t)items * n * sizeof(double2), s));
+  CK(cudaMemcpyAsync(c->rd, q, (size_t)items * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  std::vector<double2> h1((size_t)items * (m + 1)), h2((size_t)items * (m + 1)), yh;
+  std::vector<double> hn(items);
+  while (!A.all_done() && !A.maxed()) {
+    CK(cudaMemcpyAsync(c->nrm, A.beta.data(), items * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_inv(n, items, c->rd, c->nrm, c->V, s); cnt(); post();
+    A.start_cycle();
+    for (int j = 0; j < m; ++j) {
+      double2* Vj = c->V + (size_t)j * items * n;
+      double2* Zj = c->Z + (size_t)j * items * n;
+      graphed(c, j, [&]() {
+        if (c->opt.precond == EHS_PRECOND_DD) dd_apply_t<double>(c, Vj, Zj);
+        else cycle_rec<double>(c, c->H, 0, Vj, Zj, false);
+      });
+      launch_fine_apply<double>(c->H.g0, items, c->H.nrhs, c->H.cf64, c->H.h, 0.0, Zj, nullptr, c->w, 0, s);
+      const int nv = j + 1;
+      launch_mdot(n, items, nv, c->V, c->w, c->part, nblk, s);
+      launch_reduce_parts(items, nv, nblk, c->part, c->hd, 0, s);
+      launch_mupdate(n, items, nv, c->V, c->hd, c->w, c->part, nblk, 1, nullptr, s);
+      launch_reduce_parts(items, nv, nblk, c->part, c->y, 0, s);
+      launch_mupdate(n, items, nv, c->V, c->y, c->w, nullptr, nblk, 0, c->npart, s);
+      launch_reduce_norm(items, nblk, c->npart, c->nrm, s);
+      cnt(7); post();
+      CK(cudaMemcpyAsync(h1.data(), c->hd, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h2.data(), c->y, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      sync_read(c, hn.data(), c->nrm, items * sizeof(double));
+      if (!A.step(j, h1.data(), h2.data(), hn.data())) break;
+      launch_scale_inv(n, items, c->w, c->nrm, c->V + (size_t)(j + 1) * items * n, s); cnt(); post();
+    }
+    A.solve_y(yh);
+    CK(cudaMemcpyAsync(c->y, yh.data(), (size_t)items * m * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->kused, A.kused.data(), items * sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_xupdate<double2>(n, items, m, c->Z, c->y, c->kused, u, s);
+    launch_fine_apply<double>(c->H.g0, items, c->H.nrhs, c->H.cf64, c->H.h, 0.0, u, q, c->rd, 1, s);
+    launch_norm_part(n, items, c->rd, c->npart, nblk, s);
+    launch_reduce_norm(items, nblk, c->npart, c->nrm, s); cnt(4); post();
+    sync_read(c, c->hpin, c->nrm, items * sizeof(double));
+    A.end_cycle(c->hpin);
+    if (A.nonfinite || A.breakdown) break;
   }
+  return A.finish(c, info);
+}
+
+// ---- mixed form: complex64 cycle, FP64-class (df64) Krylov ----------------
+ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info) {
+  const int items = c->H.items, m = c->opt.restart, nblk = c->nblk;
+  const long long n = c->n0;
+  const long long nall = (long long)items * n;
+  cudaStream_t s = c->s;
+  Arnoldi A(items, m, c->opt.maxit, c->opt.tol);
+  launch_d2_to_df(nall, q, c->qq, s);
+  launch_norm_part_df(n, items, c->qq, c->npq, nblk, s);
+  launch_reduce_norm_df(items, nblk, c->npq, c->nrm, c->invq, s); cnt(3); post();
+  sync_read(c, c->hpin, c->nrm, items * sizeof(double));
+  A.set_b(c->hpin);
+  CK(cudaMemsetAsync(c->xq, 0, nall * sizeof(float4), s));
+  CK(cudaMemcpyAsync(c->rq, c->qq, nall * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+  std::vector<double2> h1((size_t)items * (m + 1)), h2((size_t)items * (m + 1)), yh;
+  std::vector<double> hn(items);
+  while (!A.all_done() && !A.maxed()) {
+    // V_0 = r / beta (invq holds 1/||r|| from the last norm)
+    launch_scale_df(n, items, c->rq, c->invq, c->Vq, s); cnt(); post();
+    A.start_cycle();
+    for (int j = 0; j < m; ++j) {
+      float4* Vj = c->Vq + (size_t)j * items * n;
+      float2* Zj = c->Zf + (size_t)j * items * n;
+      graphed(c, j, [&]() {
+        launch_df_to_f2(nall, Vj, c->f_in, c->s); cnt(); post();
+        if (c->opt.precond == EHS_PRECOND_DD) dd_apply_t<float>(c, c->f_in, Zj);
+        else cycle_rec<float>(c, c->H, 0, c->f_in, Zj, false);
+      });
+      launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, Zj, 1, nullptr, c->wq, 0, s);
+      const int nv = j + 1;
+      launch_mdot_df(n, items, nv, c->Vq, c->wq, c->partq, nblk, s);
+      launch_reduce_parts_df(items, nv, nblk, c->partq, c->hq, c->hhost, s);
+      launch_mupdate_df(n, items, nv, c->Vq, c->hq, c->wq, c->partq, nblk, 1, nullptr, s);
+      launch_reduce_parts_df(items, nv, nblk, c->partq, c->h2q, c->hhost + (size_t)items * 12, s);
+      launch_mupdate_df(n, items, nv, c->Vq, c->h2q, c->wq, nullptr, nblk, 0, c->npq, s);
+      launch_reduce_norm_df(items, nblk, c->npq, c->nrm, c->invq, s);
+      cnt(7); post();
+      CK(cudaMemcpyAsync(h1.data(), c->hhost, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h2.data(), c->hhost + (size_t)items * 12, (size_t)items * nv * sizeof(double2),
+                         cudaMemcpyDeviceToHost, s));
+      sync_read(c, hn.data(), c->nrm, items * sizeof(double));
+      if (!A.step(j, h1.data(), h2.data(), hn.data())) break;
+      launch_scale_df(n, items, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n, s); cnt(); post();
+    }
+    A.solve_y(yh);
+    // y to df64 on the device via the double2 -> df64 conversion
+    CK(cudaMemcpyAsync(c->hhost, yh.data(), (size_t)items * m * sizeof(double2), cudaMemcpyHostToDevice, s));
+    launch_d2_to_df((long long)items * m, c->hhost, c->yq, s);
+    CK(cudaMemcpyAsync(c->kused, A.kused.data(), items * sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_xupdate_df(n, items, m, c->Zf, c->yq, c->kused, c->xq, s);
+    launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, c->xq, 0, c->qq, c->rq, 1, s);
+    launch_norm_part_df(n, items, c->rq, c->npq, nblk, s);
+    launch_reduce_norm_df(items, nblk, c->npq, c->nrm, c->invq, s); cnt(5); post();
+    sync_read(c, c->hpin, c->nrm, items * sizeof(double));
+    A.end_cycle(c->hpin);
+    if (A.nonfinite || A.breakdown) break;
+  }
+  launch_df_to_d2(nall, c->xq, u, s); cnt(); post();
+  return A.finish(c, info);
+}
+
+ehs_status fgmres(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info) {
+  return c->opt.prec == EHS_C64 ? fgmres_df(c, q, u, info) : fgmres_c128(c, q, u, info);
 }
 
 __global__ void k_conj(long long n, double2* v) {
@@ -585,7 +725,29 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     c->kused = dalloc<int>(c, items);
     c->f_in = dalloc<float2>(c, (size_t)items * n);
     c->f_out = dalloc<float2>(c, (size_t)items * n);
+    if (opts->prec == EHS_C64) {   // df64 Krylov workspace of the mixed form
+      H.cfdf = dalloc<float4>(c, (size_t)2 * H.nsets * H.g0.ncell);
+      launch_coef_df((long long)H.nsets * H.g0.ncell, H.cf64, H.cfdf, c->s); cnt(); post();
+      c->Vq = dalloc<float4>(c, (size_t)(m + 1) * items * n);
+      c->Zf = dalloc<float2>(c, (size_t)m * items * n);
+      c->wq = dalloc<float4>(c, (size_t)items * n);
+      c->rq = dalloc<float4>(c, (size_t)items * n);
+      c->qq = dalloc<float4>(c, (size_t)items * n);
+      c->xq = dalloc<float4>(c, (size_t)items * n);
+      c->partq = dalloc<float4>(c, (size_t)items * 12 * c->nblk);
+      c->hq = dalloc<float4>(c, (size_t)items * 12);
+      c->h2q = dalloc<float4>(c, (size_t)items * 12);
+      c->yq = dalloc<float4>(c, (size_t)items * 12);
+      c->npq = dalloc<float2>(c, (size_t)items * c->nblk);
+      c->invq = dalloc<float2>(c, items);
+      c->hhost = dalloc<double2>(c, (size_t)items * 24);
+    }
     CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));
+    CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    c->pg.assign(m, nullptr);
+    c->pg_nodes.assign(m, 0);
+    const char* ng = getenv("EHS_NO_GRAPHS");
+    c->use_graphs = !(ng && ng[0] == '1');
     CK(cudaStreamSynchronize(c->s));
     return EHS_OK;
   });
@@ -600,7 +762,10 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
 
 ehs_status ehs_destroy(ehs_ctx* c) {
   if (!c) return EHS_OK;
-  if (c->s) cudaStreamSynchronize(c->s);
+  cudaStreamSynchronize(c->s);
+  for (cudaGraphExec_t g : c->pg)
+    if (g) cudaGraphExecDestroy(g);
+  if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->allocs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);

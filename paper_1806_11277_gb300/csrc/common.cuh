@@ -52,10 +52,12 @@ struct Grid {
 };
 
 EHS_HD void cell_coords(const Grid& g, long long c, int i[3]) {
-  i[0] = (int)(c % g.n[0]);
-  long long t = c / g.n[0];
-  i[1] = (int)(t % g.n[1]);
-  i[2] = (int)(t / g.n[1]);
+  const unsigned cc = (unsigned)c;                 // ncell < 2^31 on every level
+  const unsigned t = cc / (unsigned)g.n[0];
+  i[0] = (int)(cc - t * (unsigned)g.n[0]);
+  const unsigned z = t / (unsigned)g.n[1];
+  i[1] = (int)(t - z * (unsigned)g.n[1]);
+  i[2] = (int)z;
 }
 EHS_HD long long cell_index(const Grid& g, const int i[3]) {
   return ((long long)i[2] * g.n[1] + i[1]) * g.n[0] + i[0];
@@ -91,7 +93,7 @@ struct StencilLayout {
 };
 
 // slot of coefficient (a, b, offset o) or -1 if outside the stored box
-EHS_HD int st_slot(const StencilLayout& L, int a, int b, int ox, int oy, int oz) {
+__host__ __device__ constexpr int st_slot(const StencilLayout& L, int a, int b, int ox, int oy, int oz) {
   int q = L.pidx[a][b];
   if (q < 0) return -1;
   const PairBox& P = L.p[q];
@@ -104,7 +106,7 @@ EHS_HD int st_slot(const StencilLayout& L, int a, int b, int ox, int oy, int oz)
 // 1..n-1 are unknowns), 1 = cell-like with zero ghosts (u tangential),
 // 2 = cell-like with clamped ghosts (p).  pw(kind, j, J, nc) is the weight of
 // coarse index J in fine index j (fine grid has 2 nc cells).
-EHS_HD double pw(int kind, int j, int J, int nc) {
+__host__ __device__ constexpr double pw(int kind, int j, int J, int nc) {
   const int nf = 2 * nc;
   if (kind == 0) {
     if (j < 1 || j > nf - 1 || J < 1 || J > nc - 1) return 0.0;
@@ -123,8 +125,120 @@ EHS_HD double pw(int kind, int j, int J, int nc) {
   }
   return w;
 }
+// pw() in quarters as an integer (all transfer weights are multiples of 1/4):
+// the transfer kernels use this so they never touch the FP64 pipe
+__host__ __device__ constexpr int pw4(int kind, int j, int J, int nc) {
+  const int nf = 2 * nc;
+  if (kind == 0) {
+    if (j < 1 || j > nf - 1 || J < 1 || J > nc - 1) return 0;
+    if ((j & 1) == 0) return (j == 2 * J) ? 4 : 0;
+    return (J == (j - 1) / 2 || J == (j + 1) / 2) ? 2 : 0;
+  }
+  if (j < 0 || j > nf - 1 || J < 0 || J > nc - 1) return 0;
+  const int Jc = j >> 1;
+  const int nb = (j & 1) ? Jc + 1 : Jc - 1;
+  int w = 0;
+  if (J == Jc) w += 3;
+  if (nb >= 0 && nb < nc) {
+    if (J == nb) w += 1;
+  } else if (kind == 2 && J == Jc) {
+    w += 1;
+  }
+  return w;
+}
+
 // kind of component a along direction k
-EHS_HD int tkind(int a, int k, int d) { return a == d ? 2 : (a == k ? 0 : 1); }
+__host__ __device__ constexpr int tkind(int a, int k, int d) { return a == d ? 2 : (a == k ? 0 : 1); }
+
+// Level-0 stencil layout of the mixed operator: (u_k, u_k) a 3^d box, (u_k, p)
+// offsets -1..0 along k, (p, u_k) offsets 0..1 along k, (p, p) the centre.
+__host__ __device__ constexpr StencilLayout make_fine_layout(int d) {
+  StencilLayout L{};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) L.pidx[a][b] = -1;
+  int q = 0, base = 0;
+  for (int a = 0; a <= d; ++a) {
+    L.row_first[a] = q;
+    const int nb = a < d ? 2 : d + 1;
+    for (int t = 0; t < nb; ++t) {
+      const int b = a < d ? (t == 0 ? a : d) : t;
+      PairBox& P = L.p[q];
+      P.a = a; P.b = b;
+      for (int k = 0; k < 3; ++k) { P.lo[k] = 0; P.ext[k] = 1; }
+      for (int k = 0; k < d; ++k) {
+        if (a < d && b == a) { P.lo[k] = -1; P.ext[k] = 3; }
+        else if (a < d && k == a) { P.lo[k] = -1; P.ext[k] = 2; }
+        else if (a == d && b < d && k == b) { P.lo[k] = 0; P.ext[k] = 2; }
+      }
+      P.base = base;
+      base += P.ext[0] * P.ext[1] * P.ext[2];
+      L.pidx[a][b] = q++;
+    }
+  }
+  L.row_first[d + 1] = q;
+  L.npair = q;
+  L.nslot = base;
+  return L;
+}
+
+// Galerkin coarse layout: the box of each pair on the next coarser level,
+// from the fine box and the 1D transfer supports (interior rows).
+__host__ __device__ constexpr StencilLayout make_coarse_layout(int d, const StencilLayout& F) {
+  StencilLayout C{};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) C.pidx[a][b] = -1;
+  const int nc = 64, I = 32;
+  int base = 0;
+  for (int q = 0; q < F.npair; ++q) {
+    const PairBox& P = F.p[q];
+    PairBox& Q = C.p[q];
+    Q.a = P.a; Q.b = P.b;
+    for (int k = 0; k < 3; ++k) {
+      if (k >= d) { Q.lo[k] = 0; Q.ext[k] = 1; continue; }
+      const int ka = tkind(P.a, k, d), kb = tkind(P.b, k, d);
+      int mn = 1 << 30, mx = -(1 << 30);
+      for (int i = 2 * I - 4; i <= 2 * I + 5; ++i) {
+        if (pw(ka, i, I, nc) == 0.0) continue;
+        for (int o = P.lo[k]; o < P.lo[k] + P.ext[k]; ++o) {
+          const int j = i + o;
+          for (int J = j / 2 - 3; J <= j / 2 + 3; ++J) {
+            if (pw(kb, j, J, nc) == 0.0) continue;
+            mn = J - I < mn ? J - I : mn;
+            mx = J - I > mx ? J - I : mx;
+          }
+        }
+      }
+      Q.lo[k] = mn;
+      Q.ext[k] = mx - mn + 1;
+    }
+    Q.base = base;
+    base += Q.ext[0] * Q.ext[1] * Q.ext[2];
+    C.pidx[Q.a][Q.b] = q;
+  }
+  C.npair = F.npair;
+  C.nslot = base;
+  for (int a = 0; a < 5; ++a) C.row_first[a] = F.row_first[a];
+  return C;
+}
+
+// layout of Galerkin level lv >= 1 (the boxes are the same from level 2 on)
+__host__ __device__ constexpr StencilLayout level_layout(int d, int lv) {
+  StencilLayout L = make_fine_layout(d);
+  for (int l = 0; l < lv; ++l) L = make_coarse_layout(d, L);
+  return L;
+}
+__host__ __device__ constexpr bool same_layout(const StencilLayout& A, const StencilLayout& B) {
+  if (A.npair != B.npair || A.nslot != B.nslot) return false;
+  for (int q = 0; q < A.npair; ++q) {
+    if (A.p[q].a != B.p[q].a || A.p[q].b != B.p[q].b || A.p[q].base != B.p[q].base) return false;
+    for (int k = 0; k < 3; ++k)
+      if (A.p[q].lo[k] != B.p[q].lo[k] || A.p[q].ext[k] != B.p[q].ext[k]) return false;
+  }
+  return true;
+}
+static_assert(same_layout(level_layout(2, 2), level_layout(2, 3)), "2D Galerkin boxes settle at level 2");
+static_assert(same_layout(level_layout(3, 2), level_layout(3, 3)), "3D Galerkin boxes settle at level 2");
+static_assert(level_layout(2, 1).nslot == 87 && level_layout(2, 2).nslot == 135, "2D table sizes");
 
 // a valid unknown slot?  (u_k at i_k == 0 is a boundary face)
 EHS_HD bool slot_valid(int a, int d, const int i[3]) { return a == d || i[a] >= 1; }

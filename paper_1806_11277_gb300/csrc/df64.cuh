@@ -1,0 +1,98 @@
+// Double-float ("df64") arithmetic: a real number carried as an unevaluated
+// sum hi + lo of two floats (about 48 significant bits).  GB300 runs FP32 FMA
+// about 54x faster than FP64 FMA, so the FP64-class parts of the solver (outer
+// Krylov, its operator, the coarsest solve) use this representation instead
+// of the FP64 pipe.
+//
+// Building blocks are the classical error-free transformations: Knuth's
+// TwoSum and Dekker's FastTwoSum for sums, and the FMA-based TwoProduct for
+// products (the product error a*b - fl(a*b) is exactly fma(a, b, -fl(a*b))).
+// Addition is the "sloppy" double-float add (one TwoSum on the high parts,
+// then renormalisation), whose error bound has the same form as an IEEE
+// addition with a 48-bit significand.  The __fadd_rn / __fmul_rn intrinsics
+// keep the compiler from contracting these steps into FMAs.
+//
+// Storage: a real df64 is a float2 (x = hi, y = lo); a complex df64 is a
+// float4 (x = re.hi, y = re.lo, z = im.hi, w = im.lo), 16 bytes like complex128.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ehs {
+
+struct dfr {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfr df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  const float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfr df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+__device__ __forceinline__ dfr df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ dfr df_add(dfr a, dfr b) {
+  const dfr s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfr df_neg(dfr a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfr df_sub(dfr a, dfr b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfr df_mul(dfr a, dfr b) {
+  const dfr p = df_two_prod(a.hi, b.hi);
+  return df_fast_two_sum(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ dfr df_mulf(dfr a, float b) {
+  const dfr p = df_two_prod(a.hi, b);
+  return df_fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+__device__ __forceinline__ dfr df_from_f(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ dfr df_from_d(double a) {
+  const float hi = __double2float_rn(a);
+  return {hi, __double2float_rn(a - (double)hi)};
+}
+__device__ __forceinline__ double df_to_d(dfr a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfr df_zero() { return {0.0f, 0.0f}; }
+
+// complex df64
+struct dfc {
+  dfr re, im;
+};
+__device__ __forceinline__ dfc dfc_ld(const float4* p) {
+  const float4 v = __ldg(p);
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ dfc dfc_ldv(const float4* p) {   // plain (non-__ldg) load
+  const float4 v = *p;
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void dfc_st(float4* p, dfc a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ dfc dfc_zero() { return {df_zero(), df_zero()}; }
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+  return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+// a * b with b a single-precision complex
+__device__ __forceinline__ dfc dfc_mulf(dfc a, float2 b) {
+  return {df_sub(df_mulf(a.re, b.x), df_mulf(a.im, b.y)), df_add(df_mulf(a.re, b.y), df_mulf(a.im, b.x))};
+}
+// conj(a) * b
+__device__ __forceinline__ dfc dfc_cmul(dfc a, dfc b) {
+  return {df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dfc dfc_scale(dfc a, dfr s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
+__device__ __forceinline__ dfc dfc_scalef(dfc a, float s) { return {df_mulf(a.re, s), df_mulf(a.im, s)}; }
+__device__ __forceinline__ dfc dfc_from_f2(float2 z) { return {df_from_f(z.x), df_from_f(z.y)}; }
+__device__ __forceinline__ float2 dfc_to_f2(dfc a) {
+  return make_float2(__fadd_rn(a.re.hi, a.re.lo), __fadd_rn(a.im.hi, a.im.lo));
+}
+__device__ __forceinline__ dfc dfc_from_d2(double2 z) { return {df_from_d(z.x), df_from_d(z.y)}; }
+__device__ __forceinline__ double2 dfc_to_d2(dfc a) { return make_double2(df_to_d(a.re), df_to_d(a.im)); }
+
+}  // namespace ehs

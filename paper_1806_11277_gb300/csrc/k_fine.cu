@@ -386,42 +386,7 @@ void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
     k_fine_vanka<T, 3><<<grid1(np, items, 128), 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo);
 }
 
-void fine_table_layout(int d, StencilLayout* L) {
-  *L = StencilLayout{};
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) L->pidx[a][b] = -1;
-  int q = 0, base = 0;
-  auto add = [&](int a, int b, const int lo[3], const int ext[3]) {
-    PairBox& P = L->p[q];
-    P.a = a; P.b = b;
-    for (int k = 0; k < 3; ++k) { P.lo[k] = lo[k]; P.ext[k] = ext[k]; }
-    P.base = base;
-    base += ext[0] * ext[1] * ext[2];
-    L->pidx[a][b] = q++;
-  };
-  for (int a = 0; a <= d; ++a) {
-    L->row_first[a] = q;
-    if (a < d) {
-      int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
-      for (int k = 0; k < d; ++k) { lo[k] = -1; ext[k] = 3; }
-      add(a, a, lo, ext);
-      int lo2[3] = {0, 0, 0}, ext2[3] = {1, 1, 1};
-      lo2[a] = -1; ext2[a] = 2;
-      add(a, d, lo2, ext2);
-    } else {
-      for (int b = 0; b < d; ++b) {
-        int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
-        ext[b] = 2;
-        add(d, b, lo, ext);
-      }
-      int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
-      add(d, d, lo, ext);
-    }
-  }
-  L->row_first[d + 1] = q;
-  L->npair = q;
-  L->nslot = base;
-}
+void fine_table_layout(int d, StencilLayout* L) { *L = make_fine_layout(d); }
 
 void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double h,
                        double alpha, const StencilLayout& L, double2* tab, cudaStream_t s) {

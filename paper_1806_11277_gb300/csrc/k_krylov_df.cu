@@ -1,0 +1,397 @@
+// FP64-class (double-float) kernels of the outer FGMRES solve, its operator
+// K (unshifted, Sec. 3 eq. elasticHelmReformulatedSystem), the true residual,
+// and the coarsest-level solve.  Same algorithms as k_krylov.cu / k_fine.cu /
+// k_dense.cu, carried out in df64 (see df64.cuh) on the FP32 pipe.
+//
+// Layouts: Krylov basis V and solution x as complex df64 (float4 per value),
+// preconditioned directions Z as complex64 (the multigrid cycle's output
+// precision), fine coefficients as 4 df64 reals per cell, coarsest inverse as
+// complex df64.
+#include "df64.cuh"
+#include "kernels.h"
+
+namespace ehs {
+
+struct Coef4df {
+  dfr mu, kap, mr, mi;
+};
+
+namespace {
+
+constexpr int KB = 256;
+constexpr int MAXV = 12;
+
+__device__ __forceinline__ dfr shfl_df(dfr v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ dfc warp_sum_df(dfc v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.re = df_add(v.re, shfl_df(v.re, o));
+    v.im = df_add(v.im, shfl_df(v.im, o));
+  }
+  return v;
+}
+__device__ __forceinline__ dfr warp_sum_df(dfr v) {
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_df(v, o));
+  return v;
+}
+
+__device__ __forceinline__ void block_store_df(const dfc* acc, int nv, float4* part, int item, int nblk) {
+  __shared__ dfc sh[KB / 32][MAXV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = 0; i < nv; ++i) {
+    const dfc v = warp_sum_df(acc[i]);
+    if (lane == 0) sh[wid][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    dfc s = dfc_zero();
+    for (int w = 0; w < KB / 32; ++w) s = dfc_add(s, sh[w][threadIdx.x]);
+    dfc_st(part + ((long long)item * nv + threadIdx.x) * nblk + blockIdx.x, s);
+  }
+}
+__device__ __forceinline__ void block_store_norm(dfr v, float2* part, int item, int nblk) {
+  __shared__ dfr shn[KB / 32];
+  v = warp_sum_df(v);
+  if ((threadIdx.x & 31) == 0) shn[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dfr s = df_zero();
+    for (int i = 0; i < KB / 32; ++i) s = df_add(s, shn[i]);
+    part[(long long)item * nblk + blockIdx.x] = make_float2(s.hi, s.lo);
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const float4* __restrict__ V,
+                                                const float4* __restrict__ w, float4* part, int nblk) {
+  const int item = blockIdx.y;
+  dfc acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = dfc_zero();
+  const float4* wv = w + (long long)item * n;
+  for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+    const dfc we = dfc_ld(wv + e);
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      acc[i] = dfc_add(acc[i], dfc_cmul(dfc_ld(V + ((long long)i * items + item) * n + e), we));
+  }
+  block_store_df(acc, NV, part, item, nblk);
+}
+
+// w -= sum_i V_i h_i; optional partial dots of V with the new w and |w|^2
+template <int NV>
+__global__ void __launch_bounds__(KB) k_mupdate_df(long long n, int items, const float4* __restrict__ V,
+                                                   const float4* __restrict__ h, float4* __restrict__ w,
+                                                   float4* part, int nblk, int dot, float2* nrm_part) {
+  const int item = blockIdx.y;
+  dfc hh[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) hh[i] = dfc_ld(h + (long long)item * NV + i);
+  dfc acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = dfc_zero();
+  dfr nacc = df_zero();
+  float4* wv = w + (long long)item * n;
+  for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+    dfc we = dfc_ldv(wv + e);
+    dfc vv[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
+      we = dfc_sub(we, dfc_mul(vv[i], hh[i]));
+    }
+    dfc_st(wv + e, we);
+    if (dot) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = dfc_add(acc[i], dfc_cmul(vv[i], we));
+    }
+    nacc = df_add(nacc, df_add(df_mul(we.re, we.re), df_mul(we.im, we.im)));
+  }
+  if (dot) block_store_df(acc, NV, part, item, nblk);
+  if (nrm_part) block_store_norm(nacc, nrm_part, item, nblk);
+}
+
+__global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2* part, int nblk) {
+  const int item = blockIdx.y;
+  const float4* wv = w + (long long)item * n;
+  dfr nacc = df_zero();
+  for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+    const dfc we = dfc_ld(wv + e);
+    nacc = df_add(nacc, df_add(df_mul(we.re, we.re), df_mul(we.im, we.im)));
+  }
+  block_store_norm(nacc, part, item, nblk);
+}
+
+// one warp per output; writes the df64 value and its double copy for the host
+__global__ void k_reduce_parts_df(int nout, int nblk, const float4* __restrict__ part, float4* out,
+                                  double2* outd) {
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= nout) return;
+  dfc s = dfc_zero();
+  for (int b = lane; b < nblk; b += 32) s = dfc_add(s, dfc_ld(part + (long long)o * nblk + b));
+  s = warp_sum_df(s);
+  if (lane == 0) {
+    dfc_st(out + o, s);
+    outd[o] = dfc_to_d2(s);
+  }
+}
+// norm = sqrt(sum); writes the double norm for the host and 1/norm in df64
+__global__ void k_reduce_norm_df(int items, int nblk, const float2* __restrict__ part, double* out,
+                                 float2* inv) {
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= items) return;
+  dfr s = df_zero();
+  for (int b = lane; b < nblk; b += 32) {
+    const float2 v = part[(long long)o * nblk + b];
+    s = df_add(s, {v.x, v.y});
+  }
+  s = warp_sum_df(s);
+  if (lane == 0) {
+    const double nrm = sqrt(df_to_d(s));   // one FP64 sqrt per item
+    out[o] = nrm;
+    const dfr iv = df_from_d(nrm > 0.0 ? 1.0 / nrm : 0.0);
+    if (inv) inv[o] = make_float2(iv.hi, iv.lo);
+  }
+}
+
+__global__ void k_scale_df(long long n, const float4* __restrict__ w, const float2* __restrict__ inv,
+                           float4* __restrict__ out) {
+  const int item = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float2 s = inv[item];
+  dfc_st(out + (long long)item * n + e, dfc_scale(dfc_ld(w + (long long)item * n + e), {s.x, s.y}));
+}
+
+__global__ void k_xupdate_df(long long n, int items, int m, const float2* __restrict__ Z,
+                             const float4* __restrict__ y, const int* __restrict__ kused,
+                             float4* __restrict__ x) {
+  const int item = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int k = kused[item];
+  dfc acc = dfc_ldv(x + (long long)item * n + e);
+  for (int i = 0; i < k; ++i)
+    acc = dfc_add(acc, dfc_mulf(dfc_ld(y + (long long)item * m + i),
+                                __ldg(Z + ((long long)i * items + item) * n + e)));
+  dfc_st(x + (long long)item * n + e, acc);
+}
+
+__global__ void k_d2_to_df(long long n, const double2* __restrict__ in, float4* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dfc_st(out + e, dfc_from_d2(in[e]));
+}
+__global__ void k_df_to_d2(long long n, const float4* __restrict__ in, double2* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = dfc_to_d2(dfc_ld(in + e));
+}
+__global__ void k_df_to_f2(long long n, const float4* __restrict__ in, float2* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = dfc_to_f2(dfc_ld(in + e));
+}
+__global__ void k_coef_df(long long n, const Coef4<double>* __restrict__ in, Coef4df* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const Coef4<double> v = in[e];
+  out[e] = {df_from_d(v.mu), df_from_d(v.kap), df_from_d(v.mr), df_from_d(v.mi)};
+}
+
+// --- FP64-class fine operator --------------------------------------------
+template <typename V> __device__ __forceinline__ dfc ldx(const V* p, long long i);
+template <> __device__ __forceinline__ dfc ldx<float4>(const float4* p, long long i) { return dfc_ld(p + i); }
+template <> __device__ __forceinline__ dfc ldx<float2>(const float2* p, long long i) {
+  return dfc_from_f2(__ldg(p + i));
+}
+__device__ __forceinline__ Coef4df ldcf_df(const Coef4df* p, long long c) {
+  const float4* q = reinterpret_cast<const float4*>(p) + 2 * c;
+  const float4 a = __ldg(q), b = __ldg(q + 1);
+  return {{a.x, a.y}, {a.z, a.w}, {b.x, b.y}, {b.z, b.w}};
+}
+
+struct FinePdf {
+  dfr h2inv, hinv, alpha;
+};
+
+template <typename V, int D>
+__device__ __forceinline__ dfc row_u_df(const Grid& g, int k, long long c, const int i[3],
+                                        const Coef4df* cf, const V* xk, const V* p, const FinePdf& P) {
+  const long long sk = stride_of(g, k);
+  const Coef4df c0 = ldcf_df(cf, c), c1 = ldcf_df(cf, c - sk);
+  const dfc xc = ldx<V>(xk, c);
+  dfc nb = dfc_zero();
+  if (i[k] + 1 < g.n[k]) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c + sk), c0.mu));
+  if (i[k] - 1 >= 1) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c - sk), c1.mu));
+  const dfr base = df_add(c0.mu, c1.mu);
+  dfr wsum = base;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == k) continue;
+    const long long sj = stride_of(g, j);
+    const bool hp = i[j] + 1 < g.n[j], hm = i[j] - 1 >= 0;
+    const long long cp = hp ? c + sj : c, cm = hm ? c - sj : c;
+    dfr wp = df_add(base, df_add(ldcf_df(cf, cp).mu, ldcf_df(cf, cp - sk).mu));
+    dfr wm = df_add(base, df_add(ldcf_df(cf, cm).mu, ldcf_df(cf, cm - sk).mu));
+    wp = {wp.hi * 0.25f, wp.lo * 0.25f};   // exact scaling by a power of two
+    wm = {wm.hi * 0.25f, wm.lo * 0.25f};
+    wsum = df_add(wsum, df_add(wp, wm));
+    if (hp) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c + sj), wp));
+    if (hm) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c - sj), wm));
+  }
+  dfr rf = df_add(c0.mr, c1.mr), gf = df_add(c0.mi, c1.mi);
+  rf = {rf.hi * 0.5f, rf.lo * 0.5f};
+  gf = {gf.hi * 0.5f, gf.lo * 0.5f};
+  const dfc dg = {df_sub(df_mul(wsum, P.h2inv), rf), df_add(gf, df_mul(P.alpha, rf))};
+  dfc y = dfc_sub(dfc_mul(dg, xc), dfc_scale(nb, P.h2inv));
+  return dfc_add(y, dfc_scale(dfc_sub(ldx<V>(p, c), ldx<V>(p, c - sk)), P.hinv));
+}
+
+template <typename V, int D>
+__device__ __forceinline__ dfc row_p_df(const Grid& g, long long c, const int i[3], const Coef4df& c0,
+                                        const V* x, const FinePdf& P) {
+  const long long N = g.ncell;
+  const dfc pc = ldx<V>(x + (long long)D * N, c);
+  dfc s = dfc_zero();
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const V* xk = x + (long long)k * N;
+    if (i[k] >= 1) s = dfc_add(s, ldx<V>(xk, c));
+    if (i[k] + 1 < g.n[k]) s = dfc_sub(s, ldx<V>(xk, c + stride_of(g, k)));
+  }
+  return dfc_sub(dfc_scale(s, P.hinv), dfc_scale(pc, c0.kap));
+}
+
+// y = K x (mode 0) or y = b - K x (mode 1); x of type V, b and y complex df64
+template <typename V, int D>
+__global__ void k_fine_apply_df(Grid g, int nrhs, const Coef4df* __restrict__ cf, FinePdf P,
+                                const V* __restrict__ x, const float4* __restrict__ b,
+                                float4* __restrict__ y, int mode) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int item = blockIdx.y;
+  const long long N = g.ncell;
+  const long long vo = (long long)item * (D + 1) * N;
+  const Coef4df* cs = cf + (long long)(item / nrhs) * N;
+  const V* xv = x + vo;
+  int i[3];
+  cell_coords(g, c, i);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    dfc r = dfc_zero();
+    if (i[k] >= 1) {
+      r = row_u_df<V, D>(g, k, c, i, cs, xv + (long long)k * N, xv + (long long)D * N, P);
+      if (mode) r = dfc_sub(dfc_ld(b + vo + (long long)k * N + c), r);
+    }
+    dfc_st(y + vo + (long long)k * N + c, r);
+  }
+  dfc r = row_p_df<V, D>(g, c, i, ldcf_df(cs, c), xv, P);
+  if (mode) r = dfc_sub(dfc_ld(b + vo + (long long)D * N + c), r);
+  dfc_st(y + vo + (long long)D * N + c, r);
+}
+
+// coarsest: x = Ainv r with Ainv in complex df64, r and x complex64; one warp per row
+__global__ void k_dense_apply_df(int N, int nrhs, const float4* __restrict__ inv,
+                                 const float2* __restrict__ r, float2* __restrict__ x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.y;
+  if (warp >= N) return;
+  const float4* row = inv + ((long long)(item / nrhs) * N + warp) * N;
+  const float2* rv = r + (long long)item * N;
+  dfc acc = dfc_zero();
+  for (int j = lane; j < N; j += 32) acc = dfc_add(acc, dfc_mulf(dfc_ld(row + j), __ldg(rv + j)));
+  acc = warp_sum_df(acc);
+  if (lane == 0) x[(long long)item * N + warp] = dfc_to_f2(acc);
+}
+
+inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+FinePdf mkPdf(double h, double alpha) {
+  FinePdf P;
+  auto split = [](double v) {
+    dfr r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+  };
+  P.h2inv = split(1.0 / (h * h));
+  P.hinv = split(1.0 / h);
+  P.alpha = split(alpha);
+  return P;
+}
+
+}  // namespace
+
+#define EHS_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
+void launch_mdot_df(long long n, int items, int nv, const float4* V, const float4* w, float4* part,
+                    int nblk, cudaStream_t s) {
+  const dim3 g(nblk, items);
+  switch (nv) {
+#define X(k) case k: k_mdot_df<k><<<g, KB, 0, s>>>(n, items, V, w, part, nblk); break;
+    EHS_NV_CASES(X)
+#undef X
+    default: break;
+  }
+}
+void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
+                       float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s) {
+  const dim3 g(nblk, items);
+  switch (nv) {
+#define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part); break;
+    EHS_NV_CASES(X)
+#undef X
+    default: break;
+  }
+}
+void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s) {
+  k_norm_part_df<<<dim3(nblk, items), KB, 0, s>>>(n, w, part, nblk);
+}
+void launch_reduce_parts_df(int items, int nv, int nblk, const float4* part, float4* out, double2* outd,
+                            cudaStream_t s) {
+  const int nout = items * nv;
+  k_reduce_parts_df<<<nb((long long)nout * 32, 128), 128, 0, s>>>(nout, nblk, part, out, outd);
+}
+void launch_reduce_norm_df(int items, int nblk, const float2* part, double* out, float2* inv, cudaStream_t s) {
+  k_reduce_norm_df<<<nb((long long)items * 32, 128), 128, 0, s>>>(items, nblk, part, out, inv);
+}
+void launch_scale_df(long long n, int items, const float4* w, const float2* inv, float4* out, cudaStream_t s) {
+  k_scale_df<<<dim3(nb(n, 256), items), 256, 0, s>>>(n, w, inv, out);
+}
+void launch_xupdate_df(long long n, int items, int m, const float2* Z, const float4* y, const int* kused,
+                       float4* x, cudaStream_t s) {
+  k_xupdate_df<<<dim3(nb(n, 256), items), 256, 0, s>>>(n, items, m, Z, y, kused, x);
+}
+void launch_d2_to_df(long long n, const double2* in, float4* out, cudaStream_t s) {
+  k_d2_to_df<<<nb(n, 256), 256, 0, s>>>(n, in, out);
+}
+void launch_df_to_d2(long long n, const float4* in, double2* out, cudaStream_t s) {
+  k_df_to_d2<<<nb(n, 256), 256, 0, s>>>(n, in, out);
+}
+void launch_df_to_f2(long long n, const float4* in, float2* out, cudaStream_t s) {
+  k_df_to_f2<<<nb(n, 256), 256, 0, s>>>(n, in, out);
+}
+void launch_coef_df(long long n, const Coef4<double>* in, void* out, cudaStream_t s) {
+  k_coef_df<<<nb(n, 256), 256, 0, s>>>(n, in, (Coef4df*)out);
+}
+void launch_fine_apply_df(const Grid& g, int items, int nrhs, const void* cf, double h, double alpha,
+                          const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s) {
+  const FinePdf P = mkPdf(h, alpha);
+  const dim3 grid(nb(g.ncell, 128), items);
+  const Coef4df* c = (const Coef4df*)cf;
+  if (g.d == 2) {
+    if (x_is_c64) k_fine_apply_df<float2, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode);
+    else k_fine_apply_df<float4, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode);
+  } else {
+    if (x_is_c64) k_fine_apply_df<float2, 3><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode);
+    else k_fine_apply_df<float4, 3><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode);
+  }
+}
+void launch_dense_apply_df(int N, int items, int nrhs, const float4* inv, const float2* r, float2* x,
+                           cudaStream_t s) {
+  const int wpb = 8;
+  k_dense_apply_df<<<dim3((N + wpb - 1) / wpb, items), 32 * wpb, 0, s>>>(N, nrhs, inv, r, x);
+}
+
+}  // namespace ehs

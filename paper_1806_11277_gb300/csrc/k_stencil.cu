@@ -12,42 +12,7 @@
 namespace ehs {
 
 // ------------------------------------------------------------------ layout
-void coarse_layout(int d, const StencilLayout& F, StencilLayout* C) {
-  *C = StencilLayout{};
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) C->pidx[a][b] = -1;
-  const int nc = 64, I = 32;
-  int base = 0;
-  for (int q = 0; q < F.npair; ++q) {
-    const PairBox& P = F.p[q];
-    PairBox& Q = C->p[q];
-    Q.a = P.a; Q.b = P.b;
-    for (int k = 0; k < 3; ++k) {
-      if (k >= d) { Q.lo[k] = 0; Q.ext[k] = 1; continue; }
-      const int ka = tkind(P.a, k, d), kb = tkind(P.b, k, d);
-      int mn = 1 << 30, mx = -(1 << 30);
-      for (int i = 2 * I - 4; i <= 2 * I + 5; ++i) {
-        if (pw(ka, i, I, nc) == 0.0) continue;
-        for (int o = P.lo[k]; o < P.lo[k] + P.ext[k]; ++o) {
-          const int j = i + o;
-          for (int J = j / 2 - 3; J <= j / 2 + 3; ++J) {
-            if (pw(kb, j, J, nc) == 0.0) continue;
-            mn = std::min(mn, J - I);
-            mx = std::max(mx, J - I);
-          }
-        }
-      }
-      Q.lo[k] = mn;
-      Q.ext[k] = mx - mn + 1;
-    }
-    Q.base = base;
-    base += Q.ext[0] * Q.ext[1] * Q.ext[2];
-    C->pidx[Q.a][Q.b] = q;
-  }
-  C->npair = F.npair;
-  C->nslot = base;
-  for (int a = 0; a < 5; ++a) C->row_first[a] = F.row_first[a];
-}
+void coarse_layout(int d, const StencilLayout& F, StencilLayout* C) { *C = make_coarse_layout(d, F); }
 
 namespace {
 
@@ -159,66 +124,109 @@ __global__ void k_table_cast(long long n, const double2* in, C* out) {
   }
 }
 
-// value of row a at cell c (coords i) of the stored operator
-template <typename T, int D>
-__device__ __forceinline__ typename CT<T>::type st_row(
-    const Grid& g, const StencilLayout& L, const typename CT<T>::type* tab, int a, long long c,
-    const int i[3], const typename CT<T>::type* x) {
-  typedef typename CT<T>::type Cx;
-  Cx y = czero<Cx>();
-  const long long N = g.ncell;
-  for (int q = L.row_first[a]; q < L.row_first[a + 1]; ++q) {
-    const PairBox& P = L.p[q];
-    const Cx* xb = x + (long long)P.b * N;
-    int s = P.base;
-    for (int oz = 0; oz < P.ext[2]; ++oz) {
-      const int jz = i[2] + P.lo[2] + oz;
-      for (int oy = 0; oy < P.ext[1]; ++oy) {
-        const int jy = i[1] + P.lo[1] + oy;
-        const bool rowin = jz >= 0 && jz < g.n[2] && jy >= 0 && jy < g.n[1];
-        for (int ox = 0; ox < P.ext[0]; ++ox, ++s) {
-          const int jx = i[0] + P.lo[0] + ox;
-          if (rowin && jx >= 0 && jx < g.n[0]) {
-            const long long cj = ((long long)jz * g.n[1] + jy) * g.n[0] + jx;
-            y = cfma(__ldg(tab + (long long)s * N + c), __ldg(xb + cj), y);
+// Row a of the stored operator at cell c (coords i), with the stencil box of
+// Galerkin level variant LV (1 = first coarse level, 2 = all coarser ones)
+// known at compile time so that every table and vector load of the row is
+// issued back to back.
+template <typename T, int D, int LV, int Q, int QE>
+__device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
+                                        const typename CT<T>::type* __restrict__ tab,
+                                        long long c, const int i[3],
+                                        const typename CT<T>::type* __restrict__ x) {
+  if constexpr (Q < QE) {
+    constexpr StencilLayout L = level_layout(D, LV);
+    constexpr int b = L.p[Q].b, base = L.p[Q].base;
+    constexpr int lo0 = L.p[Q].lo[0], lo1 = L.p[Q].lo[1], lo2 = L.p[Q].lo[2];
+    constexpr int e0 = L.p[Q].ext[0], e1 = L.p[Q].ext[1], e2 = L.p[Q].ext[2];
+    const long long N = g.ncell;
+    const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+    const typename CT<T>::type* xb = x + (long long)b * N;
+#pragma unroll
+    for (int oz = 0; oz < e2; ++oz) {
+      const int jz = i[2] + lo2 + oz;
+#pragma unroll
+      for (int oy = 0; oy < e1; ++oy) {
+        const int jy = i[1] + lo1 + oy;
+        const bool rin = (D < 3 || (jz >= 0 && jz < g.n[2])) && jy >= 0 && jy < g.n[1];
+#pragma unroll
+        for (int ox = 0; ox < e0; ++ox) {
+          const int jx = i[0] + lo0 + ox;
+          if (rin && jx >= 0 && jx < g.n[0]) {
+            const int sl = base + (oz * e1 + oy) * e0 + ox;
+            const long long cj = c + (lo2 + oz) * sz + (lo1 + oy) * sy + (lo0 + ox);
+            y = cfma(__ldg(tab + (long long)sl * N + c), __ldg(xb + cj), y);
           }
         }
       }
     }
+    row_acc<T, D, LV, Q + 1, QE>(y, g, tab, c, i, x);
   }
+}
+
+template <typename T, int D, int LV, int A>
+__device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const typename CT<T>::type* tab,
+                                                           long long c, const int i[3],
+                                                           const typename CT<T>::type* x) {
+  constexpr StencilLayout L = level_layout(D, LV);
+  typename CT<T>::type y = czero<typename CT<T>::type>();
+  row_acc<T, D, LV, L.row_first[A], L.row_first[A + 1]>(y, g, tab, c, i, x);
   return y;
 }
 
-template <typename T, int D>
-__global__ void k_st_apply(Grid g, int nrhs, StencilLayout L, const typename CT<T>::type* __restrict__ tab,
-                           const typename CT<T>::type* __restrict__ x,
-                           const typename CT<T>::type* __restrict__ b,
-                           typename CT<T>::type* __restrict__ y, int mode) {
+// Residual pass of a Galerkin-level operation: one thread per (cell, row
+// type); blockIdx.z selects the row type, so control flow is uniform across
+// a warp and the row's stencil loop is fully unrolled.  mode 0: y = A x,
+// mode 1: y = b - A x.  colour >= 0 restricts the pressure rows to cells of
+// that colour (the rows a red-black half-sweep needs).
+template <typename T, int D, int LV, int A>
+__device__ __forceinline__ void st_one_row(const Grid& g, const typename CT<T>::type* ts, long long c,
+                                           const int i[3], const typename CT<T>::type* xv,
+                                           const typename CT<T>::type* bv, typename CT<T>::type* yv,
+                                           int mode) {
   typedef typename CT<T>::type Cx;
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
-  const int item = blockIdx.y;
   const long long N = g.ncell;
-  const long long vo = (long long)item * (D + 1) * N;
-  const Cx* ts = tab + (long long)(item / nrhs) * L.nslot * N;
-  int i[3];
-  cell_coords(g, c, i);
-  for (int a = 0; a <= D; ++a) {
-    Cx r = czero<Cx>();
-    if (slot_valid(a, D, i)) {
-      r = st_row<T, D>(g, L, ts, a, c, i, x + vo);
-      if (mode) r = csub(__ldg(b + vo + (long long)a * N + c), r);
-    }
-    y[vo + (long long)a * N + c] = r;
+  Cx r = czero<Cx>();
+  if (slot_valid(A, D, i)) {
+    r = st_row_ct<T, D, LV, A>(g, ts, c, i, xv);
+    if (mode) r = csub(__ldg(bv + (long long)A * N + c), r);
   }
+  yv[(long long)A * N + c] = r;
 }
 
-template <typename T, int D>
-__global__ void k_st_vanka(Grid g, int nrhs, StencilLayout L, const typename CT<T>::type* __restrict__ tab,
-                           T wu, T wp, int colour, const typename CT<T>::type* __restrict__ b,
-                           const typename CT<T>::type* __restrict__ xi,
-                           typename CT<T>::type* __restrict__ xo) {
+template <typename T, int D, int LV>
+__global__ void __launch_bounds__(128) k_st_rows(Grid g, int nrhs, const typename CT<T>::type* __restrict__ tab,
+                                                 const typename CT<T>::type* __restrict__ x,
+                                                 const typename CT<T>::type* __restrict__ b,
+                                                 typename CT<T>::type* __restrict__ y, int mode, int colour) {
+  constexpr StencilLayout L = level_layout(D, LV);
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int a = blockIdx.z;
+  const int item = blockIdx.y;
+  int i[3];
+  cell_coords(g, c, i);
+  if (a == D && colour >= 0 && ((i[0] + i[1] + i[2]) & 1) != colour) return;
+  const long long N = g.ncell;
+  const long long vo = (long long)item * (D + 1) * N;
+  const typename CT<T>::type* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  const typename CT<T>::type* bv = mode ? b + vo : nullptr;
+  if (a == 0) st_one_row<T, D, LV, 0>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if (a == 1) st_one_row<T, D, LV, 1>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if (a == 2) st_one_row<T, D, LV, 2>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if constexpr (D == 3) st_one_row<T, D, LV, 3>(g, ts, c, i, x + vo, bv, y + vo, mode);
+}
+
+// Update pass of one colour: the economic cell block (stored diagonal and
+// displacement-pressure couplings) is solved for every cell of the colour
+// from the residual r of the residual pass; xo receives the new iterate.
+template <typename T, int D, int LV>
+__global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const typename CT<T>::type* __restrict__ tab,
+                                                 T wu, T wp, int colour,
+                                                 const typename CT<T>::type* __restrict__ res,
+                                                 const typename CT<T>::type* __restrict__ xi,
+                                                 typename CT<T>::type* __restrict__ xo) {
   typedef typename CT<T>::type Cx;
+  constexpr StencilLayout L = level_layout(D, LV);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long N = g.ncell;
   if (t >= N / 2) return;
@@ -226,7 +234,7 @@ __global__ void k_st_vanka(Grid g, int nrhs, StencilLayout L, const typename CT<
   const long long vo = (long long)item * (D + 1) * N;
   const Cx* ts = tab + (long long)(item / nrhs) * L.nslot * N;
   const Cx* x = xi + vo;
-  const Cx* bb = b + vo;
+  const Cx* rr = res + vo;
   Cx* xout = xo + vo;
   long long c = 2 * t;
   int i[3];
@@ -234,43 +242,46 @@ __global__ void k_st_vanka(Grid g, int nrhs, StencilLayout L, const typename CT<
   if (((i[0] + i[1] + i[2]) & 1) != colour) { ++c; ++i[0]; }
   const long long co = (c & 1) ? c - 1 : c + 1;
   xout[(long long)D * N + co] = __ldg(x + (long long)D * N + co);
-
   Cx r[2 * D + 1], dg[2 * D], gr[2 * D], gc_[2 * D];
   bool ok[2 * D];
+#pragma unroll
   for (int k = 0; k < D; ++k) {
     const long long sk = stride_of(g, k);
-    int o[3] = {0, 0, 0};
+    const int sd = st_slot(L, k, k, 0, 0, 0);
+    const int sg0 = st_slot(L, k, D, 0, 0, 0);
+    const int sg1 = st_slot(L, k, D, k == 0 ? -1 : 0, k == 1 ? -1 : 0, k == 2 ? -1 : 0);
+    const int sc0 = st_slot(L, D, k, 0, 0, 0);
+    const int sc1 = st_slot(L, D, k, k == 0 ? 1 : 0, k == 1 ? 1 : 0, k == 2 ? 1 : 0);
     ok[k] = i[k] >= 1;
     if (ok[k]) {
-      r[k] = csub(__ldg(bb + (long long)k * N + c), st_row<T, D>(g, L, ts, k, c, i, x));
-      dg[k] = __ldg(ts + (long long)st_slot(L, k, k, 0, 0, 0) * N + c);
-      gr[k] = __ldg(ts + (long long)st_slot(L, k, D, 0, 0, 0) * N + c);   // K[u_k(c), p(c)]
-      gc_[k] = __ldg(ts + (long long)st_slot(L, D, k, 0, 0, 0) * N + c);  // K[p(c), u_k(c)]
+      r[k] = __ldg(rr + (long long)k * N + c);
+      dg[k] = __ldg(ts + (long long)sd * N + c);
+      gr[k] = __ldg(ts + (long long)sg0 * N + c);
+      gc_[k] = __ldg(ts + (long long)sc0 * N + c);
     }
     ok[D + k] = i[k] + 1 < g.n[k];
     if (ok[D + k]) {
-      int ih[3] = {i[0], i[1], i[2]};
-      ih[k] += 1;
-      r[D + k] = csub(__ldg(bb + (long long)k * N + c + sk), st_row<T, D>(g, L, ts, k, c + sk, ih, x));
-      dg[D + k] = __ldg(ts + (long long)st_slot(L, k, k, 0, 0, 0) * N + c + sk);
-      o[k] = -1;
-      gr[D + k] = __ldg(ts + (long long)st_slot(L, k, D, o[0], o[1], o[2]) * N + c + sk);
-      o[k] = 1;
-      gc_[D + k] = __ldg(ts + (long long)st_slot(L, D, k, o[0], o[1], o[2]) * N + c);
+      r[D + k] = __ldg(rr + (long long)k * N + c + sk);
+      dg[D + k] = __ldg(ts + (long long)sd * N + c + sk);
+      gr[D + k] = __ldg(ts + (long long)sg1 * N + c + sk);
+      gc_[D + k] = __ldg(ts + (long long)sc1 * N + c);
     }
   }
-  r[2 * D] = csub(__ldg(bb + (long long)D * N + c), st_row<T, D>(g, L, ts, D, c, i, x));
+  r[2 * D] = __ldg(rr + (long long)D * N + c);
   Cx sch = __ldg(ts + (long long)st_slot(L, D, D, 0, 0, 0) * N + c);
   Cx rp = r[2 * D];
   Cx dinv[2 * D];
+#pragma unroll
   for (int a = 0; a < 2 * D; ++a) {
     if (!ok[a]) continue;
     dinv[a] = cinv(dg[a]);
-    sch = csub(sch, cmul(cmul(gc_[a], dinv[a]), gr[a]));
-    rp = csub(rp, cmul(cmul(gc_[a], dinv[a]), r[a]));
+    const Cx gd = cmul(gc_[a], dinv[a]);
+    sch = csub(sch, cmul(gd, gr[a]));
+    rp = csub(rp, cmul(gd, r[a]));
   }
   const Cx dp = cmul(rp, cinv(sch));
   xout[(long long)D * N + c] = cfma(mk<T>(wp, 0), dp, __ldg(x + (long long)D * N + c));
+#pragma unroll
   for (int a = 0; a < 2 * D; ++a) {
     if (!ok[a]) continue;
     const int k = a % D;
@@ -306,26 +317,61 @@ void launch_table_cast(long long n, const double2* in, typename CT<T>::type* out
   k_table_cast<typename CT<T>::type><<<grid1(n, 1, 256), 256, 0, s>>>(n, in, out);
 }
 
+// which compile-time layout variant a runtime layout is (1 or 2)
+static int layout_variant(const StencilLayout& L, int d) {
+  if (d == 2) {
+    if (same_layout(L, level_layout(2, 1))) return 1;
+    if (same_layout(L, level_layout(2, 2))) return 2;
+  } else {
+    if (same_layout(L, level_layout(3, 1))) return 1;
+    if (same_layout(L, level_layout(3, 2))) return 2;
+  }
+  throw std::runtime_error("unexpected Galerkin stencil layout");
+}
+
 template <typename T>
 void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* tab, const typename CT<T>::type* x,
                      const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
                      cudaStream_t s) {
-  if (g.d == 2)
-    k_st_apply<T, 2><<<grid1(g.ncell, items, 128), 128, 0, s>>>(g, nrhs, L, tab, x, b, y, mode);
-  else
-    k_st_apply<T, 3><<<grid1(g.ncell, items, 128), 128, 0, s>>>(g, nrhs, L, tab, x, b, y, mode);
+  const dim3 gr((unsigned)((g.ncell + 127) / 128), items, g.d + 1);
+  const int v = layout_variant(L, g.d);
+  if (g.d == 2) {
+    if (v == 1) k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
+    else k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
+  } else {
+    if (v == 1) k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
+    else k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
+  }
 }
 
+// one colour of red-black economic Vanka on a Galerkin level: residual pass
+// into rbuf (u rows of every cell, p rows of the colour), then the update pass
 template <typename T>
 void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* tab, T wu, T wp, int colour,
                      const typename CT<T>::type* b, const typename CT<T>::type* xi,
-                     typename CT<T>::type* xo, cudaStream_t s) {
-  if (g.d == 2)
-    k_st_vanka<T, 2><<<grid1(g.ncell / 2, items, 128), 128, 0, s>>>(g, nrhs, L, tab, wu, wp, colour, b, xi, xo);
-  else
-    k_st_vanka<T, 3><<<grid1(g.ncell / 2, items, 128), 128, 0, s>>>(g, nrhs, L, tab, wu, wp, colour, b, xi, xo);
+                     typename CT<T>::type* xo, typename CT<T>::type* rbuf, cudaStream_t s) {
+  const dim3 gr((unsigned)((g.ncell + 127) / 128), items, g.d + 1);
+  const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), items, 1);
+  const int v = layout_variant(L, g.d);
+  if (g.d == 2) {
+    if (v == 1) {
+      k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
+      k_st_vupd<T, 2, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+    } else {
+      k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
+      k_st_vupd<T, 2, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+    }
+  } else {
+    if (v == 1) {
+      k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
+      k_st_vupd<T, 3, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+    } else {
+      k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
+      k_st_vupd<T, 3, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+    }
+  }
 }
 
 #define INST(T)                                                                                   \
@@ -335,7 +381,7 @@ void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
                                    cudaStream_t);                                                   \
   template void launch_st_vanka<T>(const Grid&, int, int, const StencilLayout&, const CT<T>::type*, \
                                    T, T, int, const CT<T>::type*, const CT<T>::type*, CT<T>::type*, \
-                                   cudaStream_t);
+                                   CT<T>::type*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -2,7 +2,7 @@
 // steps 2 and 4) with the bilinear staggered-grid transfer of Sec. 3: per
 // component a tensor product of 1D rules (vertex-like along the component's
 // own direction, cell-like with zero ghosts across it, cell-like with clamped
-// ghosts for p).  The 1D weights come from pw() in common.cuh.
+// ghosts for p).  The 1D weights come from pw4() in common.cuh (exact quarters).
 #include "kernels.h"
 
 namespace ehs {
@@ -31,8 +31,8 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename CT<T>::type* __restr
         int n = 0;
         const int kind = tkind(a, k, D);
         for (int i = 2 * I[k] - 1; i <= 2 * I[k] + 2; ++i) {
-          const double v = pw(kind, i, I[k], gc.n[k]);
-          if (v != 0.0) { fi[k][n] = i; fw[k][n] = (T)v; ++n; }
+          const int v = pw4(kind, i, I[k], gc.n[k]);
+          if (v != 0) { fi[k][n] = i; fw[k][n] = T(0.25) * (T)v; ++n; }
         }
         nf[k] = n;
       }
@@ -71,8 +71,8 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const typename CT<T>::type* __re
       int n = 0;
       const int kind = tkind(a, k, D);
       for (int J = (i[k] >> 1) - 1; J <= (i[k] >> 1) + 1; ++J) {
-        const double v = pw(kind, i[k], J, gc.n[k]);
-        if (v != 0.0) { ci[k][n] = J; cw[k][n] = (T)v; ++n; }
+        const int v = pw4(kind, i[k], J, gc.n[k]);
+        if (v != 0) { ci[k][n] = J; cw[k][n] = T(0.25) * (T)v; ++n; }
       }
       nc[k] = n;
     }

@@ -56,11 +56,12 @@ void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* tab, const typename CT<T>::type* x,
                      const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
                      cudaStream_t s);
+// one colour of red-black Vanka on a Galerkin level; rbuf: residual scratch of x's size
 template <typename T>
 void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* tab, T wu, T wp, int colour,
                      const typename CT<T>::type* b, const typename CT<T>::type* xi,
-                     typename CT<T>::type* xo, cudaStream_t s);
+                     typename CT<T>::type* xo, typename CT<T>::type* rbuf, cudaStream_t s);
 
 // ---- transfer -------------------------------------------------------------
 template <typename T>
@@ -102,5 +103,30 @@ void launch_scale_inv(long long n, int items, const double2* w, const double* nr
 template <typename CZ>
 void launch_xupdate(long long n, int items, int m, const CZ* Z, const double2* y /*[items][m]*/,
                     const int* kused, double2* x, cudaStream_t s);
+
+// ---- FP64-class (double-float) Krylov, operator and coarsest ----------------
+// complex df64 = float4 {re.hi, re.lo, im.hi, im.lo}; real df64 = float2 {hi, lo}
+void launch_mdot_df(long long n, int items, int nv, const float4* V, const float4* w, float4* part,
+                    int nblk, cudaStream_t s);
+void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
+                       float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s);
+void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s);
+// out (df64, device use) and outd (double copy for the host)
+void launch_reduce_parts_df(int items, int nv, int nblk, const float4* part, float4* out, double2* outd,
+                            cudaStream_t s);
+// out = norm (double), inv = 1/norm (df64; may be null)
+void launch_reduce_norm_df(int items, int nblk, const float2* part, double* out, float2* inv, cudaStream_t s);
+void launch_scale_df(long long n, int items, const float4* w, const float2* inv, float4* out, cudaStream_t s);
+void launch_xupdate_df(long long n, int items, int m, const float2* Z, const float4* y, const int* kused,
+                       float4* x, cudaStream_t s);
+void launch_d2_to_df(long long n, const double2* in, float4* out, cudaStream_t s);
+void launch_df_to_d2(long long n, const float4* in, double2* out, cudaStream_t s);
+void launch_df_to_f2(long long n, const float4* in, float2* out, cudaStream_t s);
+void launch_coef_df(long long n, const Coef4<double>* in, void* out /*Coef4df*/, cudaStream_t s);
+// y = K x (mode 0) or b - K x (mode 1); x complex64 (x_is_c64) or complex df64
+void launch_fine_apply_df(const Grid& g, int items, int nrhs, const void* cf, double h, double alpha,
+                          const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s);
+void launch_dense_apply_df(int N, int items, int nrhs, const float4* inv, const float2* r, float2* x,
+                           cudaStream_t s);
 
 }  // namespace ehs

@@ -286,3 +286,37 @@ def test_noconv_reports_best_iterate():
     assert info["iters"] == 3 and not info["converged"]
     assert 0 < info["relres"] < 1
     S.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_wcycle_matches_oracle(case):
+    ehs = _ehs()
+    meds = _media_2d(64, 2) if case == "2d" else _media_3d(16, 1)
+    levels = 4 if case == "2d" else 3
+    S = ehs.solver_for(meds, levels=levels, alpha=0.4, cycle=2)
+    shape = meds[0].shape
+    b_ = _rand_slots(shape, S.items, 15)
+    for dt, tol in ((torch.complex128, 1e-10), (torch.complex64, 5e-5)):
+        bd = torch.from_numpy(b_).to("cuda", dt)
+        xd = torch.zeros_like(bd)
+        S.vcycle(bd, xd)
+        for it, med in enumerate(meds):
+            H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, levels,
+                             w=[0.75, 0.5, 0.25][:levels - 1])
+            xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape), gamma=2), shape)
+            assert _rel(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _rel(xd[it].cpu().numpy(), xr))
+    S.close()
+
+
+def test_fgmres_wcycle_iterations_match_oracle():
+    ehs = _ehs()
+    meds = _media_2d(64, 2)
+    q, u, info = _solve_both(meds, 4, ehs.EHS_C128, alpha=0.4, cycle=2)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25])
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
