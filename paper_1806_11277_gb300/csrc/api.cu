@@ -17,6 +17,7 @@
 
 namespace ehs {
 std::atomic<long long> g_launches{0};
+thread_local ItemSel g_sel;
 }
 
 using namespace ehs;
@@ -69,6 +70,8 @@ struct Hier {
 
 struct DDGroup {          // subdomains of one colour that share one shape
   Hier H;
+  int* d_sub_act = nullptr;  // active sub-items (derived from the active global items)
+  int nsub_act = 0;
   int nsub = 0;
   std::vector<int> subs;  // global subdomain ids
   int* d_map = nullptr;   // [nsub][ncell_local] -> global cell index or -1 (outside Omega_i)
@@ -107,6 +110,11 @@ struct ehs_ctx {
   cudaStream_t cap = nullptr;
   std::vector<cudaGraphExec_t> pg;
   std::vector<long long> pg_nodes;
+  std::vector<int> pg_ver;
+  // active items of the current Arnoldi step (batch compaction)
+  int* d_act = nullptr;
+  std::vector<int> act;      // host copy; empty = all items
+  int act_ver = 0;
   std::string err;
 };
 
@@ -312,6 +320,47 @@ void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* 
 
 }  // namespace
 
+namespace {
+
+// Sets the active item list from the Arnoldi state (no list when every item
+// is active) and derives the DD sub-item lists; bumps the graph version when
+// the set changes.
+void set_active(ehs_ctx* c, const std::vector<int>& active) {
+  std::vector<int> list;
+  for (int b = 0; b < (int)active.size(); ++b)
+    if (active[b]) list.push_back(b);
+  if ((int)list.size() == (int)active.size()) list.clear();
+  if (list == c->act) return;
+  c->act = list;
+  ++c->act_ver;
+  if (list.empty()) return;
+  CK(cudaMemcpyAsync(c->d_act, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+  const int nrhs = c->H.nrhs;
+  for (int col = 0; col < 8; ++col)
+    for (DDGroup& grp : c->dd[col]) {
+      std::vector<int> sl;
+      for (int b : list) {
+        const int m = b / nrhs, r = b % nrhs;
+        for (int sdx = 0; sdx < grp.nsub; ++sdx) sl.push_back((m * grp.nsub + sdx) * nrhs + r);
+      }
+      grp.nsub_act = (int)sl.size();
+      CK(cudaMemcpyAsync(grp.d_sub_act, sl.data(), sl.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    }
+  CK(cudaStreamSynchronize(c->s));   // the host lists above are temporaries
+}
+
+// Installs the active item list (or none) for the launches in its scope.
+struct SelScope {
+  ItemSel old;
+  SelScope(const int* list, int n) : old(g_sel) { g_sel.list = list; g_sel.n = n; }
+  ~SelScope() { g_sel = old; }
+};
+inline SelScope global_sel(ehs_ctx* c) {
+  return c->act.empty() ? SelScope(nullptr, 0) : SelScope(c->d_act, (int)c->act.size());
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------- DD
 #include "dd_impl.inc"
 
@@ -447,6 +496,10 @@ void sync_read(ehs_ctx* c, void* host, const void* dev, size_t bytes) {
 // from a CUDA graph captured on the first call for slot j.
 template <typename F> void graphed(ehs_ctx* c, int j, F body) {
   if (!c->use_graphs) { body(); return; }
+  if (c->pg[j] && c->pg_ver[j] != c->act_ver) {   // the active item set changed
+    cudaGraphExecDestroy(c->pg[j]);
+    c->pg[j] = nullptr;
+  }
   if (!c->pg[j]) {
     cudaStream_t user = c->s;
     const long long l0 = g_launches.load();
@@ -468,6 +521,7 @@ template <typename F> void graphed(ehs_ctx* c, int j, F body) {
     cudaGraphDestroy(graph);
     CK(e);
     c->pg[j] = ex;
+    c->pg_ver[j] = c->act_ver;
     c->pg_nodes[j] = g_launches.load() - l0;
     g_launches -= c->pg_nodes[j];          // counted when replayed
   }
@@ -546,12 +600,16 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
   std::vector<double2> h1((size_t)items * (m + 1)), h2((size_t)items * (m + 1)), yh;
   std::vector<double> hn(items);
   while (!A.all_done() && !A.maxed()) {
-    // V_0 = r / beta (invq holds 1/||r|| from the last norm)
-    launch_scale_df(n, items, c->rq, c->invq, c->Vq, s); cnt(); post();
     A.start_cycle();
+    set_active(c, A.active);
+    {  // V_0 = r / beta (invq holds 1/||r|| from the last norm)
+      SelScope sel = global_sel(c);
+      launch_scale_df(n, items, c->rq, c->invq, c->Vq, s); cnt(); post();
+    }
     for (int j = 0; j < m; ++j) {
       float4* Vj = c->Vq + (size_t)j * items * n;
       float2* Zj = c->Zf + (size_t)j * items * n;
+      SelScope sel = global_sel(c);      // only the items still iterating
       graphed(c, j, [&]() {
         launch_df_to_f2(nall, Vj, c->f_in, c->s); cnt(); post();
         if (c->opt.precond == EHS_PRECOND_DD) dd_apply_t<float>(c, c->f_in, Zj);
@@ -571,6 +629,8 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
                          cudaMemcpyDeviceToHost, s));
       sync_read(c, hn.data(), c->nrm, items * sizeof(double));
       if (!A.step(j, h1.data(), h2.data(), hn.data())) break;
+      set_active(c, A.active);
+      SelScope sel2 = global_sel(c);
       launch_scale_df(n, items, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n, s); cnt(); post();
     }
     A.solve_y(yh);
@@ -746,6 +806,10 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     c->pg.assign(m, nullptr);
     c->pg_nodes.assign(m, 0);
+    c->pg_ver.assign(m, -1);
+    c->d_act = dalloc<int>(c, items);
+    for (int col = 0; col < 8; ++col)
+      for (DDGroup& grp : c->dd[col]) grp.d_sub_act = dalloc<int>(c, grp.H.items);
     const char* ng = getenv("EHS_NO_GRAPHS");
     c->use_graphs = !(ng && ng[0] == '1');
     CK(cudaStreamSynchronize(c->s));

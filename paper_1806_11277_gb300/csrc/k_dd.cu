@@ -10,10 +10,10 @@ namespace {
 
 template <typename C>
 __global__ void k_dd_gather(long long nl, int nsub, int nrhs, long long ng, const int* __restrict__ map,
-                            const C* __restrict__ res, C* __restrict__ out) {
+                            const C* __restrict__ res, C* __restrict__ out, const int* __restrict__ il) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nl) return;
-  const int bl = blockIdx.y;
+  const int bl = il ? il[blockIdx.y] : blockIdx.y;
   const int r = bl % nrhs, s = (bl / nrhs) % nsub, m = bl / (nrhs * nsub);
   const int gs = map[(long long)s * nl + e];
   C v; v.x = 0; v.y = 0;
@@ -23,10 +23,10 @@ __global__ void k_dd_gather(long long nl, int nsub, int nrhs, long long ng, cons
 
 template <typename C>
 __global__ void k_dd_scatter(long long nl, int nsub, int nrhs, long long ng, const int* __restrict__ map,
-                             const C* __restrict__ xs, C* __restrict__ x) {
+                             const C* __restrict__ xs, C* __restrict__ x, const int* __restrict__ il) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nl) return;
-  const int bl = blockIdx.y;
+  const int bl = il ? il[blockIdx.y] : blockIdx.y;
   const int r = bl % nrhs, s = (bl / nrhs) % nsub, m = bl / (nrhs * nsub);
   const int gs = map[(long long)s * nl + e];
   if (gs < 0) return;
@@ -41,12 +41,14 @@ __global__ void k_dd_scatter(long long nl, int nsub, int nrhs, long long ng, con
 template <typename T>
 void launch_dd_gather(long long nl, int items_l, int nsub, int nrhs, long long ng, const int* map,
                       const typename CT<T>::type* res, typename CT<T>::type* out, cudaStream_t s) {
-  k_dd_gather<<<dim3((unsigned)((nl + 255) / 256), items_l), 256, 0, s>>>(nl, nsub, nrhs, ng, map, res, out);
+  k_dd_gather<<<dim3((unsigned)((nl + 255) / 256), sel_items(items_l)), 256, 0, s>>>(nl, nsub, nrhs, ng, map, res, out,
+                                                                                   g_sel.list);
 }
 template <typename T>
 void launch_dd_scatter(long long nl, int items_l, int nsub, int nrhs, long long ng, const int* map,
                        const typename CT<T>::type* xs, typename CT<T>::type* x, cudaStream_t s) {
-  k_dd_scatter<<<dim3((unsigned)((nl + 255) / 256), items_l), 256, 0, s>>>(nl, nsub, nrhs, ng, map, xs, x);
+  k_dd_scatter<<<dim3((unsigned)((nl + 255) / 256), sel_items(items_l)), 256, 0, s>>>(nl, nsub, nrhs, ng, map, xs, x,
+                                                                                    g_sel.list);
 }
 template void launch_dd_gather<float>(long long, int, int, int, long long, const int*, const float2*, float2*, cudaStream_t);
 template void launch_dd_gather<double>(long long, int, int, int, long long, const int*, const double2*, double2*, cudaStream_t);

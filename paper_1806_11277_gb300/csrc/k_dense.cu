@@ -121,10 +121,10 @@ __global__ void k_gj_extract(int N, const double2* __restrict__ M, double2* __re
 template <typename T>
 __global__ void k_dense_apply(int N, int nrhs, const double2* __restrict__ inv,
                               const typename CT<T>::type* __restrict__ r,
-                              typename CT<T>::type* __restrict__ x) {
+                              typename CT<T>::type* __restrict__ x, const int* __restrict__ il) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   if (warp >= N) return;
   const double2* row = inv + ((long long)(item / nrhs) * N + warp) * N;
   const typename CT<T>::type* rv = r + (long long)item * N;
@@ -172,8 +172,8 @@ template <typename T>
 void launch_dense_apply(int N, int items, int nrhs, const double2* inv, const typename CT<T>::type* r,
                         typename CT<T>::type* x, cudaStream_t s) {
   const int wpb = 8;
-  dim3 grid((N + wpb - 1) / wpb, items);
-  k_dense_apply<T><<<grid, 32 * wpb, 0, s>>>(N, nrhs, inv, r, x);
+  dim3 grid((N + wpb - 1) / wpb, sel_items(items));
+  k_dense_apply<T><<<grid, 32 * wpb, 0, s>>>(N, nrhs, inv, r, x, g_sel.list);
 }
 
 template void launch_dense_apply<float>(int, int, int, const double2*, const float2*, float2*, cudaStream_t);

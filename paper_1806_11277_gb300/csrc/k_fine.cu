@@ -94,11 +94,11 @@ template <typename T, int D>
 __global__ void k_fine_apply(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, FineP<T> P,
                              const typename CT<T>::type* __restrict__ x,
                              const typename CT<T>::type* __restrict__ b,
-                             typename CT<T>::type* __restrict__ y, int mode) {
+                             typename CT<T>::type* __restrict__ y, int mode, const int* __restrict__ il) {
   typedef typename CT<T>::type C;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long N = g.ncell;
   const long long vo = (long long)item * (D + 1) * N;
   const Coef4<T>* cs = cf + (long long)(item / nrhs) * N;
@@ -128,12 +128,12 @@ template <typename T, int D>
 __global__ void k_fine_vanka(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, FineP<T> P,
                              T wu, T wp, int colour, const typename CT<T>::type* __restrict__ b,
                              const typename CT<T>::type* __restrict__ xi,
-                             typename CT<T>::type* __restrict__ xo) {
+                             typename CT<T>::type* __restrict__ xo, const int* __restrict__ il) {
   typedef typename CT<T>::type C;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long npair = g.ncell >> 1;
   if (t >= npair) return;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long N = g.ncell;
   const long long vo = (long long)item * (D + 1) * N;
   const Coef4<T>* cs = cf + (long long)(item / nrhs) * N;
@@ -367,10 +367,11 @@ void launch_fine_apply(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
                        const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
                        cudaStream_t s) {
   const FineP<T> P = mkP<T>(h, alpha);
+  const dim3 gr((unsigned)((g.ncell + 255) / 256), sel_items(items));
   if (g.d == 2)
-    k_fine_apply<T, 2><<<grid1(g.ncell, items, 256), 256, 0, s>>>(g, nrhs, cf, P, x, b, y, mode);
+    k_fine_apply<T, 2><<<gr, 256, 0, s>>>(g, nrhs, cf, P, x, b, y, mode, g_sel.list);
   else
-    k_fine_apply<T, 3><<<grid1(g.ncell, items, 256), 256, 0, s>>>(g, nrhs, cf, P, x, b, y, mode);
+    k_fine_apply<T, 3><<<gr, 256, 0, s>>>(g, nrhs, cf, P, x, b, y, mode, g_sel.list);
 }
 
 template <typename T>
@@ -380,10 +381,11 @@ void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
                        typename CT<T>::type* xo, cudaStream_t s) {
   const FineP<T> P = mkP<T>(h, alpha);
   const long long np = g.ncell / 2;
+  const dim3 gr((unsigned)((np + 127) / 128), sel_items(items));
   if (g.d == 2)
-    k_fine_vanka<T, 2><<<grid1(np, items, 128), 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo);
+    k_fine_vanka<T, 2><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
   else
-    k_fine_vanka<T, 3><<<grid1(np, items, 128), 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo);
+    k_fine_vanka<T, 3><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
 }
 
 void fine_table_layout(int d, StencilLayout* L) { *L = make_fine_layout(d); }

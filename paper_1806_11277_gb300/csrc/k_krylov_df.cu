@@ -64,8 +64,8 @@ __device__ __forceinline__ void block_store_norm(dfr v, float2* part, int item, 
 
 template <int NV>
 __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const float4* __restrict__ V,
-                                                const float4* __restrict__ w, float4* part, int nblk) {
-  const int item = blockIdx.y;
+                                                const float4* __restrict__ w, float4* part, int nblk, const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   dfc acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = dfc_zero();
@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const fl
 template <int NV>
 __global__ void __launch_bounds__(KB) k_mupdate_df(long long n, int items, const float4* __restrict__ V,
                                                    const float4* __restrict__ h, float4* __restrict__ w,
-                                                   float4* part, int nblk, int dot, float2* nrm_part) {
-  const int item = blockIdx.y;
+                                                   float4* part, int nblk, int dot, float2* nrm_part, const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   dfc hh[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) hh[i] = dfc_ld(h + (long long)item * NV + i);
@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(KB) k_mupdate_df(long long n, int items, const
   if (nrm_part) block_store_norm(nacc, nrm_part, item, nblk);
 }
 
-__global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2* part, int nblk) {
-  const int item = blockIdx.y;
+__global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2* part, int nblk, const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const float4* wv = w + (long long)item * n;
   dfr nacc = df_zero();
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
@@ -125,10 +125,11 @@ __global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2
 
 // one warp per output; writes the df64 value and its double copy for the host
 __global__ void k_reduce_parts_df(int nout, int nblk, const float4* __restrict__ part, float4* out,
-                                  double2* outd) {
-  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                  double2* outd, int nv, const int* __restrict__ il) {
+  const int oo = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (o >= nout) return;
+  if (oo >= nout) return;
+  const int o = il ? il[oo / nv] * nv + oo % nv : oo;
   dfc s = dfc_zero();
   for (int b = lane; b < nblk; b += 32) s = dfc_add(s, dfc_ld(part + (long long)o * nblk + b));
   s = warp_sum_df(s);
@@ -139,10 +140,11 @@ __global__ void k_reduce_parts_df(int nout, int nblk, const float4* __restrict__
 }
 // norm = sqrt(sum); writes the double norm for the host and 1/norm in df64
 __global__ void k_reduce_norm_df(int items, int nblk, const float2* __restrict__ part, double* out,
-                                 float2* inv) {
-  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                 float2* inv, const int* __restrict__ il) {
+  const int oo = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (o >= items) return;
+  if (oo >= items) return;
+  const int o = il ? il[oo] : oo;
   dfr s = df_zero();
   for (int b = lane; b < nblk; b += 32) {
     const float2 v = part[(long long)o * nblk + b];
@@ -158,8 +160,8 @@ __global__ void k_reduce_norm_df(int items, int nblk, const float2* __restrict__
 }
 
 __global__ void k_scale_df(long long n, const float4* __restrict__ w, const float2* __restrict__ inv,
-                           float4* __restrict__ out) {
-  const int item = blockIdx.y;
+                           float4* __restrict__ out, const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const float2 s = inv[item];
@@ -267,10 +269,10 @@ __device__ __forceinline__ dfc row_p_df(const Grid& g, long long c, const int i[
 template <typename V, int D>
 __global__ void k_fine_apply_df(Grid g, int nrhs, const Coef4df* __restrict__ cf, FinePdf P,
                                 const V* __restrict__ x, const float4* __restrict__ b,
-                                float4* __restrict__ y, int mode) {
+                                float4* __restrict__ y, int mode, const int* __restrict__ il) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long N = g.ncell;
   const long long vo = (long long)item * (D + 1) * N;
   const Coef4df* cs = cf + (long long)(item / nrhs) * N;
@@ -293,10 +295,11 @@ __global__ void k_fine_apply_df(Grid g, int nrhs, const Coef4df* __restrict__ cf
 
 // coarsest: x = Ainv r with Ainv in complex df64, r and x complex64; one warp per row
 __global__ void k_dense_apply_df(int N, int nrhs, const float4* __restrict__ inv,
-                                 const float2* __restrict__ r, float2* __restrict__ x) {
+                                 const float2* __restrict__ r, float2* __restrict__ x,
+                                 const int* __restrict__ il) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   if (warp >= N) return;
   const float4* row = inv + ((long long)(item / nrhs) * N + warp) * N;
   const float2* rv = r + (long long)item * N;
@@ -327,9 +330,9 @@ FinePdf mkPdf(double h, double alpha) {
 #define EHS_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
 void launch_mdot_df(long long n, int items, int nv, const float4* V, const float4* w, float4* part,
                     int nblk, cudaStream_t s) {
-  const dim3 g(nblk, items);
+  const dim3 g(nblk, sel_items(items));
   switch (nv) {
-#define X(k) case k: k_mdot_df<k><<<g, KB, 0, s>>>(n, items, V, w, part, nblk); break;
+#define X(k) case k: k_mdot_df<k><<<g, KB, 0, s>>>(n, items, V, w, part, nblk, g_sel.list); break;
     EHS_NV_CASES(X)
 #undef X
     default: break;
@@ -337,27 +340,28 @@ void launch_mdot_df(long long n, int items, int nv, const float4* V, const float
 }
 void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
                        float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s) {
-  const dim3 g(nblk, items);
+  const dim3 g(nblk, sel_items(items));
   switch (nv) {
-#define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part); break;
+#define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part, g_sel.list); break;
     EHS_NV_CASES(X)
 #undef X
     default: break;
   }
 }
 void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s) {
-  k_norm_part_df<<<dim3(nblk, items), KB, 0, s>>>(n, w, part, nblk);
+  k_norm_part_df<<<dim3(nblk, sel_items(items)), KB, 0, s>>>(n, w, part, nblk, g_sel.list);
 }
 void launch_reduce_parts_df(int items, int nv, int nblk, const float4* part, float4* out, double2* outd,
                             cudaStream_t s) {
-  const int nout = items * nv;
-  k_reduce_parts_df<<<nb((long long)nout * 32, 128), 128, 0, s>>>(nout, nblk, part, out, outd);
+  const int nout = (int)sel_items(items) * nv;
+  k_reduce_parts_df<<<nb((long long)nout * 32, 128), 128, 0, s>>>(nout, nblk, part, out, outd, nv, g_sel.list);
 }
 void launch_reduce_norm_df(int items, int nblk, const float2* part, double* out, float2* inv, cudaStream_t s) {
-  k_reduce_norm_df<<<nb((long long)items * 32, 128), 128, 0, s>>>(items, nblk, part, out, inv);
+  const int ni = (int)sel_items(items);
+  k_reduce_norm_df<<<nb((long long)ni * 32, 128), 128, 0, s>>>(ni, nblk, part, out, inv, g_sel.list);
 }
 void launch_scale_df(long long n, int items, const float4* w, const float2* inv, float4* out, cudaStream_t s) {
-  k_scale_df<<<dim3(nb(n, 256), items), 256, 0, s>>>(n, w, inv, out);
+  k_scale_df<<<dim3(nb(n, 256), sel_items(items)), 256, 0, s>>>(n, w, inv, out, g_sel.list);
 }
 void launch_xupdate_df(long long n, int items, int m, const float2* Z, const float4* y, const int* kused,
                        float4* x, cudaStream_t s) {
@@ -378,20 +382,20 @@ void launch_coef_df(long long n, const Coef4<double>* in, void* out, cudaStream_
 void launch_fine_apply_df(const Grid& g, int items, int nrhs, const void* cf, double h, double alpha,
                           const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s) {
   const FinePdf P = mkPdf(h, alpha);
-  const dim3 grid(nb(g.ncell, 128), items);
+  const dim3 grid(nb(g.ncell, 128), sel_items(items));
   const Coef4df* c = (const Coef4df*)cf;
   if (g.d == 2) {
-    if (x_is_c64) k_fine_apply_df<float2, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode);
-    else k_fine_apply_df<float4, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode);
+    if (x_is_c64) k_fine_apply_df<float2, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode, g_sel.list);
+    else k_fine_apply_df<float4, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode, g_sel.list);
   } else {
-    if (x_is_c64) k_fine_apply_df<float2, 3><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode);
-    else k_fine_apply_df<float4, 3><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode);
+    if (x_is_c64) k_fine_apply_df<float2, 3><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode, g_sel.list);
+    else k_fine_apply_df<float4, 3><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode, g_sel.list);
   }
 }
 void launch_dense_apply_df(int N, int items, int nrhs, const float4* inv, const float2* r, float2* x,
                            cudaStream_t s) {
   const int wpb = 8;
-  k_dense_apply_df<<<dim3((N + wpb - 1) / wpb, items), 32 * wpb, 0, s>>>(N, nrhs, inv, r, x);
+  k_dense_apply_df<<<dim3((N + wpb - 1) / wpb, sel_items(items)), 32 * wpb, 0, s>>>(N, nrhs, inv, r, x, g_sel.list);
 }
 
 }  // namespace ehs

@@ -197,12 +197,13 @@ template <typename T, int D, int LV>
 __global__ void __launch_bounds__(128) k_st_rows(Grid g, int nrhs, const typename CT<T>::type* __restrict__ tab,
                                                  const typename CT<T>::type* __restrict__ x,
                                                  const typename CT<T>::type* __restrict__ b,
-                                                 typename CT<T>::type* __restrict__ y, int mode, int colour) {
+                                                 typename CT<T>::type* __restrict__ y, int mode, int colour,
+                                                 const int* __restrict__ il) {
   constexpr StencilLayout L = level_layout(D, LV);
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const int a = blockIdx.z;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   int i[3];
   cell_coords(g, c, i);
   if (a == D && colour >= 0 && ((i[0] + i[1] + i[2]) & 1) != colour) return;
@@ -224,13 +225,14 @@ __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const typenam
                                                  T wu, T wp, int colour,
                                                  const typename CT<T>::type* __restrict__ res,
                                                  const typename CT<T>::type* __restrict__ xi,
-                                                 typename CT<T>::type* __restrict__ xo) {
+                                                 typename CT<T>::type* __restrict__ xo,
+                                                 const int* __restrict__ il) {
   typedef typename CT<T>::type Cx;
   constexpr StencilLayout L = level_layout(D, LV);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long N = g.ncell;
   if (t >= N / 2) return;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long vo = (long long)item * (D + 1) * N;
   const Cx* ts = tab + (long long)(item / nrhs) * L.nslot * N;
   const Cx* x = xi + vo;
@@ -334,14 +336,14 @@ void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* tab, const typename CT<T>::type* x,
                      const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
                      cudaStream_t s) {
-  const dim3 gr((unsigned)((g.ncell + 127) / 128), items, g.d + 1);
+  const dim3 gr((unsigned)((g.ncell + 127) / 128), sel_items(items), g.d + 1);
   const int v = layout_variant(L, g.d);
   if (g.d == 2) {
-    if (v == 1) k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
-    else k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
+    if (v == 1) k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
+    else k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
   } else {
-    if (v == 1) k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
-    else k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1);
+    if (v == 1) k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
+    else k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
   }
 }
 
@@ -352,24 +354,24 @@ void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* tab, T wu, T wp, int colour,
                      const typename CT<T>::type* b, const typename CT<T>::type* xi,
                      typename CT<T>::type* xo, typename CT<T>::type* rbuf, cudaStream_t s) {
-  const dim3 gr((unsigned)((g.ncell + 127) / 128), items, g.d + 1);
-  const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), items, 1);
+  const dim3 gr((unsigned)((g.ncell + 127) / 128), sel_items(items), g.d + 1);
+  const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), sel_items(items), 1);
   const int v = layout_variant(L, g.d);
   if (g.d == 2) {
     if (v == 1) {
-      k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
-      k_st_vupd<T, 2, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+      k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
+      k_st_vupd<T, 2, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
     } else {
-      k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
-      k_st_vupd<T, 2, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+      k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
+      k_st_vupd<T, 2, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
     }
   } else {
     if (v == 1) {
-      k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
-      k_st_vupd<T, 3, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+      k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
+      k_st_vupd<T, 3, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
     } else {
-      k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour);
-      k_st_vupd<T, 3, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo);
+      k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
+      k_st_vupd<T, 3, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
     }
   }
 }

@@ -10,11 +10,11 @@ namespace {
 
 template <typename T, int D>
 __global__ void k_restrict(Grid gf, Grid gc, const typename CT<T>::type* __restrict__ rf,
-                           typename CT<T>::type* __restrict__ rc) {
+                           typename CT<T>::type* __restrict__ rc, const int* __restrict__ il) {
   typedef typename CT<T>::type C;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= gc.ncell) return;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const C* f = rf + (long long)item * (D + 1) * gf.ncell;
   C* o = rc + (long long)item * (D + 1) * gc.ncell;
   int I[3];
@@ -51,11 +51,11 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename CT<T>::type* __restr
 
 template <typename T, int D>
 __global__ void k_prolong_add(Grid gf, Grid gc, const typename CT<T>::type* __restrict__ ec,
-                              typename CT<T>::type* __restrict__ xf) {
+                              typename CT<T>::type* __restrict__ xf, const int* __restrict__ il) {
   typedef typename CT<T>::type C;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= gf.ncell) return;
-  const int item = blockIdx.y;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
   const C* e = ec + (long long)item * (D + 1) * gc.ncell;
   C* x = xf + (long long)item * (D + 1) * gf.ncell;
   int i[3];
@@ -98,18 +98,18 @@ template <typename T>
 void launch_restrict(const Grid& gf, const Grid& gc, int items, const typename CT<T>::type* rf,
                      typename CT<T>::type* rc, cudaStream_t s) {
   if (gf.d == 2)
-    k_restrict<T, 2><<<grid1(gc.ncell, items, 128), 128, 0, s>>>(gf, gc, rf, rc);
+    k_restrict<T, 2><<<grid1(gc.ncell, sel_items(items), 128), 128, 0, s>>>(gf, gc, rf, rc, g_sel.list);
   else
-    k_restrict<T, 3><<<grid1(gc.ncell, items, 128), 128, 0, s>>>(gf, gc, rf, rc);
+    k_restrict<T, 3><<<grid1(gc.ncell, sel_items(items), 128), 128, 0, s>>>(gf, gc, rf, rc, g_sel.list);
 }
 
 template <typename T>
 void launch_prolong_add(const Grid& gf, const Grid& gc, int items, const typename CT<T>::type* ec,
                         typename CT<T>::type* xf, cudaStream_t s) {
   if (gf.d == 2)
-    k_prolong_add<T, 2><<<grid1(gf.ncell, items, 256), 256, 0, s>>>(gf, gc, ec, xf);
+    k_prolong_add<T, 2><<<grid1(gf.ncell, sel_items(items), 256), 256, 0, s>>>(gf, gc, ec, xf, g_sel.list);
   else
-    k_prolong_add<T, 3><<<grid1(gf.ncell, items, 256), 256, 0, s>>>(gf, gc, ec, xf);
+    k_prolong_add<T, 3><<<grid1(gf.ncell, sel_items(items), 256), 256, 0, s>>>(gf, gc, ec, xf, g_sel.list);
 }
 
 #define INST(T)                                                                                 \

@@ -7,6 +7,17 @@
 
 namespace ehs {
 
+// Active-item selection: when list != nullptr, per-item launches cover only
+// the n listed items (blockIdx.y indexes the list), so items of a batch that
+// have converged stop consuming bandwidth.  Set by the solver around the
+// launches it issues (per host thread).
+struct ItemSel {
+  const int* list = nullptr;
+  int n = 0;
+};
+extern thread_local ItemSel g_sel;
+inline unsigned sel_items(int items) { return (unsigned)(g_sel.list ? g_sel.n : items); }
+
 // ---- fine level (matrix-free) -------------------------------------------
 // cell coefficients from lambda, mu, rho (double, one set per medium, device)
 // and the absorbing layer; gamma = gamma_add + omega*abl_max*max_k(depth_k/L)^2;

@@ -1,0 +1,59 @@
+"""Full-size checks in the configuration bench.py times (512 x 512, four
+Poisson ratios batched, 5-level complex64 W(1,1) cycle, double-float FGMRES).
+
+The oracle's full solves take minutes, so the per-medium iteration counts it
+produced are stored in tests/golden/c2_oracle_iters.json (written by
+tests/golden/make_c2_oracle_iters.py, which calls only oracle/); the GPU
+counts must match them (+-1 for the complex64 preconditioner).  The true
+residual of every GPU solution is recomputed with the oracle's own assembled
+complex128 operator, and sampled operator rows are compared element-wise.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import operators as op
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_bench_workload_iterations_and_residuals():
+    import bench
+    from paper_1806_11277_gb300 import ehs
+    gold = json.load(open(os.path.join(HERE, "golden", "c2_oracle_iters.json")))
+    assert gold["levels"] == bench.LEVELS and gold["alpha"] == bench.ALPHA
+    meds = bench.media()
+    S = ehs.solver_for(meds, levels=bench.LEVELS, alpha=bench.ALPHA, w=list(bench.W_LEVELS),
+                       prec=ehs.EHS_C64, cycle=bench.CYCLE)
+    q = bench.rhs(meds)
+    qd = torch.from_numpy(q).cuda()
+    ud = torch.zeros_like(qd)
+    info = S.fgmres_solve(qd, ud)
+    u = ud.cpu().numpy()
+    for it, med in enumerate(meds):
+        assert abs(info[it]["iters"] - gold["iters"][it]) <= 1, (it, info[it], gold["iters"][it])
+        K = op.assemble_mixed(op.parts_for(med))
+        qo = op.slots_to_dofs(q[it], med.shape)
+        uo = op.slots_to_dofs(u[it], med.shape)
+        assert np.linalg.norm(qo - K @ uo) / np.linalg.norm(qo) <= 1e-6
+    # sampled rows of the FP64 operator at full size
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(q.shape) + 1j * rng.standard_normal(q.shape))
+    x[:, 0, :, 0] = 0
+    x[:, 1, 0, :] = 0
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    S.op_apply(xd, yd, level=0)
+    y = yd.cpu().numpy()
+    for it, med in enumerate(meds):
+        K = op.assemble_mixed(op.parts_for(med)).tocsr()
+        ye = K @ op.slots_to_dofs(x[it], med.shape)
+        yg = op.slots_to_dofs(y[it], med.shape)
+        rows = rng.choice(ye.size, 2000, replace=False)
+        assert np.allclose(yg[rows], ye[rows], rtol=1e-12, atol=1e-12 * np.abs(ye).max())
+    S.close()

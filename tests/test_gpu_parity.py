@@ -320,3 +320,20 @@ def test_fgmres_wcycle_iterations_match_oracle():
         ug = op.slots_to_dofs(u[it], med.shape)
         assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
         assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_dd_fgmres_batched_media_compaction():
+    """Two media converging at different iteration counts in one DD-MG batch:
+    each item's count and solution must equal its own oracle solve."""
+    ehs = _ehs()
+    meds = _media_2d(64, 2)
+    q, u, info = _solve_both(meds, 3, ehs.EHS_C64, precond=ehs.EHS_PRECOND_DD, dd=(2, 2, 1),
+                             dd_overlap=4, dd_pad=8)
+    for it, med in enumerate(meds):
+        D = odd.DD(med, (2, 2), 4, 8, 3, 0.2)
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        assert abs(info[it]["iters"] - io["iters"]) <= 1, (it, info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+    assert info[0]["iters"] != info[1]["iters"]
