@@ -47,11 +47,37 @@ WORKLOAD = ("2D heterogeneous media 512x512 (GRF corr 20, Vp 1.5-4.5, rho 1-2.5)
             f"({LEVELS} levels, alpha {ALPHA}) inside FP64-class (double-float) FGMRES(10) to 1e-6")
 # Galerkin level-1 apply (k_st_rows): 87 complex64 stencil coefficients 696 + x 24 + y 24
 ST_ROWS_L1_BYTES_PER_CELL_C64 = 87 * 8 + 24 + 24
+# DRAM read + write bytes of one k_st_rows<float,2,1> launch of the c2 line, from an
+# ncu capture of this kernel as it stands (set to None whenever the kernel changes)
+ROWS_L1_TRAFFIC_C2 = 190.79e6 + 7.07e6
 
 
 def media(seed=0):
     from paper_1806_11277_gb300 import synth
     return [synth.random_2d(n=N_GRID, sigma=s, seed=seed) for s in SIGMAS]
+
+
+# Other workloads (bench.py --config NAME); "c2" above is the default line.
+OTHER = {
+    # 128^3 layered + random 3D medium, DD into 2x2x2 overlapping subdomains,
+    # one shifted-Laplacian V-cycle per subdomain, complex64 preconditioner
+    "c3": dict(
+        workload=("3D layered+random medium 128^3 (5 layers Vp 1.5-4.5 x (1 + 0.1 GRF), Poisson 0.25-0.45, "
+                  "rho = 0.25 Vp + 1.5), 8 points per S-wavelength, 16-cell ABL; DD 2x2x2 (overlap 4, "
+                  "pad 8) with one complex64 5-level V(1,1) cycle per subdomain inside double-float FGMRES(10)"),
+        media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).layered_3d(
+            n=128, seed=0, corr=10.0, abl=16)],
+        kw=dict(levels=5, alpha=0.4, w=[0.75, 0.5, 0.25, 0.25], cycle=1, precond=1, dd=(2, 2, 2),
+                dd_overlap=4, dd_pad=8),
+        rows_l1_bytes=468 * 8 + 32 + 32, kernel="k_st_rows<float,3,1> (Galerkin level 1, all rows)"),
+    # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
+    "c1": dict(
+        workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "
+                  "x-force; 3-level V(1,1), alpha 0.2, complex128 FGMRES(10)"),
+        media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).homogeneous_2d()],
+        kw=dict(levels=3, alpha=0.2, w=[0.75, 0.5], cycle=1, prec=0),
+        rows_l1_bytes=87 * 16 + 48 + 48, kernel="k_st_rows<double,2,1> (Galerkin level 1, all rows)"),
+}
 
 
 def rhs(meds):
@@ -197,17 +223,59 @@ def run_gpu(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream()
-    meds = media()
+    cfg = OTHER.get(args.config)
+    meds = media() if cfg is None else cfg["media"]()
+    kw = dict(levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=ehs.EHS_C64, cycle=CYCLE)
+    if cfg is not None:
+        kw.update(cfg["kw"])
+    nsolve = len(meds)
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        S = ehs.solver_for(meds, levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=ehs.EHS_C64,
-                           cycle=CYCLE, stream=stream.cuda_stream)
+        S = ehs.solver_for(meds, stream=stream.cuda_stream, **kw)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     q_host = rhs(meds)
     qd = torch.from_numpy(q_host).to(dev)
     ud = torch.zeros_like(qd)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    def roofline():
+        # roofline of the dominant kernel family, the Galerkin-level stencil rows
+        # (k_st_rows): one launch = ehs_op_apply on level 1 (all rows, every cell),
+        # one launch per sample, L2 flushed before each, events on the solver's stream
+        shp1 = S.level_shape(1)
+        ncell1 = int(np.prod(shp1[2:])) * nsolve
+        x1 = torch.randn(shp1, dtype=torch.complex64 if kw["prec"] == ehs.EHS_C64 else torch.complex128, device=dev)
+        x1[:, 0, ..., 0] = 0         # boundary slots: u_k at i_k = 0
+        if len(shp1) == 4:
+            x1[:, 1, 0, :] = 0
+        else:
+            x1[:, 1, :, 0, :] = 0
+            x1[:, 2, 0, :, :] = 0
+        y1 = torch.zeros_like(x1)
+        kt = []
+        for r in range(args.kernel_reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                # the 512 MiB flush runs long enough that the events and the launch
+                # are queued behind it: no host gap lands inside the events
+                flush.fill_(1)
+                e0.record(stream)
+                S.op_apply(x1, y1, level=1)
+                e1.record(stream)
+            e1.synchronize()
+            kt.append(e0.elapsed_time(e1) / 1e3)
+        t_launch = statistics.median(kt)
+        peak, peak_kind = peaks()
+        alg = (ST_ROWS_L1_BYTES_PER_CELL_C64 if cfg is None else cfg["rows_l1_bytes"]) * ncell1
+        achieved = alg / t_launch / 1e9
+        return t_launch, alg, achieved
+
+    if args.roofline_only:              # the roofline kernel loop alone (for ncu captures)
+        t_launch, alg, achieved = roofline()
+        print(json.dumps({"roofline_kernel_us": t_launch * 1e6, "alg_bytes": alg, "achieved_gbs": achieved}))
+        S.close()
+        return 0
 
     def step():
         return S.fgmres_solve(qd, ud)
@@ -247,7 +315,7 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total = float(t.item())
         dist.barrier()
-    solves = len(SIGMAS) * args.steps * world
+    solves = nsolve * args.steps * world
     value = solves / total
     its = [i["iters"] for i in info]
     relres = [i["relres"] for i in info]
@@ -262,56 +330,37 @@ def run_gpu(args):
         t = time.perf_counter()
         S.fgmres_solve(q_pin, u_pin)
         e2e_t.append(time.perf_counter() - t)
-    e2e_val = len(SIGMAS) * world / (sum(e2e_t) / len(e2e_t))
+    e2e_val = nsolve * world / (sum(e2e_t) / len(e2e_t))
 
-    # roofline of the dominant kernel family, the Galerkin-level stencil rows
-    # (k_st_rows): one launch = ehs_op_apply on level 1 (all rows, every cell),
-    # one launch per sample, L2 flushed before each, events on the solver's stream
-    shp1 = S.level_shape(1)
-    ncell1 = int(np.prod(shp1[2:])) * len(SIGMAS)
-    x1 = torch.randn(shp1, dtype=torch.complex64, device=dev)
-    x1[:, 0, :, 0] = 0          # boundary slots: u_x at i_x = 0, u_y at i_y = 0
-    x1[:, 1, 0, :] = 0
-    y1 = torch.zeros_like(x1)
-    kt = []
-    for r in range(args.kernel_reps):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            S.op_apply(x1, y1, level=1)
-            e1.record(stream)
-        e1.synchronize()
-        kt.append(e0.elapsed_time(e1) / 1e3)
-    t_launch = statistics.median(kt)
+    t_launch, alg, achieved = roofline()
     peak, peak_kind = peaks()
-    alg = ST_ROWS_L1_BYTES_PER_CELL_C64 * ncell1
-    achieved = alg / t_launch / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+c128", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "media": len(SIGMAS),
-                   "sigmas": list(SIGMAS), "levels": LEVELS, "alpha": ALPHA, "cycle": "W(1,1)" if CYCLE == 2 else "V(1,1)",
+        "config": {"name": args.config, "workload": WORKLOAD if cfg is None else cfg["workload"],
+                   "grid": list(meds[0].shape), "media": nsolve,
+                   "sigmas": list(SIGMAS) if cfg is None else None, "levels": kw["levels"],
+                   "alpha": kw["alpha"], "cycle": "W(1,1)" if kw["cycle"] == 2 else "V(1,1)",
                    "krylov": "FGMRES(10), double-float (FP64-class) vectors and operator", "precond_dtype": "complex64",
                    "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
         "iters": its, "relres": relres, "setup_s": setup_s,
-        "gridpoints_x_iters_per_s": float(N_GRID * N_GRID * sum(its) * args.steps * world / total),
+        "gridpoints_x_iters_per_s": float(np.prod(meds[0].shape) * sum(its) * args.steps * world / total),
         "e2e": {"value": e2e_val, "unit": "solves/s",
                 "h2d_bytes_per_step": int(q_host.nbytes), "d2h_bytes_per_step": int(q_host.nbytes)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "k_st_rows<float,2,1> (Galerkin level 1, all rows)",
+        "roofline": {"bound": "hbm", "kernel": "k_st_rows<float,2,1> (Galerkin level 1, all rows)"
+                     if cfg is None else cfg["kernel"],
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                     "traffic": args.traffic, "alg_bytes_per_launch": alg,
+                     "traffic": args.traffic if args.traffic is not None else
+                     (ROWS_L1_TRAFFIC_C2 if cfg is None else None), "alg_bytes_per_launch": alg,
                      "launch_us": t_launch * 1e6},
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and cfg is None:
         iters_o = oracle_iteration_counts()
         t_it = []
         for s in range(len(SIGMAS)):
@@ -338,12 +387,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ehs", choices=["ehs", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c2"] + sorted(OTHER),
+                    help="c2: the 512x512 four-Poisson-ratio line (default); c3: 3D 128^3 DD-MG; c1: 64x64")
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--ref-iters", type=int, default=4)
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per launch of the roofline kernel from an ncu capture")
+                    help="DRAM bytes per launch of the roofline kernel from an ncu capture "
+                         "(default: the capture of the current kernel for the c2 line)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="skip the solves; only the roofline kernel timing loop (for ncu captures)")
     ap.add_argument("--profile-step", action="store_true",
                     help="run warm-up, then one step between cudaProfilerStart/Stop and exit")
     args = ap.parse_args()
