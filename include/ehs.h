@@ -148,6 +148,17 @@ ehs_status ehs_fgmres_solve(ehs_ctx* ctx, const void* q, void* u, ehs_solve_info
  * used.  Same argument conventions as ehs_fgmres_solve. */
 ehs_status ehs_adjoint_solve(ehs_ctx* ctx, const void* g, void* w, ehs_solve_info* info);
 
+/* Adjoint-state gradient with respect to the cell-centred medium:
+ *   g_m(c) = -Re( w^H (dK/dm_c) x ),  m in {lambda, mu, rho},
+ * summed over the right-hand sides of each medium, where x solves K x = q
+ * (ehs_fgmres_solve) and w solves K^H w = e (ehs_adjoint_solve with e the
+ * derivative of a real misfit J with respect to conj(x)); then g = dJ/dm.
+ * Frequency-domain full-waveform inversion, the application of Sec. 1.
+ * x, w: device complex128 vectors (all items); g_*: device double arrays
+ * [nmedia][ncell], overwritten. */
+ehs_status ehs_gradient(ehs_ctx* ctx, const void* x, const void* w, double* g_lambda, double* g_mu,
+                        double* g_rho);
+
 /* Allocation-free fine-level smoothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when
  * they need it -- code inside a CUDA stream capture (cudaMalloc cannot be

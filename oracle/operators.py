@@ -127,12 +127,15 @@ class Parts:
         n = lambda k: self.shape[d - 1 - k]
         ax = lambda k: d - 1 - k
         self.L = []      # weighted Laplacian per component: sum_j D^T A_e(mu) D
+        self.terms = []  # per component: list of (D, W) with the term D^T diag(W mu) D
+        self.A = []      # face-averaging matrix per component (cells -> u_k faces)
         self.M = []      # A_f(rho (1 - i gamma / omega)) per component (diagonal)
         self.Ms = []     # A_f(rho) per component (shift mass)
         self.G = []      # centres -> u_k faces gradient
         mass_cell = rho * (1.0 - 1j * gamma / omega)
         for k in range(d):
             Lk = None
+            tk = []
             for j in range(d):
                 mats, wmats = [], []
                 for a in range(d):
@@ -150,18 +153,23 @@ class Parts:
                         mats.append(sp.identity(na, format="csr"))
                         wmats.append(sp.identity(na, format="csr"))
                 D = kron_axes(mats)
-                w = kron_axes(wmats) @ mu.ravel()
+                Wm = kron_axes(wmats)
+                w = Wm @ mu.ravel()
+                tk.append((D, Wm))
                 term = D.T @ sp.diags(w) @ D
                 Lk = term if Lk is None else Lk + term
             self.L.append(Lk.tocsr())
+            self.terms.append(tk)
             A = kron_axes([avg_centre_to_face(self.shape[a]) if a == ax(k)
                            else sp.identity(self.shape[a], format="csr") for a in range(d)])
+            self.A.append(A)
             self.M.append(sp.diags(A @ mass_cell.ravel()))
             self.Ms.append(sp.diags(A @ rho.ravel()))
             self.G.append(kron_axes([grad_centre_to_face(self.shape[a], h) if a == ax(k)
                                      else sp.identity(self.shape[a], format="csr")
                                      for a in range(d)]))
         self.lam_mu = (lam + mu).ravel()
+        self.gamma = gamma.ravel()
 
 
 def assemble_mixed(parts: Parts, alpha=0.0):

@@ -100,6 +100,8 @@ struct ehs_ctx {
   float4 *hq = nullptr, *h2q = nullptr, *yq = nullptr;
   float2 *Zf = nullptr, *npq = nullptr, *invq = nullptr;
   double2* hhost = nullptr;   // device double copies of h for the host
+  double* d_rho = nullptr;   // media kept for the gradient: rho and omega per set
+  double* d_om = nullptr;
   double2* dd_x = nullptr;   // DD accumulated correction (c128 or c64 view)
   double2* dd_r = nullptr;
   int nblk = 1;
@@ -764,7 +766,9 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
                              prob->gamma_add, H.cf64, c->s);
     cnt(); post();
     CK(cudaStreamSynchronize(c->s));
-    dfree(c, dl); dfree(c, dm); dfree(c, dr); dfree(c, dom);
+    dfree(c, dl); dfree(c, dm);
+    c->d_rho = dr;
+    c->d_om = dom;
     build_hier(c, H);
     if (opts->precond == EHS_PRECOND_DD) dd_build(c);
     // Krylov workspace
@@ -901,6 +905,21 @@ ehs_status ehs_adjoint_solve(ehs_ctx* c, const void* g, void* w, ehs_solve_info*
   return guard(c, [&]() -> ehs_status {
     if (!g || !w) throw ArgError("null vector");
     return solve_common(c, g, w, info, true);
+  });
+}
+
+ehs_status ehs_gradient(ehs_ctx* c, const void* x, const void* w, double* g_lambda, double* g_mu,
+                        double* g_rho) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (!x || !w || !g_lambda || !g_mu || !g_rho) throw ArgError("null argument");
+    if (!is_device_ptr(x) || !is_device_ptr(w) || !is_device_ptr(g_lambda) || !is_device_ptr(g_mu) ||
+        !is_device_ptr(g_rho))
+      throw ArgError("ehs_gradient takes device pointers");
+    launch_gradient(c->H.g0, c->H.nsets, c->H.nrhs, c->H.cf64, c->d_rho, c->d_om, c->H.h,
+                    (const double2*)x, (const double2*)w, g_lambda, g_mu, g_rho, c->s);
+    cnt(); post();
+    return EHS_OK;
   });
 }
 

@@ -140,4 +140,9 @@ void launch_fine_apply_df(const Grid& g, int items, int nrhs, const void* cf, do
 void launch_dense_apply_df(int N, int items, int nrhs, const float4* inv, const float2* r, float2* x,
                            cudaStream_t s);
 
+// adjoint-state gradient -Re(w^H dK/dm x) per cell, summed over each medium's rhs
+void launch_gradient(const Grid& g, int nsets, int nrhs, const Coef4<double>* cf, const double* rho,
+                     const double* omegas, double h, const double2* x, const double2* w, double* gl,
+                     double* gm, double* gr, cudaStream_t s);
+
 }  // namespace ehs

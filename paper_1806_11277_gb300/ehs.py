@@ -44,7 +44,7 @@ class SolveInfo(C.Structure):
 EXPORTS = ["ehs_default_opts", "ehs_create", "ehs_destroy", "ehs_op_apply", "ehs_smooth",
            "ehs_vcycle", "ehs_dd_precond", "ehs_fgmres_solve", "ehs_adjoint_solve", "ehs_items",
            "ehs_level_len", "ehs_level_dims", "ehs_sync", "ehs_kernel_launches", "ehs_last_error",
-           "ehs_fine_smooth_noalloc"]
+           "ehs_fine_smooth_noalloc", "ehs_gradient"]
 
 _lib = None
 
@@ -79,6 +79,7 @@ def load(path=LIB_PATH):
     lib.ehs_last_error.argtypes = [vp]
     lib.ehs_last_error.restype = C.c_char_p
     lib.ehs_fine_smooth_noalloc.argtypes = [C.POINTER(Problem), i, d, d, d, i, i, vp, vp, vp]
+    lib.ehs_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)
     _lib = lib
@@ -199,6 +200,18 @@ class Solver:
 
     def adjoint_solve(self, g, w, raise_noconv=True):
         return self._solve(self.lib.ehs_adjoint_solve, g, w, raise_noconv)
+
+    def gradient(self, x, w, out=None):
+        """(g_lambda, g_mu, g_rho): -Re(w^H dK/dm x) per cell, summed over each medium's rhs.
+        x, w: complex128 CUDA tensors of all items; returns float64 CUDA tensors
+        of shape (nmedia, *grid)."""
+        import torch
+        if out is None:
+            out = [torch.empty((self.nmedia,) + tuple(self.shape), dtype=torch.float64, device=x.device)
+                   for _ in range(3)]
+        self._check(self.lib.ehs_gradient(self.ctx, _ptr(x), _ptr(w), _ptr(out[0]), _ptr(out[1]),
+                                          _ptr(out[2])))
+        return out
 
     def sync(self):
         self._check(self.lib.ehs_sync(self.ctx))
