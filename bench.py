@@ -70,6 +70,13 @@ OTHER = {
         kw=dict(levels=5, alpha=0.4, w=[0.75, 0.5, 0.25, 0.25], cycle=1, precond=1, dd=(2, 2, 2),
                 dd_overlap=4, dd_pad=8),
         rows_l1_bytes=468 * 8 + 32 + 32, kernel="k_st_rows<float,3,1> (Galerkin level 1, all rows)"),
+    # the c2 workload with FP16 / BF16 storage of the Galerkin stencil tables
+    "c2h": dict(workload=WORKLOAD + "; Galerkin tables stored as FP16 pairs (FP32 accumulation)",
+                media=lambda: media(), kw=dict(coef_half=1), rows_l1_bytes=87 * 4 + 24 + 24,
+                kernel="k_st_rows<float,__half2,2,1> (Galerkin level 1, all rows)"),
+    "c2b": dict(workload=WORKLOAD + "; Galerkin tables stored as BF16 pairs (FP32 accumulation)",
+                media=lambda: media(), kw=dict(coef_half=2), rows_l1_bytes=87 * 4 + 24 + 24,
+                kernel="k_st_rows<float,__nv_bfloat162,2,1> (Galerkin level 1, all rows)"),
     # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
     "c1": dict(
         workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "

@@ -96,6 +96,9 @@ typedef struct {
   int dd_overlap;        /* overlap in cells (DD only) */
   int dd_pad;            /* absorbing padding in cells on interface sides (DD only) */
   double dd_abl_max;     /* gamma/omega at the outer edge of the padding (DD only) */
+  int coef_half;         /* storage of the Galerkin stencil coefficients used by the
+                            complex64 cycle: 0 complex64, 1 FP16 pairs, 2 BF16 pairs
+                            (products accumulate in FP32; the FP64 masters stay) */
 } ehs_opts;
 
 typedef struct {

@@ -50,6 +50,7 @@ struct Level {
   StencilLayout L{};
   double2* tab64 = nullptr;   // Galerkin levels and coarsest: [nsets][nslot][ncell]
   float2* tab32 = nullptr;
+  void* tabh = nullptr;       // half-precision copy (FP16 or BF16 pairs) for the complex64 cycle
   double2* inv = nullptr;     // coarsest: [nsets][N][N]
   float4* invdf = nullptr;    // coarsest inverse in complex df64 (used by the complex64 cycle)
   void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
@@ -62,6 +63,7 @@ struct Hier {
   double h = 1, alpha = 0;
   double wp_ratio = 1;
   int nu1 = 1, nu2 = 1, cyc = 1;
+  int half = 0;                // Galerkin tables of the complex64 cycle: 0 complex64, 1 FP16, 2 BF16
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
   void* cfdf = nullptr;        // df64 coefficients (outer-Krylov operator of the global problem)
@@ -182,6 +184,10 @@ void build_hier(ehs_ctx* c, Hier& H) {
     const long long nt = (long long)H.nsets * L.L.nslot * L.g.ncell;
     L.tab32 = dalloc<float2>(c, nt);
     launch_table_cast<float>(nt, L.tab64, L.tab32, c->s); cnt(); post();
+    if (H.half) {
+      L.tabh = dalloc<float>(c, nt);   // 4 bytes per complex coefficient
+      launch_table_half(nt, L.tab64, L.tabh, H.half, c->s); cnt(); post();
+    }
     Lf = L.L;
     tf = L.tab64;
   }
@@ -212,18 +218,26 @@ template <> struct PT<float> { static const int i = 1; };
 template <typename T> const Coef4<T>* cfp(const Hier& H);
 template <> const Coef4<double>* cfp<double>(const Hier& H) { return H.cf64; }
 template <> const Coef4<float>* cfp<float>(const Hier& H) { return H.cf32; }
-template <typename T> const typename CT<T>::type* tabp(const Level& L);
-template <> const double2* tabp<double>(const Level& L) { return L.tab64; }
-template <> const float2* tabp<float>(const Level& L) { return L.tab32; }
+// stencil table of a Galerkin level for the cycle precision T, and its format
+template <typename T> const void* tabp(const Hier& H, const Level& L, int* fmt);
+template <> const void* tabp<double>(const Hier&, const Level& L, int* fmt) { *fmt = 0; return L.tab64; }
+template <> const void* tabp<float>(const Hier& H, const Level& L, int* fmt) {
+  if (H.half && L.tabh) { *fmt = H.half; return L.tabh; }
+  *fmt = 0;
+  return L.tab32;
+}
 
 template <typename T>
 void level_apply(ehs_ctx* c, const Hier& H, int l, double alpha, const typename CT<T>::type* x,
                  const typename CT<T>::type* b, typename CT<T>::type* y, int mode) {
   const Level& L = H.lv[l];
-  if (l == 0)
+  if (l == 0) {
     launch_fine_apply<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, alpha, x, b, y, mode, c->s);
-  else
-    launch_st_apply<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), x, b, y, mode, c->s);
+  } else {
+    int fmt = 0;
+    const void* tab = tabp<T>(H, L, &fmt);
+    launch_st_apply<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, x, b, y, mode, c->s);
+  }
   cnt(); post();
 }
 
@@ -239,8 +253,10 @@ void level_sweep(ehs_ctx* c, const Hier& H, int l, const typename CT<T>::type* b
   } else {
     typedef typename CT<T>::type C;
     C* rb = (C*)L.ws[PT<T>::i][3];
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 0, b, x, t, rb, c->s);
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tabp<T>(L), wu, wp, 1, b, t, x, rb, c->s);
+    int fmt = 0;
+    const void* tab = tabp<T>(H, L, &fmt);
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 0, b, x, t, rb, c->s);
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 1, b, t, x, rb, c->s);
     cnt(2);
   }
   cnt(2); post();
@@ -305,6 +321,7 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (!(O->tol > 0)) throw ArgError("tol must be positive");
   if (P->abl_cells < 0 || 2 * P->abl_cells > P->n[0]) throw ArgError("bad abl_cells");
   if (O->precond != EHS_PRECOND_MG && O->precond != EHS_PRECOND_DD) throw ArgError("bad precond");
+  if (O->coef_half < 0 || O->coef_half > 2) throw ArgError("coef_half must be 0, 1 (FP16) or 2 (BF16)");
 }
 
 void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* rho, long long n) {
@@ -745,6 +762,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     H.h = prob->h; H.alpha = opts->alpha;
     H.wp_ratio = opts->wp_ratio > 0 ? opts->wp_ratio : 1.0;
     H.nu1 = opts->nu_pre; H.nu2 = opts->nu_post; H.cyc = opts->cycle;
+    H.half = opts->coef_half;
     c->n0 = (long long)(c->d + 1) * H.g0.ncell;
     const long long nc = (long long)H.nsets * H.g0.ncell;
     check_media(c, prob->lambda, prob->mu, prob->rho, nc);

@@ -7,9 +7,25 @@
 // 1D transfer supports, so the hierarchy never stores offsets it cannot use.
 #include <algorithm>
 #include <stdexcept>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace ehs {
+
+// Stencil-table element load: complex64/complex128 tables as stored, and the
+// half-precision table formats (FP16 or BF16 real/imag pairs) widened to
+// complex64 so that accumulation stays in FP32.
+template <typename T> __device__ __forceinline__ typename CT<T>::type ldtab(const typename CT<T>::type* p) {
+  return __ldg(p);
+}
+template <typename T> __device__ __forceinline__ float2 ldtab(const __half2* p) {
+  return __half22float2(__ldg(p));
+}
+template <typename T> __device__ __forceinline__ float2 ldtab(const __nv_bfloat162* p) {
+  return __bfloat1622float2(__ldg(p));
+}
 
 // ------------------------------------------------------------------ layout
 void coarse_layout(int d, const StencilLayout& F, StencilLayout* C) { *C = make_coarse_layout(d, F); }
@@ -128,9 +144,9 @@ __global__ void k_table_cast(long long n, const double2* in, C* out) {
 // Galerkin level variant LV (1 = first coarse level, 2 = all coarser ones)
 // known at compile time so that every table and vector load of the row is
 // issued back to back.
-template <typename T, int D, int LV, int Q, int QE>
+template <typename T, typename TT, int D, int LV, int Q, int QE>
 __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
-                                        const typename CT<T>::type* __restrict__ tab,
+                                        const TT* __restrict__ tab,
                                         long long c, const int i[3],
                                         const typename CT<T>::type* __restrict__ x) {
   if constexpr (Q < QE) {
@@ -154,22 +170,22 @@ __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
           if (rin && jx >= 0 && jx < g.n[0]) {
             const int sl = base + (oz * e1 + oy) * e0 + ox;
             const long long cj = c + (lo2 + oz) * sz + (lo1 + oy) * sy + (lo0 + ox);
-            y = cfma(__ldg(tab + (long long)sl * N + c), __ldg(xb + cj), y);
+            y = cfma(ldtab<T>(tab + (long long)sl * N + c), __ldg(xb + cj), y);
           }
         }
       }
     }
-    row_acc<T, D, LV, Q + 1, QE>(y, g, tab, c, i, x);
+    row_acc<T, TT, D, LV, Q + 1, QE>(y, g, tab, c, i, x);
   }
 }
 
-template <typename T, int D, int LV, int A>
-__device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const typename CT<T>::type* tab,
+template <typename T, typename TT, int D, int LV, int A>
+__device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const TT* tab,
                                                            long long c, const int i[3],
                                                            const typename CT<T>::type* x) {
   constexpr StencilLayout L = level_layout(D, LV);
   typename CT<T>::type y = czero<typename CT<T>::type>();
-  row_acc<T, D, LV, L.row_first[A], L.row_first[A + 1]>(y, g, tab, c, i, x);
+  row_acc<T, TT, D, LV, L.row_first[A], L.row_first[A + 1]>(y, g, tab, c, i, x);
   return y;
 }
 
@@ -178,8 +194,8 @@ __device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const t
 // a warp and the row's stencil loop is fully unrolled.  mode 0: y = A x,
 // mode 1: y = b - A x.  colour >= 0 restricts the pressure rows to cells of
 // that colour (the rows a red-black half-sweep needs).
-template <typename T, int D, int LV, int A>
-__device__ __forceinline__ void st_one_row(const Grid& g, const typename CT<T>::type* ts, long long c,
+template <typename T, typename TT, int D, int LV, int A>
+__device__ __forceinline__ void st_one_row(const Grid& g, const TT* ts, long long c,
                                            const int i[3], const typename CT<T>::type* xv,
                                            const typename CT<T>::type* bv, typename CT<T>::type* yv,
                                            int mode) {
@@ -187,14 +203,14 @@ __device__ __forceinline__ void st_one_row(const Grid& g, const typename CT<T>::
   const long long N = g.ncell;
   Cx r = czero<Cx>();
   if (slot_valid(A, D, i)) {
-    r = st_row_ct<T, D, LV, A>(g, ts, c, i, xv);
+    r = st_row_ct<T, TT, D, LV, A>(g, ts, c, i, xv);
     if (mode) r = csub(__ldg(bv + (long long)A * N + c), r);
   }
   yv[(long long)A * N + c] = r;
 }
 
-template <typename T, int D, int LV>
-__global__ void __launch_bounds__(128) k_st_rows(Grid g, int nrhs, const typename CT<T>::type* __restrict__ tab,
+template <typename T, typename TT, int D, int LV>
+__global__ void __launch_bounds__(128) k_st_rows(Grid g, int nrhs, const TT* __restrict__ tab,
                                                  const typename CT<T>::type* __restrict__ x,
                                                  const typename CT<T>::type* __restrict__ b,
                                                  typename CT<T>::type* __restrict__ y, int mode, int colour,
@@ -209,19 +225,19 @@ __global__ void __launch_bounds__(128) k_st_rows(Grid g, int nrhs, const typenam
   if (a == D && colour >= 0 && ((i[0] + i[1] + i[2]) & 1) != colour) return;
   const long long N = g.ncell;
   const long long vo = (long long)item * (D + 1) * N;
-  const typename CT<T>::type* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  const TT* ts = tab + (long long)(item / nrhs) * L.nslot * N;
   const typename CT<T>::type* bv = mode ? b + vo : nullptr;
-  if (a == 0) st_one_row<T, D, LV, 0>(g, ts, c, i, x + vo, bv, y + vo, mode);
-  else if (a == 1) st_one_row<T, D, LV, 1>(g, ts, c, i, x + vo, bv, y + vo, mode);
-  else if (a == 2) st_one_row<T, D, LV, 2>(g, ts, c, i, x + vo, bv, y + vo, mode);
-  else if constexpr (D == 3) st_one_row<T, D, LV, 3>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  if (a == 0) st_one_row<T, TT, D, LV, 0>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if (a == 1) st_one_row<T, TT, D, LV, 1>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if (a == 2) st_one_row<T, TT, D, LV, 2>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if constexpr (D == 3) st_one_row<T, TT, D, LV, 3>(g, ts, c, i, x + vo, bv, y + vo, mode);
 }
 
 // Update pass of one colour: the economic cell block (stored diagonal and
 // displacement-pressure couplings) is solved for every cell of the colour
 // from the residual r of the residual pass; xo receives the new iterate.
-template <typename T, int D, int LV>
-__global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const typename CT<T>::type* __restrict__ tab,
+template <typename T, typename TT, int D, int LV>
+__global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const TT* __restrict__ tab,
                                                  T wu, T wp, int colour,
                                                  const typename CT<T>::type* __restrict__ res,
                                                  const typename CT<T>::type* __restrict__ xi,
@@ -234,7 +250,7 @@ __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const typenam
   if (t >= N / 2) return;
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long vo = (long long)item * (D + 1) * N;
-  const Cx* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  const TT* ts = tab + (long long)(item / nrhs) * L.nslot * N;
   const Cx* x = xi + vo;
   const Cx* rr = res + vo;
   Cx* xout = xo + vo;
@@ -257,20 +273,20 @@ __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const typenam
     ok[k] = i[k] >= 1;
     if (ok[k]) {
       r[k] = __ldg(rr + (long long)k * N + c);
-      dg[k] = __ldg(ts + (long long)sd * N + c);
-      gr[k] = __ldg(ts + (long long)sg0 * N + c);
-      gc_[k] = __ldg(ts + (long long)sc0 * N + c);
+      dg[k] = ldtab<T>(ts + (long long)sd * N + c);
+      gr[k] = ldtab<T>(ts + (long long)sg0 * N + c);
+      gc_[k] = ldtab<T>(ts + (long long)sc0 * N + c);
     }
     ok[D + k] = i[k] + 1 < g.n[k];
     if (ok[D + k]) {
       r[D + k] = __ldg(rr + (long long)k * N + c + sk);
-      dg[D + k] = __ldg(ts + (long long)sd * N + c + sk);
-      gr[D + k] = __ldg(ts + (long long)sg1 * N + c + sk);
-      gc_[D + k] = __ldg(ts + (long long)sc1 * N + c);
+      dg[D + k] = ldtab<T>(ts + (long long)sd * N + c + sk);
+      gr[D + k] = ldtab<T>(ts + (long long)sg1 * N + c + sk);
+      gc_[D + k] = ldtab<T>(ts + (long long)sc1 * N + c);
     }
   }
   r[2 * D] = __ldg(rr + (long long)D * N + c);
-  Cx sch = __ldg(ts + (long long)st_slot(L, D, D, 0, 0, 0) * N + c);
+  Cx sch = ldtab<T>(ts + (long long)st_slot(L, D, D, 0, 0, 0) * N + c);
   Cx rp = r[2 * D];
   Cx dinv[2 * D];
 #pragma unroll
@@ -331,58 +347,91 @@ static int layout_variant(const StencilLayout& L, int d) {
   throw std::runtime_error("unexpected Galerkin stencil layout");
 }
 
-template <typename T>
-void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
-                     const typename CT<T>::type* tab, const typename CT<T>::type* x,
-                     const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
-                     cudaStream_t s) {
+template <typename T, typename TT>
+static void st_apply_t(const Grid& g, int items, int nrhs, int v, const TT* tab, const typename CT<T>::type* x,
+                       const typename CT<T>::type* b, typename CT<T>::type* y, int mode, int colour,
+                       cudaStream_t s) {
   const dim3 gr((unsigned)((g.ncell + 127) / 128), sel_items(items), g.d + 1);
-  const int v = layout_variant(L, g.d);
   if (g.d == 2) {
-    if (v == 1) k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
-    else k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
+    if (v == 1) k_st_rows<T, TT, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+    else k_st_rows<T, TT, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
   } else {
-    if (v == 1) k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
-    else k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, -1, g_sel.list);
+    if (v == 1) k_st_rows<T, TT, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+    else k_st_rows<T, TT, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
   }
+}
+template <typename T, typename TT>
+static void st_vupd_t(const Grid& g, int items, int nrhs, int v, const TT* tab, T wu, T wp, int colour,
+                      const typename CT<T>::type* r, const typename CT<T>::type* xi, typename CT<T>::type* xo,
+                      cudaStream_t s) {
+  const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), sel_items(items), 1);
+  if (g.d == 2) {
+    if (v == 1) k_st_vupd<T, TT, 2, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+    else k_st_vupd<T, TT, 2, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+  } else {
+    if (v == 1) k_st_vupd<T, TT, 3, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+    else k_st_vupd<T, TT, 3, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+  }
+}
+// dispatch on the table storage format (0: as T, 1: FP16 pairs, 2: BF16 pairs; T = float only)
+template <typename T>
+static void st_apply_any(const Grid& g, int items, int nrhs, int v, const void* tab, int fmt,
+                         const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y,
+                         int mode, int colour, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (fmt == 1) return st_apply_t<T, __half2>(g, items, nrhs, v, (const __half2*)tab, x, b, y, mode, colour, s);
+    if (fmt == 2) return st_apply_t<T, __nv_bfloat162>(g, items, nrhs, v, (const __nv_bfloat162*)tab, x, b, y, mode, colour, s);
+  }
+  st_apply_t<T, typename CT<T>::type>(g, items, nrhs, v, (const typename CT<T>::type*)tab, x, b, y, mode, colour, s);
+}
+template <typename T>
+static void st_vupd_any(const Grid& g, int items, int nrhs, int v, const void* tab, int fmt, T wu, T wp,
+                        int colour, const typename CT<T>::type* r, const typename CT<T>::type* xi,
+                        typename CT<T>::type* xo, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (fmt == 1) return st_vupd_t<T, __half2>(g, items, nrhs, v, (const __half2*)tab, wu, wp, colour, r, xi, xo, s);
+    if (fmt == 2) return st_vupd_t<T, __nv_bfloat162>(g, items, nrhs, v, (const __nv_bfloat162*)tab, wu, wp, colour, r, xi, xo, s);
+  }
+  st_vupd_t<T, typename CT<T>::type>(g, items, nrhs, v, (const typename CT<T>::type*)tab, wu, wp, colour, r, xi, xo, s);
+}
+
+template <typename T>
+void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
+                     const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y,
+                     int mode, cudaStream_t s) {
+  st_apply_any<T>(g, items, nrhs, layout_variant(L, g.d), tab, fmt, x, b, y, mode, -1, s);
 }
 
 // one colour of red-black economic Vanka on a Galerkin level: residual pass
 // into rbuf (u rows of every cell, p rows of the colour), then the update pass
 template <typename T>
-void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L,
-                     const typename CT<T>::type* tab, T wu, T wp, int colour,
-                     const typename CT<T>::type* b, const typename CT<T>::type* xi,
+void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
+                     T wu, T wp, int colour, const typename CT<T>::type* b, const typename CT<T>::type* xi,
                      typename CT<T>::type* xo, typename CT<T>::type* rbuf, cudaStream_t s) {
-  const dim3 gr((unsigned)((g.ncell + 127) / 128), sel_items(items), g.d + 1);
-  const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), sel_items(items), 1);
   const int v = layout_variant(L, g.d);
-  if (g.d == 2) {
-    if (v == 1) {
-      k_st_rows<T, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
-      k_st_vupd<T, 2, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
-    } else {
-      k_st_rows<T, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
-      k_st_vupd<T, 2, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
-    }
-  } else {
-    if (v == 1) {
-      k_st_rows<T, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
-      k_st_vupd<T, 3, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
-    } else {
-      k_st_rows<T, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, tab, xi, b, rbuf, 1, colour, g_sel.list);
-      k_st_vupd<T, 3, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, rbuf, xi, xo, g_sel.list);
-    }
-  }
+  st_apply_any<T>(g, items, nrhs, v, tab, fmt, xi, b, rbuf, 1, colour, s);
+  st_vupd_any<T>(g, items, nrhs, v, tab, fmt, wu, wp, colour, rbuf, xi, xo, s);
+}
+
+// FP64 master table -> half-precision pairs (fmt 1: FP16, 2: BF16)
+__global__ void k_table_half(long long n, const double2* __restrict__ in, void* out, int fmt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = in[i];
+  if (fmt == 1) ((__half2*)out)[i] = __floats2half2_rn((float)v.x, (float)v.y);
+  else ((__nv_bfloat162*)out)[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+}
+void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaStream_t s) {
+  k_table_half<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out, fmt);
 }
 
 #define INST(T)                                                                                   \
   template void launch_table_cast<T>(long long, const double2*, CT<T>::type*, cudaStream_t);       \
-  template void launch_st_apply<T>(const Grid&, int, int, const StencilLayout&, const CT<T>::type*, \
+  template void launch_st_apply<T>(const Grid&, int, int, const StencilLayout&, const void*, int,   \
                                    const CT<T>::type*, const CT<T>::type*, CT<T>::type*, int,       \
                                    cudaStream_t);                                                   \
-  template void launch_st_vanka<T>(const Grid&, int, int, const StencilLayout&, const CT<T>::type*, \
-                                   T, T, int, const CT<T>::type*, const CT<T>::type*, CT<T>::type*, \
+  template void launch_st_vanka<T>(const Grid&, int, int, const StencilLayout&, const void*, int, T, \
+                                   T, int, const CT<T>::type*, const CT<T>::type*, CT<T>::type*,    \
                                    CT<T>::type*, cudaStream_t);
 INST(float)
 INST(double)

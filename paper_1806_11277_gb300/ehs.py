@@ -34,7 +34,8 @@ class Opts(C.Structure):
                 ("wp_ratio", C.c_double), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("cycle", C.c_int), ("restart", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("precond", C.c_int), ("prec", C.c_int), ("nrhs", C.c_int), ("dd", C.c_int * 3),
-                ("dd_overlap", C.c_int), ("dd_pad", C.c_int), ("dd_abl_max", C.c_double)]
+                ("dd_overlap", C.c_int), ("dd_pad", C.c_int), ("dd_abl_max", C.c_double),
+                ("coef_half", C.c_int)]
 
 
 class SolveInfo(C.Structure):

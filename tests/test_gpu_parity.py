@@ -337,3 +337,45 @@ def test_dd_fgmres_batched_media_compaction():
         assert abs(info[it]["iters"] - io["iters"]) <= 1, (it, info[it], io["iters"])
         assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
     assert info[0]["iters"] != info[1]["iters"]
+
+
+@pytest.mark.parametrize("fmt,tol", [(1, 2e-3), (2, 1.5e-2)])
+def test_half_tables_operator(fmt, tol):
+    """Galerkin levels with FP16 (fmt 1) / BF16 (fmt 2) coefficient storage,
+    FP32 accumulation: relative error of K_l x against the FP64 oracle within
+    the format's rounding (unit roundoff 4.9e-4 FP16, 3.9e-3 BF16)."""
+    ehs = _ehs()
+    meds = _media_2d(64, 2)
+    S = ehs.solver_for(meds, levels=4, alpha=0.4, coef_half=fmt)
+    for b, med in enumerate(meds):
+        H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25])
+        for l in (1, 2):
+            shp = S.level_shape(l)
+            x = _rand_slots(tuple(shp[2:]), S.items, 40 + l)
+            xd = torch.from_numpy(x).to("cuda", torch.complex64)
+            yd = torch.zeros_like(xd)
+            S.op_apply(xd, yd, level=l)
+            xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), tuple(shp[2:]))
+            ye = op.dofs_to_slots(H.K[l] @ xe, tuple(shp[2:]))
+            err = _rel(yd[b].cpu().numpy(), ye)
+            assert err <= tol, (fmt, l, err)
+    S.close()
+
+
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_half_tables_fgmres(fmt):
+    """Half-precision Galerkin tables inside the complex64 W-cycle: the FP64-class
+    outer FGMRES still reaches 1e-6, the solution stays within 1e-5 of the
+    oracle's, and the iteration count moves by at most 2."""
+    ehs = _ehs()
+    meds = _media_2d(64, 4)
+    q, u, info = _solve_both(meds, 4, ehs.EHS_C64, alpha=0.4, cycle=2, coef_half=fmt)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25])
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        assert info[it]["converged"] and np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo) <= 1e-6
+        assert abs(info[it]["iters"] - io["iters"]) <= 2, (fmt, it, info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
