@@ -54,6 +54,7 @@ struct Level {
   double2* inv = nullptr;     // coarsest: [nsets][N][N]
   float4* invdf = nullptr;    // coarsest inverse in complex df64 (used by the complex64 cycle)
   void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
+  int rows_var[2] = {0, 0};      // residual-pass launch shape per precision (setup autotuner)
   double w = 0.5;
 };
 
@@ -152,6 +153,8 @@ Grid mkgrid(int d, int nx, int ny, int nz) {
 }
 
 // ------------------------------------------------------------ hierarchy
+template <typename T> void autotune_rows(ehs_ctx* c, Hier& H);
+
 void build_hier(ehs_ctx* c, Hier& H) {
   const int d = H.g0.d;
   H.cf32 = dalloc<Coef4<float>>(c, (size_t)H.nsets * H.g0.ncell);
@@ -209,6 +212,13 @@ void build_hier(ehs_ctx* c, Hier& H) {
   dfree(c, M); dfree(c, fb); dfree(c, pv); dfree(c, derr);
   if (herr & EHS_DEVERR_BOX) throw CudaError("Galerkin stencil fell outside its box");
   if (herr & EHS_DEVERR_SINGULAR) throw ArgError("coarsest Galerkin operator is singular");
+  autotune_rows<float>(c, H);
+  autotune_rows<double>(c, H);
+  if (const char* f = getenv("EHS_ROWS_VARIANT")) {   // fixed launch shape (tests)
+    const int v = atoi(f);
+    if (v >= 0 && v < ST_ROWS_VARIANTS)
+      for (Level& L : H.lv) L.rows_var[0] = L.rows_var[1] = v;
+  }
 }
 
 template <typename T> struct PT;
@@ -236,7 +246,7 @@ void level_apply(ehs_ctx* c, const Hier& H, int l, double alpha, const typename 
   } else {
     int fmt = 0;
     const void* tab = tabp<T>(H, L, &fmt);
-    launch_st_apply<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, x, b, y, mode, c->s);
+    launch_st_apply<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, x, b, y, mode, L.rows_var[PT<T>::i], c->s);
   }
   cnt(); post();
 }
@@ -255,11 +265,49 @@ void level_sweep(ehs_ctx* c, const Hier& H, int l, const typename CT<T>::type* b
     C* rb = (C*)L.ws[PT<T>::i][3];
     int fmt = 0;
     const void* tab = tabp<T>(H, L, &fmt);
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 0, b, x, t, rb, c->s);
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 1, b, t, x, rb, c->s);
+    const int var = L.rows_var[PT<T>::i];
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 0, b, x, t, rb, var, c->s);
+    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 1, b, t, x, rb, var, c->s);
     cnt(2);
   }
   cnt(2); post();
+}
+
+// Setup autotuner: times every residual-pass launch shape of each smoothed
+// Galerkin level (its working precision and table format, on the level's own
+// buffers) and keeps the fastest.  Runs at setup, outside any capture.
+template <typename T>
+void autotune_rows(ehs_ctx* c, Hier& H) {
+  typedef typename CT<T>::type C;
+  const int p = PT<T>::i;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int l = 1; l + 1 < H.nlev; ++l) {
+    Level& L = H.lv[l];
+    int fmt = 0;
+    const void* tab = tabp<T>(H, L, &fmt);
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < ST_ROWS_VARIANTS; ++v) {
+      float tsum = 0.0f;
+      for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaEventRecord(e0, c->s));
+        launch_st_apply<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, (const C*)L.ws[p][1], (const C*)L.ws[p][0],
+                           (C*)L.ws[p][3], 1, v, c->s);
+        CK(cudaEventRecord(e1, c->s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep) tsum += ms;                // the first run warms caches and code
+      }
+      cnt(4); post();
+      if (tsum < best) { best = tsum; bestv = v; }
+    }
+    L.rows_var[p] = bestv;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
 }
 
 template <typename T>

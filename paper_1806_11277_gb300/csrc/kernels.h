@@ -64,16 +64,18 @@ template <typename T>
 void launch_table_cast(long long n, const double2* in, typename CT<T>::type* out, cudaStream_t s);
 // tab: stencil table of level-layout L in format fmt (0: complex T, 1: FP16
 // pairs, 2: BF16 pairs; the half formats serve the complex64 cycle only)
+// var: residual-pass launch shape, 0 .. ST_ROWS_VARIANTS-1 (chosen by the setup autotuner)
+#define ST_ROWS_VARIANTS 4
 template <typename T>
 void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
                      const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y,
-                     int mode, cudaStream_t s);
+                     int mode, int var, cudaStream_t s);
 void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaStream_t s);
 // one colour of red-black Vanka on a Galerkin level; rbuf: residual scratch of x's size
 template <typename T>
 void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
                      T wu, T wp, int colour, const typename CT<T>::type* b, const typename CT<T>::type* xi,
-                     typename CT<T>::type* xo, typename CT<T>::type* rbuf, cudaStream_t s);
+                     typename CT<T>::type* xo, typename CT<T>::type* rbuf, int var, cudaStream_t s);
 
 // ---- transfer -------------------------------------------------------------
 template <typename T>

@@ -379,3 +379,37 @@ def test_half_tables_fgmres(fmt):
         assert info[it]["converged"] and np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo) <= 1e-6
         assert abs(info[it]["iters"] - io["iters"]) <= 2, (fmt, it, info[it], io["iters"])
         assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_galerkin_rows_launch_shapes_agree(variant, monkeypatch):
+    """Every residual-pass launch shape the setup autotuner can pick (1 or 2
+    cells per thread, 64..256 threads) gives the oracle's Galerkin operator."""
+    ehs = _ehs()
+    monkeypatch.setenv("EHS_ROWS_VARIANT", str(variant))
+    meds = _media_2d(64, 2)
+    for fmt in (0, 1):
+        S = ehs.solver_for(meds, levels=4, alpha=0.4, coef_half=fmt)
+        for b, med in enumerate(meds):
+            H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25])
+            for l in (1, 2):
+                shp = S.level_shape(l)
+                x = _rand_slots(tuple(shp[2:]), S.items, 50 + l)
+                for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5 if fmt == 0 else 2e-3)):
+                    if fmt and dt == torch.complex128:
+                        continue
+                    xd = torch.from_numpy(x).to("cuda", dt)
+                    yd = torch.zeros_like(xd)
+                    S.op_apply(xd, yd, level=l)
+                    xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), tuple(shp[2:]))
+                    ye = op.dofs_to_slots(H.K[l] @ xe, tuple(shp[2:]))
+                    assert _rel(yd[b].cpu().numpy(), ye) <= tol, (variant, fmt, l, dt)
+        S.close()
+    # a full solve with this launch shape keeps the oracle's iteration counts
+    q, u, info = _solve_both(meds, 4, ehs.EHS_C64, alpha=0.4, cycle=2)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25])
+        qo = op.slots_to_dofs(q[it], med.shape)
+        _, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
+        assert abs(info[it]["iters"] - io["iters"]) <= 1
