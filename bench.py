@@ -64,12 +64,27 @@ OTHER = {
     "c3": dict(
         workload=("3D layered+random medium 128^3 (5 layers Vp 1.5-4.5 x (1 + 0.1 GRF), Poisson 0.25-0.45, "
                   "rho = 0.25 Vp + 1.5), 8 points per S-wavelength, 16-cell ABL; DD 2x2x2 (overlap 4, "
-                  "pad 8) with one complex64 5-level V(1,1) cycle per subdomain inside double-float FGMRES(10)"),
+                  "pad 8) with one complex64 5-level V(1,1) cycle per subdomain (damping 0.5/0.5/0.2/0.2) inside "
+                  "double-float FGMRES(10)"),
         media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).layered_3d(
             n=128, seed=0, corr=10.0, abl=16)],
-        kw=dict(levels=5, alpha=0.4, w=[0.75, 0.5, 0.25, 0.25], cycle=1, precond=1, dd=(2, 2, 2),
+        kw=dict(levels=5, alpha=0.4, w=[0.5, 0.5, 0.2, 0.2], cycle=1, precond=1, dd=(2, 2, 2),
                 dd_overlap=4, dd_pad=8),
-        rows_l1_bytes=468 * 8 + 32 + 32, kernel="k_st_rows<float,3,1> (Galerkin level 1, all rows)"),
+        roof_level=0, rows_l1_bytes=32 + 16 + 32,
+        kernel="k_fine_apply<float,3> (fine K x: x 32 + coefficients 16 + y 32 B per cell)"),
+    # batched multi-source 3D: 192^3, 8 x-forces on a surface line in one batch,
+    # uneven 3x3x2 subdomains (shape groups per colour), complex64 V-cycles
+    "c4": dict(
+        workload=("3D layered+random medium 192^3, 8 x-forces on the line z = ABL+2, y = n/2 solved as one "
+                  "batch; DD 3x3x2 (uneven subdomains, overlap 4, pad 8), one complex64 5-level V(1,1) per "
+                  "subdomain, double-float FGMRES(10)"),
+        media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).layered_3d(
+            n=192, seed=0, corr=10.0, abl=16, nsrc=8)],
+        nrhs=8,
+        kw=dict(levels=5, alpha=0.4, w=[0.5, 0.5, 0.2, 0.2], cycle=1, precond=1, dd=(3, 3, 2),
+                dd_overlap=4, dd_pad=8, nrhs=8, maxit=800),
+        roof_level=0, rows_l1_bytes=32 + 16 + 32,
+        kernel="k_fine_apply<float,3> (fine K x: x 32 + coefficients 16 + y 32 B per cell)"),
     # the c2 workload with FP16 / BF16 storage of the Galerkin stencil tables
     "c2h": dict(workload=WORKLOAD + "; Galerkin tables stored as FP16 pairs (FP32 accumulation)",
                 media=lambda: media(), kw=dict(coef_half=1), rows_l1_bytes=87 * 4 + 24 + 24,
@@ -77,6 +92,12 @@ OTHER = {
     "c2b": dict(workload=WORKLOAD + "; Galerkin tables stored as BF16 pairs (FP32 accumulation)",
                 media=lambda: media(), kw=dict(coef_half=2), rows_l1_bytes=87 * 4 + 24 + 24,
                 kernel="k_st_rows<float,__nv_bfloat162,2,1> (Galerkin level 1, all rows)"),
+    # the c2 workload in the plain FP64 GPU form: complex128 W-cycle and FP64 Krylov
+    "c4b": None,   # filled below: c4 with BF16 Galerkin tables
+    "c2f64": dict(workload=WORKLOAD.replace("complex64 W(1,1)", "complex128 W(1,1)").replace(
+                      "FP64-class (double-float) FGMRES", "FP64 FGMRES") + "; plain FP64 GPU form",
+                  media=lambda: media(), kw=dict(prec=0), rows_l1_bytes=87 * 16 + 48 + 48,
+                  kernel="k_st_rows<double,2,1> (Galerkin level 1, all rows)"),
     # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
     "c1": dict(
         workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "
@@ -87,9 +108,17 @@ OTHER = {
 }
 
 
-def rhs(meds):
+def rhs(meds, nrhs=1):
+    """nrhs right-hand sides per medium (the medium's first nrhs sources)."""
     from paper_1806_11277_gb300 import synth
-    return np.stack([synth.point_rhs(m.shape, m.sources)[0] for m in meds])
+    out = []
+    for m in meds:
+        out += synth.point_rhs(m.shape, m.sources[:nrhs])
+    return np.stack(out)
+
+
+OTHER["c4b"] = dict(OTHER["c4"], workload=OTHER["c4"]["workload"] + "; Galerkin tables stored as BF16 pairs",
+                    kw=dict(OTHER["c4"]["kw"], coef_half=2))
 
 
 def peaks():
@@ -214,6 +243,17 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU leg
+def max_over_ranks(total, dist, dev):
+    """Whole-job time: the maximum of the ranks' timed totals (replicas, weak scaling)."""
+    if not dist:
+        return total
+    import torch
+    t = torch.tensor([total], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     from paper_1806_11277_gb300 import ehs
@@ -235,13 +275,14 @@ def run_gpu(args):
     kw = dict(levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=ehs.EHS_C64, cycle=CYCLE)
     if cfg is not None:
         kw.update(cfg["kw"])
-    nsolve = len(meds)
+    nsolve = len(meds) * (1 if cfg is None else cfg.get("nrhs", 1))
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         S = ehs.solver_for(meds, stream=stream.cuda_stream, **kw)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    q_host = rhs(meds)
+    nrhs = 1 if cfg is None else cfg.get("nrhs", 1)
+    q_host = rhs(meds, nrhs)
     qd = torch.from_numpy(q_host).to(dev)
     ud = torch.zeros_like(qd)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -249,7 +290,8 @@ def run_gpu(args):
         # roofline of the dominant kernel family, the Galerkin-level stencil rows
         # (k_st_rows): one launch = ehs_op_apply on level 1 (all rows, every cell),
         # one launch per sample, L2 flushed before each, events on the solver's stream
-        shp1 = S.level_shape(1)
+        lvl = 1 if cfg is None else cfg.get("roof_level", 1)
+        shp1 = S.level_shape(lvl)
         ncell1 = int(np.prod(shp1[2:])) * nsolve
         x1 = torch.randn(shp1, dtype=torch.complex64 if kw["prec"] == ehs.EHS_C64 else torch.complex128, device=dev)
         x1[:, 0, ..., 0] = 0         # boundary slots: u_k at i_k = 0
@@ -268,7 +310,7 @@ def run_gpu(args):
                 # are queued behind it: no host gap lands inside the events
                 flush.fill_(1)
                 e0.record(stream)
-                S.op_apply(x1, y1, level=1)
+                S.op_apply(x1, y1, level=lvl)
                 e1.record(stream)
             e1.synchronize()
             kt.append(e0.elapsed_time(e1) / 1e3)
@@ -316,12 +358,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     launches = ehs.kernel_launches() - l0
     clk = clocks.stop()
-    total = sum(times)
-    if dist:
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-        dist.barrier()
+    total = max_over_ranks(sum(times), dist, dev)
     solves = nsolve * args.steps * world
     value = solves / total
     its = [i["iters"] for i in info]

@@ -65,6 +65,7 @@ struct Hier {
   double wp_ratio = 1;
   int nu1 = 1, nu2 = 1, cyc = 1;
   int half = 0;                // Galerkin tables of the complex64 cycle: 0 complex64, 1 FP16, 2 BF16
+  bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
   void* cfdf = nullptr;        // df64 coefficients (outer-Krylov operator of the global problem)
@@ -155,10 +156,20 @@ Grid mkgrid(int d, int nx, int ny, int nz) {
 // ------------------------------------------------------------ hierarchy
 template <typename T> void autotune_rows(ehs_ctx* c, Hier& H);
 
-void build_hier(ehs_ctx* c, Hier& H) {
+// Builds the hierarchy of H from H.cf64.  precs: work buffers for the FP64
+// cycle (bit 0) and the complex64 cycle (bit 1).  coef_only: only the fine
+// coefficients (the global problem of a DD context, whose cycles run on the
+// subdomain hierarchies).
+void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
   const int d = H.g0.d;
   H.cf32 = dalloc<Coef4<float>>(c, (size_t)H.nsets * H.g0.ncell);
   launch_coef_cast<float>((long long)H.nsets * H.g0.ncell, H.cf64, H.cf32, c->s); cnt(); post();
+  if (coef_only) {
+    H.lv.resize(1);
+    H.lv[0].g = H.g0;
+    H.coef_only = true;
+    return;
+  }
   H.lv.resize(H.nlev);
   Grid g = H.g0;
   for (int l = 0; l < H.nlev; ++l) {
@@ -167,8 +178,8 @@ void build_hier(ehs_ctx* c, Hier& H) {
     L.w = c->opt.w[l < 8 ? l : 7];
     const long long nv = (long long)H.items * (d + 1) * g.ncell;
     for (int k = 0; k < 4; ++k) {
-      L.ws[0][k] = dalloc<double2>(c, nv);
-      L.ws[1][k] = dalloc<float2>(c, nv);
+      if (precs & 1) L.ws[0][k] = dalloc<double2>(c, nv);
+      if (precs & 2) L.ws[1][k] = dalloc<float2>(c, nv);
     }
     if (l + 1 < H.nlev) g = mkgrid(d, g.n[0] / 2, g.n[1] / 2, g.n[2] / 2);
   }
@@ -212,8 +223,8 @@ void build_hier(ehs_ctx* c, Hier& H) {
   dfree(c, M); dfree(c, fb); dfree(c, pv); dfree(c, derr);
   if (herr & EHS_DEVERR_BOX) throw CudaError("Galerkin stencil fell outside its box");
   if (herr & EHS_DEVERR_SINGULAR) throw ArgError("coarsest Galerkin operator is singular");
-  autotune_rows<float>(c, H);
-  autotune_rows<double>(c, H);
+  if (precs & 2) autotune_rows<float>(c, H);
+  if (precs & 1) autotune_rows<double>(c, H);
   if (const char* f = getenv("EHS_ROWS_VARIANT")) {   // fixed launch shape (tests)
     const int v = atoi(f);
     if (v >= 0 && v < ST_ROWS_VARIANTS)
@@ -835,7 +846,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     dfree(c, dl); dfree(c, dm);
     c->d_rho = dr;
     c->d_om = dom;
-    build_hier(c, H);
+    build_hier(c, H, 3, opts->precond == EHS_PRECOND_DD);
     if (opts->precond == EHS_PRECOND_DD) dd_build(c);
     // Krylov workspace
     const int m = opts->restart, items = H.items;
@@ -910,6 +921,7 @@ ehs_status ehs_destroy(ehs_ctx* c) {
 ehs_status ehs_op_apply(ehs_ctx* c, int level, int shifted, int prec, const void* x, void* y) {
   if (!c) return EHS_ERR_ARG;
   return guard(c, [&]() -> ehs_status {
+    if (level > 0 && c->H.coef_only) throw ArgError("a DD context builds no global coarse levels");
     if (level < 0 || level >= c->H.nlev) throw ArgError("level out of range");
     if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
     if (!x || !y) throw ArgError("null vector");
@@ -923,6 +935,7 @@ ehs_status ehs_op_apply(ehs_ctx* c, int level, int shifted, int prec, const void
 ehs_status ehs_smooth(ehs_ctx* c, int level, int nsweeps, int prec, const void* b, void* x) {
   if (!c) return EHS_ERR_ARG;
   return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
     if (level < 0 || level >= c->H.nlev - 1) throw ArgError("level out of range (the coarsest level is solved, not smoothed)");
     if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
     if (!b || !x || nsweeps < 0) throw ArgError("bad argument");
@@ -939,6 +952,7 @@ ehs_status ehs_smooth(ehs_ctx* c, int level, int nsweeps, int prec, const void* 
 ehs_status ehs_vcycle(ehs_ctx* c, int prec, const void* b, void* x) {
   if (!c) return EHS_ERR_ARG;
   return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
     if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
     if (!b || !x) throw ArgError("null vector");
     if (prec == EHS_C128) cycle_rec<double>(c, c->H, 0, (const double2*)b, (double2*)x, false);
@@ -951,7 +965,7 @@ ehs_status ehs_dd_precond(ehs_ctx* c, int prec, const void* r, void* z) {
   if (!c) return EHS_ERR_ARG;
   return guard(c, [&]() -> ehs_status {
     if (c->opt.precond != EHS_PRECOND_DD) throw ArgError("context was not created with the DD preconditioner");
-    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (prec != c->opt.prec) throw ArgError("a DD context runs its subdomain cycles in opts.prec only");
     if (!r || !z) throw ArgError("null vector");
     dd_apply(c, prec, (const double2*)r, (double2*)z);
     return EHS_OK;
@@ -991,11 +1005,11 @@ ehs_status ehs_gradient(ehs_ctx* c, const void* x, const void* w, double* g_lamb
 
 int ehs_items(const ehs_ctx* c) { return c ? c->H.items : 0; }
 long long ehs_level_len(const ehs_ctx* c, int level) {
-  if (!c || level < 0 || level >= c->H.nlev) return -1;
+  if (!c || level < 0 || level >= (int)c->H.lv.size()) return -1;
   return (long long)(c->d + 1) * c->H.lv[level].g.ncell;
 }
 int ehs_level_dims(const ehs_ctx* c, int level, int n[3]) {
-  if (!c || level < 0 || level >= c->H.nlev) return -1;
+  if (!c || level < 0 || level >= (int)c->H.lv.size()) return -1;
   for (int k = 0; k < 3; ++k) n[k] = c->H.lv[level].g.n[k];
   return 0;
 }
