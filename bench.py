@@ -98,6 +98,11 @@ OTHER = {
                       "FP64-class (double-float) FGMRES", "FP64 FGMRES") + "; plain FP64 GPU form",
                   media=lambda: media(), kw=dict(prec=0), rows_l1_bytes=87 * 16 + 48 + 48,
                   kernel="k_st_rows<double,2,1> (Galerkin level 1, all rows)"),
+    # the c2 workload with full cell-block Vanka (closed form on the fine level,
+    # stored complex64 block inverses on the Galerkin levels)
+    "c2v": dict(workload=WORKLOAD + "; full (2d+1)^2 cell-block Vanka instead of the economic block",
+                media=lambda: media(), kw=dict(vanka_full=1), rows_l1_bytes=87 * 8 + 24 + 24,
+                kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
     # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
     "c1": dict(
         workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "

@@ -99,6 +99,12 @@ typedef struct {
   int coef_half;         /* storage of the Galerkin stencil coefficients used by the
                             complex64 cycle: 0 complex64, 1 FP16 pairs, 2 BF16 pairs
                             (products accumulate in FP32; the FP64 masters stay) */
+  int vanka_full;        /* cell-wise relaxation block (Sec. 4.2): 0 economic (eq.
+                            RelaxationMatrix, the default), 1 full (2d+1)^2 block; on
+                            Galerkin levels the full block inverses are formed at setup in
+                            FP64 and stored per colour in the cycle's precision (FP16 /
+                            BF16 pairs with coef_half, as the implementation remark of
+                            Sec. 4 stores them in half precision) */
 } ehs_opts;
 
 typedef struct {

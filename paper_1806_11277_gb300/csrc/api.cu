@@ -53,6 +53,7 @@ struct Level {
   void* tabh = nullptr;       // half-precision copy (FP16 or BF16 pairs) for the complex64 cycle
   double2* inv = nullptr;     // coarsest: [nsets][N][N]
   float4* invdf = nullptr;    // coarsest inverse in complex df64 (used by the complex64 cycle)
+  void* binv[2] = {nullptr, nullptr};  // full Vanka block inverses [prec: 0 double2, 1 float2 or half pairs]
   void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
   int rows_var[2] = {0, 0};      // residual-pass launch shape per precision (setup autotuner)
   double w = 0.5;
@@ -65,6 +66,7 @@ struct Hier {
   double wp_ratio = 1;
   int nu1 = 1, nu2 = 1, cyc = 1;
   int half = 0;                // Galerkin tables of the complex64 cycle: 0 complex64, 1 FP16, 2 BF16
+  int full = 0;                // 1: full cell-block Vanka instead of the economic block
   bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
@@ -205,6 +207,24 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
     Lf = L.L;
     tf = L.tab64;
   }
+  // full Vanka: block inverses of every smoothed Galerkin level (FP64, then the cycle's formats)
+  for (int l = 1; H.full && l + 1 < H.nlev; ++l) {
+    Level& L = H.lv[l];
+    const long long nb = (long long)H.nsets * 2 * (2 * d + 1) * (2 * d + 1) * (L.g.ncell / 2);
+    double2* b64 = dalloc<double2>(c, nb);
+    launch_block_inv(L.g, H.nsets, L.L, L.tab64, b64, derr, c->s); cnt(); post();
+    if (precs & 2) {
+      if (H.half) {
+        L.binv[1] = dalloc<float>(c, nb);
+        launch_table_half(nb, b64, L.binv[1], H.half, c->s); cnt(); post();
+      } else {
+        L.binv[1] = dalloc<float2>(c, nb);
+        launch_table_cast<float>(nb, b64, (float2*)L.binv[1], c->s); cnt(); post();
+      }
+    }
+    if (precs & 1) L.binv[0] = b64;
+    else dfree(c, b64);
+  }
   // coarsest: dense FP64 inverse
   Level& C = H.lv[H.nlev - 1];
   const long long N = (long long)(d + 1) * C.g.ncell;
@@ -269,16 +289,23 @@ void level_sweep(ehs_ctx* c, const Hier& H, int l, const typename CT<T>::type* b
   const Level& L = H.lv[l];
   const T wu = (T)L.w, wp = (T)(L.w * H.wp_ratio);
   if (l == 0) {
-    launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 0, b, x, t, c->s);
-    launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 1, b, t, x, c->s);
+    launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 0, b, x, t, c->s, H.full);
+    launch_fine_vanka<T>(L.g, H.items, H.nrhs, cfp<T>(H), H.h, H.alpha, wu, wp, 1, b, t, x, c->s, H.full);
   } else {
     typedef typename CT<T>::type C;
     C* rb = (C*)L.ws[PT<T>::i][3];
     int fmt = 0;
     const void* tab = tabp<T>(H, L, &fmt);
     const int var = L.rows_var[PT<T>::i];
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 0, b, x, t, rb, var, c->s);
-    launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 1, b, t, x, rb, var, c->s);
+    if (H.full) {
+      const void* bi = L.binv[PT<T>::i];
+      const int bfmt = sizeof(T) == 4 ? H.half : 0;
+      launch_st_vanka_full<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, bi, bfmt, wu, wp, 0, b, x, t, rb, var, c->s);
+      launch_st_vanka_full<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, bi, bfmt, wu, wp, 1, b, t, x, rb, var, c->s);
+    } else {
+      launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 0, b, x, t, rb, var, c->s);
+      launch_st_vanka<T>(L.g, H.items, H.nrhs, L.L, tab, fmt, wu, wp, 1, b, t, x, rb, var, c->s);
+    }
     cnt(2);
   }
   cnt(2); post();
@@ -381,6 +408,7 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (P->abl_cells < 0 || 2 * P->abl_cells > P->n[0]) throw ArgError("bad abl_cells");
   if (O->precond != EHS_PRECOND_MG && O->precond != EHS_PRECOND_DD) throw ArgError("bad precond");
   if (O->coef_half < 0 || O->coef_half > 2) throw ArgError("coef_half must be 0, 1 (FP16) or 2 (BF16)");
+  if (O->vanka_full != 0 && O->vanka_full != 1) throw ArgError("vanka_full must be 0 or 1");
 }
 
 void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* rho, long long n) {
@@ -822,6 +850,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     H.wp_ratio = opts->wp_ratio > 0 ? opts->wp_ratio : 1.0;
     H.nu1 = opts->nu_pre; H.nu2 = opts->nu_post; H.cyc = opts->cycle;
     H.half = opts->coef_half;
+    H.full = opts->vanka_full;
     c->n0 = (long long)(c->d + 1) * H.g0.ncell;
     const long long nc = (long long)H.nsets * H.g0.ncell;
     check_media(c, prob->lambda, prob->mu, prob->rho, nc);

@@ -120,11 +120,18 @@ __global__ void k_fine_apply(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, 
   y[vo + (long long)D * N + c] = r;
 }
 
-// One colour of red-black economic Vanka.  Thread = pair of cells along x
-// (2t, 2t+1); the one of the requested colour is relaxed, the other one's p is
-// copied.  All u faces are written (each face belongs to exactly one cell of
-// each colour), so xo is a complete new iterate.
-template <typename T, int D>
+// One colour of red-black cell-wise Vanka (Sec. 4.2).  Thread = pair of cells
+// along x (2t, 2t+1); the one of the requested colour is relaxed, the other
+// one's p is copied.  All u faces are written (each face belongs to exactly one
+// cell of each colour), so xo is a complete new iterate.
+// FULL = false: economic block (eq. RelaxationMatrix: diagonal of the
+// displacement block, displacement-pressure couplings, pressure diagonal).
+// FULL = true: the whole (2d+1)^2 block of K_s.  On the fine level the only
+// displacement couplings inside one cell are between the low and high face of
+// the same component, K[u_k(c), u_k(c+e_k)] = -mu_c/h^2 (the normal difference
+// across the cell), so the block is an arrowhead with d 2x2 diagonal blocks and
+// is solved in closed form through the pressure Schur complement.
+template <typename T, int D, bool FULL>
 __global__ void k_fine_vanka(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, FineP<T> P,
                              T wu, T wp, int colour, const typename CT<T>::type* __restrict__ b,
                              const typename CT<T>::type* __restrict__ xi,
@@ -174,7 +181,52 @@ __global__ void k_fine_vanka(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, 
     g_[D + k] = mk<T>(-P.hinv, 0);       // K[u_k(c+e_k), p(c)] = -1/h
   }
   r[2 * D] = csub(ldc(bb + (long long)D * N, c), row_p<T, D>(g, c, i, c0, x, P));
-  // arrowhead solve: B = [[diag(dg), g], [g^T, -kap]]
+  if constexpr (FULL) {
+    // B = [[A, g], [g^T, -kap]], A = blockdiag_k [[dg_lo, e], [e, dg_hi]], e = -mu_c/h^2.
+    // s = A^{-1} r_u, q = A^{-1} g; dp = (r_p - g.s) / (-kap - g.q); du = s - q dp.
+    const T e = -c0.mu * P.h2inv;
+    C sch = mk<T>(-c0.kap, 0);
+    C rp = r[2 * D];
+    C sv[2 * D], qv[2 * D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int lo = k, hi = D + k;
+      if (ok[lo] && ok[hi]) {
+        const C det = csub(cmul(dg[lo], dg[hi]), mk<T>(e * e, 0));
+        const C di = cinv(det);
+        sv[lo] = cmul(di, csub(cmul(dg[hi], r[lo]), cscale(r[hi], e)));
+        sv[hi] = cmul(di, csub(cmul(dg[lo], r[hi]), cscale(r[lo], e)));
+        qv[lo] = cmul(di, csub(cmul(dg[hi], g_[lo]), cscale(g_[hi], e)));
+        qv[hi] = cmul(di, csub(cmul(dg[lo], g_[hi]), cscale(g_[lo], e)));
+      } else {
+#pragma unroll
+        for (int a = lo; a <= hi; a += D) {
+          if (!ok[a]) { sv[a] = czero<C>(); qv[a] = czero<C>(); continue; }
+          const C dinv = cinv(dg[a]);
+          sv[a] = cmul(r[a], dinv);
+          qv[a] = cmul(g_[a], dinv);
+        }
+      }
+#pragma unroll
+      for (int a = lo; a <= hi; a += D) {
+        if (!ok[a]) continue;
+        sch = csub(sch, cmul(g_[a], qv[a]));
+        rp = csub(rp, cmul(g_[a], sv[a]));
+      }
+    }
+    const C dp = cmul(rp, cinv(sch));
+    xout[(long long)D * N + c] = cfma(mk<T>(wp, 0), dp, ldc(x + (long long)D * N, c));
+#pragma unroll
+    for (int a = 0; a < 2 * D; ++a) {
+      if (!ok[a]) continue;
+      const int k = a % D;
+      const long long idx = (long long)k * N + c + (a >= D ? stride_of(g, k) : 0);
+      const C du = csub(sv[a], cmul(qv[a], dp));
+      xout[idx] = cfma(mk<T>(wu, 0), du, ldc(x, idx));
+    }
+    return;
+  }
+  // economic arrowhead solve: B = [[diag(dg), g], [g^T, -kap]]
   C sch = mk<T>(-c0.kap, 0);
   C rp = r[2 * D];
   C dinv[2 * D];
@@ -378,14 +430,17 @@ template <typename T>
 void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, double h,
                        double alpha, T wu, T wp, int colour,
                        const typename CT<T>::type* b, const typename CT<T>::type* xi,
-                       typename CT<T>::type* xo, cudaStream_t s) {
+                       typename CT<T>::type* xo, cudaStream_t s, int full) {
   const FineP<T> P = mkP<T>(h, alpha);
   const long long np = g.ncell / 2;
   const dim3 gr((unsigned)((np + 127) / 128), sel_items(items));
-  if (g.d == 2)
-    k_fine_vanka<T, 2><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
-  else
-    k_fine_vanka<T, 3><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
+  if (g.d == 2) {
+    if (full) k_fine_vanka<T, 2, true><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
+    else k_fine_vanka<T, 2, false><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
+  } else {
+    if (full) k_fine_vanka<T, 3, true><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
+    else k_fine_vanka<T, 3, false><<<gr, 128, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
+  }
 }
 
 void fine_table_layout(int d, StencilLayout* L) { *L = make_fine_layout(d); }
@@ -411,7 +466,7 @@ void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double
                                      CT<T>::type*, int, cudaStream_t);                             \
   template void launch_fine_vanka<T>(const Grid&, int, int, const Coef4<T>*, double,              \
                                      double, T, T, int, const CT<T>::type*, const CT<T>::type*,    \
-                                     CT<T>::type*, cudaStream_t);
+                                     CT<T>::type*, cudaStream_t, int);
 INST(float)
 INST(double)
 #undef INST

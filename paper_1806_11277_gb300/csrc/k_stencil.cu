@@ -420,6 +420,126 @@ __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const TT* __r
   }
 }
 
+// Full cell-wise Vanka on a Galerkin level (Sec. 4.2, with the setup-time
+// block inversion of the implementation remark in Sec. 4): the cell block is
+// B_c = K_c[I_c, I_c] over the 2d faces and the pressure of cell c, all
+// couplings kept.  DOF a of the block: a < d the low face of u_a (cell c),
+// d <= a < 2d the high face of u_{a-d} (cell c + e_{a-d}), 2d the pressure.
+// Boundary faces are not unknowns: their rows and columns are the identity.
+// Output layout per set: [colour][a * (2d+1) + b][t], t = cell pair index, so
+// the update pass of one colour reads its inverses contiguously.
+template <int D, int LV>
+__global__ void k_block_inv(Grid g, const double2* __restrict__ tab, double2* __restrict__ out,
+                            int* __restrict__ err) {
+  constexpr StencilLayout L = level_layout(D, LV);
+  constexpr int NB = 2 * D + 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long N = g.ncell, H = N / 2;
+  if (t >= H) return;
+  const int set = blockIdx.y, colour = blockIdx.z;
+  const double2* ts = tab + (long long)set * L.nslot * N;
+  long long c = 2 * t;
+  int i[3];
+  cell_coords(g, c, i);
+  if (((i[0] + i[1] + i[2]) & 1) != colour) { ++c; ++i[0]; }
+  int comp[NB], off[NB][3];
+  bool ok[NB];
+  long long cell[NB];
+  for (int a = 0; a < NB; ++a) {
+    const int k = a < D ? a : (a < 2 * D ? a - D : D);
+    comp[a] = k;
+    off[a][0] = off[a][1] = off[a][2] = 0;
+    cell[a] = c;
+    if (a < D) ok[a] = i[k] >= 1;
+    else if (a < 2 * D) { ok[a] = i[k] + 1 < g.n[k]; off[a][k] = 1; cell[a] = c + stride_of(g, k); }
+    else ok[a] = true;
+  }
+  double2 M[NB][2 * NB];   // [B | I] reduced to [I | B^{-1}]
+  for (int a = 0; a < NB; ++a)
+    for (int b = 0; b < NB; ++b) {
+      double2 v = make_double2(a == b ? 1.0 : 0.0, 0.0);
+      if (ok[a] && ok[b]) {
+        const int sl = st_slot(L, comp[a], comp[b], off[b][0] - off[a][0], off[b][1] - off[a][1],
+                               off[b][2] - off[a][2]);
+        v = sl >= 0 ? ts[(long long)sl * N + cell[a]] : make_double2(0.0, 0.0);
+      }
+      M[a][b] = v;
+      M[a][NB + b] = make_double2(a == b ? 1.0 : 0.0, 0.0);
+    }
+  for (int k = 0; k < NB; ++k) {          // Gauss-Jordan with partial pivoting
+    int pr = k;
+    double best = M[k][k].x * M[k][k].x + M[k][k].y * M[k][k].y;
+    for (int a = k + 1; a < NB; ++a) {
+      const double m2 = M[a][k].x * M[a][k].x + M[a][k].y * M[a][k].y;
+      if (m2 > best) { best = m2; pr = a; }
+    }
+    if (!(best > 0.0)) { atomicOr(err, EHS_DEVERR_SINGULAR); return; }
+    if (pr != k)
+      for (int b = 0; b < 2 * NB; ++b) { const double2 tmp = M[k][b]; M[k][b] = M[pr][b]; M[pr][b] = tmp; }
+    const double2 piv = cinv(M[k][k]);
+    for (int b = 0; b < 2 * NB; ++b) M[k][b] = cmul(M[k][b], piv);
+    for (int a = 0; a < NB; ++a) {
+      if (a == k) continue;
+      const double2 f = M[a][k];
+      for (int b = 0; b < 2 * NB; ++b) M[a][b] = csub(M[a][b], cmul(f, M[k][b]));
+    }
+  }
+  double2* o = out + ((long long)set * 2 + colour) * NB * NB * H + t;
+  for (int a = 0; a < NB; ++a)
+    for (int b = 0; b < NB; ++b) o[(long long)(a * NB + b) * H] = M[a][NB + b];
+}
+
+// Update pass of one colour with the stored full block inverses (storage TI:
+// complex T, or FP16 / BF16 pairs widened to FP32): x[I_c] += W B_c^{-1} r[I_c].
+template <typename T, typename TI, int D>
+__global__ void __launch_bounds__(128) k_st_vupd_full(Grid g, int nrhs, const TI* __restrict__ binv,
+                                                      T wu, T wp, int colour,
+                                                      const typename CT<T>::type* __restrict__ res,
+                                                      const typename CT<T>::type* __restrict__ xi,
+                                                      typename CT<T>::type* __restrict__ xo,
+                                                      const int* __restrict__ il) {
+  typedef typename CT<T>::type Cx;
+  constexpr int NB = 2 * D + 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long N = g.ncell, H = N / 2;
+  if (t >= H) return;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  const long long vo = (long long)item * (D + 1) * N;
+  const TI* bs = binv + ((long long)(item / nrhs) * 2 + colour) * NB * NB * H + t;
+  const Cx* x = xi + vo;
+  const Cx* rr = res + vo;
+  Cx* xout = xo + vo;
+  long long c = 2 * t;
+  int i[3];
+  cell_coords(g, c, i);
+  if (((i[0] + i[1] + i[2]) & 1) != colour) { ++c; ++i[0]; }
+  const long long co = (c & 1) ? c - 1 : c + 1;
+  xout[(long long)D * N + co] = __ldg(x + (long long)D * N + co);
+  Cx r[NB];
+  long long idx[NB];
+  bool ok[NB];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    idx[k] = (long long)k * N + c;
+    idx[D + k] = (long long)k * N + c + stride_of(g, k);
+    ok[k] = i[k] >= 1;
+    ok[D + k] = i[k] + 1 < g.n[k];
+  }
+  idx[2 * D] = (long long)D * N + c;
+  ok[2 * D] = true;
+#pragma unroll
+  for (int a = 0; a < NB; ++a) r[a] = ok[a] ? __ldg(rr + idx[a]) : czero<Cx>();
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    if (!ok[a]) continue;
+    Cx acc = czero<Cx>();
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (ok[b]) acc = cfma(ldtab<T>(bs + (long long)(a * NB + b) * H), r[b], acc);
+    xout[idx[a]] = cfma(mk<T>(a < 2 * D ? wu : wp, 0), acc, __ldg(x + idx[a]));
+  }
+}
+
 inline dim3 grid1(long long n, int items, int bs) { return dim3((unsigned)((n + bs - 1) / bs), items, 1); }
 
 }  // namespace
@@ -553,6 +673,46 @@ void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaS
   k_table_half<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out, fmt);
 }
 
+void launch_block_inv(const Grid& g, int nsets, const StencilLayout& L, const double2* tab, double2* out,
+                      int* err, cudaStream_t s) {
+  const dim3 gr((unsigned)((g.ncell / 2 + 63) / 64), nsets, 2);
+  const int v = layout_variant(L, g.d);
+  if (g.d == 2) {
+    if (v == 1) k_block_inv<2, 1><<<gr, 64, 0, s>>>(g, tab, out, err);
+    else k_block_inv<2, 2><<<gr, 64, 0, s>>>(g, tab, out, err);
+  } else {
+    if (v == 1) k_block_inv<3, 1><<<gr, 64, 0, s>>>(g, tab, out, err);
+    else k_block_inv<3, 2><<<gr, 64, 0, s>>>(g, tab, out, err);
+  }
+}
+
+template <typename T, typename TI>
+static void st_vupd_full_t(const Grid& g, int items, int nrhs, const TI* binv, T wu, T wp, int colour,
+                           const typename CT<T>::type* r, const typename CT<T>::type* xi,
+                           typename CT<T>::type* xo, cudaStream_t s) {
+  const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), sel_items(items), 1);
+  if (g.d == 2) k_st_vupd_full<T, TI, 2><<<gu, 128, 0, s>>>(g, nrhs, binv, wu, wp, colour, r, xi, xo, g_sel.list);
+  else k_st_vupd_full<T, TI, 3><<<gu, 128, 0, s>>>(g, nrhs, binv, wu, wp, colour, r, xi, xo, g_sel.list);
+}
+
+// one colour of red-black full Vanka on a Galerkin level: residual pass, then
+// the update with the stored block inverses binv (format bfmt as for tables)
+template <typename T>
+void launch_st_vanka_full(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
+                          const void* binv, int bfmt, T wu, T wp, int colour, const typename CT<T>::type* b,
+                          const typename CT<T>::type* xi, typename CT<T>::type* xo, typename CT<T>::type* rbuf,
+                          int var, cudaStream_t s) {
+  const int v = layout_variant(L, g.d);
+  st_apply_any<T>(g, items, nrhs, v, tab, fmt, xi, b, rbuf, 1, colour, var, s);
+  if constexpr (sizeof(T) == 4) {
+    if (bfmt == 1) return st_vupd_full_t<T, __half2>(g, items, nrhs, (const __half2*)binv, wu, wp, colour, rbuf, xi, xo, s);
+    if (bfmt == 2)
+      return st_vupd_full_t<T, __nv_bfloat162>(g, items, nrhs, (const __nv_bfloat162*)binv, wu, wp, colour, rbuf, xi, xo, s);
+  }
+  st_vupd_full_t<T, typename CT<T>::type>(g, items, nrhs, (const typename CT<T>::type*)binv, wu, wp, colour, rbuf, xi,
+                                          xo, s);
+}
+
 #define INST(T)                                                                                   \
   template void launch_table_cast<T>(long long, const double2*, CT<T>::type*, cudaStream_t);       \
   template void launch_st_apply<T>(const Grid&, int, int, const StencilLayout&, const void*, int,   \
@@ -560,7 +720,10 @@ void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaS
                                    cudaStream_t);                                                   \
   template void launch_st_vanka<T>(const Grid&, int, int, const StencilLayout&, const void*, int, T, \
                                    T, int, const CT<T>::type*, const CT<T>::type*, CT<T>::type*,    \
-                                   CT<T>::type*, int, cudaStream_t);
+                                   CT<T>::type*, int, cudaStream_t); \
+  template void launch_st_vanka_full<T>(const Grid&, int, int, const StencilLayout&, const void*, int, \
+                                        const void*, int, T, T, int, const CT<T>::type*,               \
+                                        const CT<T>::type*, CT<T>::type*, CT<T>::type*, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

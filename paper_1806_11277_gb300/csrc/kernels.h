@@ -49,7 +49,7 @@ template <typename T>
 void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, double h,
                        double alpha, T wu, T wp, int colour,
                        const typename CT<T>::type* b, const typename CT<T>::type* xi,
-                       typename CT<T>::type* xo, cudaStream_t s);
+                       typename CT<T>::type* xo, cudaStream_t s, int full = 0);
 // level-0 stencil table (double) of K_s for the Galerkin setup
 void fine_table_layout(int d, StencilLayout* L);
 void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double h,
@@ -76,6 +76,16 @@ template <typename T>
 void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
                      T wu, T wp, int colour, const typename CT<T>::type* b, const typename CT<T>::type* xi,
                      typename CT<T>::type* xo, typename CT<T>::type* rbuf, int var, cudaStream_t s);
+// full Vanka (whole cell block): setup inverses of a smoothed Galerkin level,
+// out [nsets][2 colours][(2d+1)^2][ncell/2] complex FP64; err gets EHS_DEVERR_SINGULAR
+void launch_block_inv(const Grid& g, int nsets, const StencilLayout& L, const double2* tab, double2* out,
+                      int* err, cudaStream_t s);
+// one colour of red-black full Vanka on a Galerkin level (binv in format bfmt, as fmt for tables)
+template <typename T>
+void launch_st_vanka_full(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
+                          const void* binv, int bfmt, T wu, T wp, int colour, const typename CT<T>::type* b,
+                          const typename CT<T>::type* xi, typename CT<T>::type* xo, typename CT<T>::type* rbuf,
+                          int var, cudaStream_t s);
 
 // ---- transfer -------------------------------------------------------------
 template <typename T>

@@ -35,7 +35,8 @@ class Opts(C.Structure):
                 ("cycle", C.c_int), ("restart", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("precond", C.c_int), ("prec", C.c_int), ("nrhs", C.c_int), ("dd", C.c_int * 3),
                 ("dd_overlap", C.c_int), ("dd_pad", C.c_int), ("dd_abl_max", C.c_double),
-                ("coef_half", C.c_int)]
+                ("coef_half", C.c_int),
+                ("vanka_full", C.c_int)]
 
 
 class SolveInfo(C.Structure):

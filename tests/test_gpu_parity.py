@@ -413,3 +413,84 @@ def test_galerkin_rows_launch_shapes_agree(variant, monkeypatch):
         qo = op.slots_to_dofs(q[it], med.shape)
         _, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
         assert abs(info[it]["iters"] - io["iters"]) <= 1
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_full_vanka_smooth_matches_oracle(case):
+    """Full cell-block Vanka (closed form on the fine level, stored FP64-built
+    inverses on Galerkin levels) against the oracle's dense block inverses."""
+    ehs = _ehs()
+    meds = _media_2d(32, 2) if case == "2d" else _media_3d(16, 1)
+    levels = 3
+    S = ehs.solver_for(meds, levels=levels, alpha=0.2, vanka_full=1)
+    for l in range(levels - 1):
+        gshape = tuple(S.level_shape(l)[2:])
+        b_ = _rand_slots(gshape, S.items, 40 + l)
+        x_ = _rand_slots(gshape, S.items, 50 + l)
+        for dt, tol in ((torch.complex128, 1e-11), (torch.complex64, 2e-5)):
+            bd = torch.from_numpy(b_).to("cuda", dt)
+            xd = torch.from_numpy(x_).to("cuda", dt)
+            S.smooth(bd, xd, level=l, nsweeps=1)
+            for it, med in enumerate(meds):
+                H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels, economic=False)
+                be = op.slots_to_dofs(bd[it].cpu().numpy().astype(np.complex128), gshape)
+                xe = op.slots_to_dofs(torch.from_numpy(x_[it]).to(dt).numpy().astype(np.complex128), gshape)
+                xr = op.dofs_to_slots(H.relax(l, be, xe), gshape)
+                assert _rel(xd[it].cpu().numpy(), xr) <= tol, (l, dt, it, _rel(xd[it].cpu().numpy(), xr))
+    S.close()
+
+
+@pytest.mark.parametrize("fmt,tol", [(1, 3e-3), (2, 2e-2)])
+def test_full_vanka_half_inverses(fmt, tol):
+    """Block inverses stored as FP16 / BF16 pairs (the half-precision storage of
+    Sec. 4's implementation remark): one Galerkin-level sweep within the
+    storage rounding of the FP64 result."""
+    ehs = _ehs()
+    meds = _media_2d(32, 1)
+    S = ehs.solver_for(meds, levels=3, alpha=0.2, vanka_full=1, coef_half=fmt)
+    gshape = tuple(S.level_shape(1)[2:])
+    b_ = _rand_slots(gshape, S.items, 61)
+    x_ = _rand_slots(gshape, S.items, 62)
+    bd = torch.from_numpy(b_).to("cuda", torch.complex64)
+    xd = torch.from_numpy(x_).to("cuda", torch.complex64)
+    S.smooth(bd, xd, level=1, nsweeps=1)
+    H = mg.Hierarchy(_oracle_parts(meds[0], 0.2), meds[0].shape, 3, economic=False)
+    xr = op.dofs_to_slots(H.relax(1, op.slots_to_dofs(b_[0], gshape), op.slots_to_dofs(x_[0], gshape)), gshape)
+    err = _rel(xd[0].cpu().numpy(), xr)
+    assert err <= tol, err
+    S.close()
+
+
+@pytest.mark.parametrize("prec_name", ["c128", "c64"])
+def test_full_vanka_fgmres_matches_oracle(prec_name):
+    ehs = _ehs()
+    prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
+    meds = _media_2d(64, 2)
+    q, u, info = _solve_both(meds, 4, prec, alpha=0.4, cycle=2, vanka_full=1)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25], economic=False)
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        assert info[it]["converged"]
+        if prec == ehs.EHS_C128:
+            assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
+        else:
+            assert abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_full_vanka_dd_fgmres():
+    """DD whose subdomain cycles use full Vanka: same iteration count and
+    solution as the oracle DD with full-block subdomain smoothers."""
+    ehs = _ehs()
+    med = synth.homogeneous_2d()
+    q, u, info = _solve_both([med], 3, ehs.EHS_C128, precond=ehs.EHS_PRECOND_DD, dd=(2, 2, 1),
+                             dd_overlap=4, dd_pad=8, vanka_full=1)
+    D = odd.DD(med, (2, 2), 4, 8, 3, 0.2, economic=False)
+    qo = op.slots_to_dofs(q[0], med.shape)
+    xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
+    ug = op.slots_to_dofs(u[0], med.shape)
+    assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
+    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
