@@ -143,7 +143,8 @@ class DD:
     """Multicolour DD preconditioner for the unshifted global K."""
 
     def __init__(self, medium, nsub, overlap, pad, levels, alpha, dd_abl_max=1.0,
-                 local="mg", w=None, economic=True, abl_max=1.0, gamma_add=0.01 * np.pi):
+                 local="mg", w=None, economic=True, abl_max=1.0, gamma_add=0.01 * np.pi,
+                 coarse_dd=None):
         shape = medium.lam.shape
         d = len(shape)
         self.shape = shape
@@ -161,7 +162,8 @@ class DD:
             sd.ndof = sum(op.dof_sizes(sd.shape))
             if local == "mg":
                 Ks = op.assemble_mixed(lparts, alpha)
-                sd.hier = Hierarchy(Ks, sd.shape, levels, w=w, economic=economic)
+                sd.hier = Hierarchy(Ks, sd.shape, levels, w=w, economic=economic,
+                                    coarse_dd=coarse_dd)   # DD-MG-DD with coarse_dd (Sec. 4)
                 sd.solve = lambda r, H=sd.hier: H.cycle(r)
             else:                                      # exact local solve of H_i
                 lu = spla.splu(op.assemble_mixed(lparts, 0.0).tocsc())

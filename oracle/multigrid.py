@@ -12,7 +12,9 @@
   (Sec. 3; economic block = eq. RelaxationMatrix), red-black or
   lexicographic cell order.
 * Cycle: Algorithm TwoCycle applied recursively (once: V, twice: W); the
-  coarsest level is solved exactly with a sparse LU.
+  coarsest level is solved exactly with a sparse LU, or (MG-DD, Sec. 4) by
+  one multiplicative sweep of Algorithm DD over subdomains of the coarsest
+  grid with exact local solves (`CoarseDD`).
 """
 from __future__ import annotations
 
@@ -171,6 +173,83 @@ class Level:
         return x
 
 
+# ------------------------------------------------------ coarse-grid DD
+def near_equal_edges(n, s):
+    """Edges of s nearly equal consecutive parts of n cells (larger parts first)."""
+    base, rem = divmod(n, s)
+    edges = [0]
+    for i in range(s):
+        edges.append(edges[-1] + base + (1 if i < rem else 0))
+    return edges
+
+
+def box_dofs(shape, lo, hi):
+    """Oracle DOF numbers of the unknowns inside the cell box [lo, hi) (numpy
+    axis order): the pressures of its cells and the faces whose two cells both
+    lie in the box.  Faces on the box surface are not unknowns of the local
+    problem (homogeneous Dirichlet), as on the outer boundary."""
+    d = len(shape)
+    out = []
+    off = 0
+    for k in range(d):
+        cs = comp_shape(shape, k)
+        ak = d - 1 - k
+        # u_k array index j along axis ak is the face between cells j and j+1
+        rng = [np.arange(lo[a], hi[a]) if a != ak else np.arange(lo[a], hi[a] - 1) for a in range(d)]
+        grid = np.meshgrid(*rng, indexing="ij")
+        lin = np.ravel_multi_index(tuple(g.ravel() for g in grid), cs)
+        out.append(off + lin)
+        off += int(np.prod(cs))
+    grid = np.meshgrid(*[np.arange(lo[a], hi[a]) for a in range(d)], indexing="ij")
+    out.append(off + np.ravel_multi_index(tuple(g.ravel() for g in grid), shape))
+    return np.sort(np.concatenate(out))
+
+
+class CoarseDD:
+    """Algorithm DD as the coarsest-grid solver of MG-DD (Sec. 4), applied to
+    the assembled coarsest Galerkin operator.
+
+    Readings: cores split each direction into nsub near-equal parts
+    (nsub in direction order x, y, z); Omega_i = core grown by `overlap` cells
+    on every side, clipped to the grid; the local matrix is the coarsest
+    operator restricted to the unknowns inside Omega_i (`box_dofs`), solved
+    exactly; colours by the parity of the subdomain index along each
+    direction, c = sum_k 2^k (i_k mod 2), visited in increasing order; the
+    residual is recomputed before each colour and the subdomains of one colour
+    are corrected from that same residual; one sweep from a zero guess.
+    """
+
+    def __init__(self, K, shape, nsub, overlap):
+        d = len(shape)
+        self.K = K.tocsr()
+        self.subs = []            # (colour, dof indices, LU of the local matrix)
+        edges = [near_equal_edges(shape[d - 1 - k], nsub[k]) for k in range(d)]
+        for sidx in np.ndindex(*[nsub[k] for k in range(d)]):
+            lo = [0] * d
+            hi = [0] * d
+            colour = 0
+            for k in range(d):
+                a = d - 1 - k
+                lo[a] = max(edges[k][sidx[k]] - overlap, 0)
+                hi[a] = min(edges[k][sidx[k] + 1] + overlap, shape[a])
+                colour += (sidx[k] % 2) << k
+            idx = box_dofs(shape, lo, hi)
+            lu = spla.splu(self.K[idx][:, idx].tocsc())
+            self.subs.append((colour, idx, lu))
+        self.colours = sorted({c for c, _, _ in self.subs})
+
+    def solve(self, b):
+        x = np.zeros_like(b)
+        for col in self.colours:
+            r = b - self.K @ x
+            dx = np.zeros_like(b)
+            for c, idx, lu in self.subs:
+                if c == col:
+                    dx[idx] += lu.solve(r[idx])
+            x = x + dx
+        return x
+
+
 # ------------------------------------------------------------- hierarchy
 DEFAULT_W = {2: [0.75], 3: [0.75, 0.5], 4: [0.5, 0.5, 0.2]}
 
@@ -179,7 +258,9 @@ class Hierarchy:
     """Multigrid hierarchy of the shifted operator K_s = K_0, K_{l+1} = P_l^T K_l P_l."""
 
     def __init__(self, Ks, shape, levels, w=None, economic=True, order="rb",
-                 wu=None, wp=None):
+                 wu=None, wp=None, coarse_dd=None):
+        """coarse_dd = (nsub, overlap): MG-DD, the coarsest level solved by
+        one sweep of `CoarseDD` instead of the exact LU."""
         if w is None:
             w = DEFAULT_W.get(levels, [0.75, 0.5] + [0.25] * max(0, levels - 3))
         self.levels = levels
@@ -196,7 +277,12 @@ class Hierarchy:
             self.shapes.append(cs)
         self.lv = [Level(self.K[l], self.shapes[l], w[l], economic, wu, wp)
                    for l in range(levels - 1)]
-        self.lu = spla.splu(self.K[-1].tocsc())
+        if coarse_dd is None:
+            self.lu = spla.splu(self.K[-1].tocsc())
+            self.coarse_solve = self.lu.solve
+        else:
+            self.cdd = CoarseDD(self.K[-1], self.shapes[-1], *coarse_dd)
+            self.coarse_solve = self.cdd.solve
 
     def relax(self, l, b, x):
         lv = self.lv[l]
@@ -205,7 +291,7 @@ class Hierarchy:
     def cycle(self, b, l=0, x=None, nu1=1, nu2=1, gamma=1):
         """Algorithm TwoCycle applied recursively: gamma = 1 V-cycle, 2 W-cycle."""
         if l == self.levels - 1:
-            return self.lu.solve(b)
+            return self.coarse_solve(b)
         x = np.zeros_like(b) if x is None else x.copy()
         for _ in range(nu1):
             x = self.relax(l, b, x)
@@ -214,7 +300,7 @@ class Hierarchy:
         for _ in range(gamma):
             ec = self.cycle(rc, l + 1, ec, nu1, nu2, gamma)
             if l + 1 == self.levels - 1:
-                break                   # an exact coarse solve needs no repeat
+                break                   # one coarsest solve per visit (exact or DD)
         x = x + self.P[l] @ ec
         for _ in range(nu2):
             x = self.relax(l, b, x)

@@ -268,3 +268,71 @@ def test_full_and_economic_vanka_iterations_close():
         assert info["converged"]
         its[econ] = info["iters"]
     assert abs(its[False] - its[True]) <= 2, its
+
+
+# ---------------------------------------------------------------- MG-DD
+def test_box_dofs_counts_and_cover():
+    """Unknowns of a cell box: its cells' pressures plus, per direction k, the
+    faces with both cells inside; boxes grown by one cell cover every unknown."""
+    shape = (12, 10)
+    n = sum(op.dof_sizes(shape))
+    idx = mg.box_dofs(shape, (2, 3), (7, 9))
+    ny, nx = 5, 6
+    assert idx.size == ny * nx + (nx - 1) * ny + (ny - 1) * nx
+    assert np.unique(idx).size == idx.size
+    # the full box is every unknown
+    assert np.array_equal(mg.box_dofs(shape, (0, 0), shape), np.arange(n))
+    # four overlapping boxes cover all unknowns
+    seen = np.zeros(n, bool)
+    for lo, hi in [((0, 0), (7, 6)), ((0, 4), (7, 10)), ((5, 0), (12, 6)), ((5, 4), (12, 10))]:
+        seen[mg.box_dofs(shape, lo, hi)] = True
+    assert seen.all()
+
+
+def _coarse_problem():
+    med = synth.random_2d(n=32, sigma=0.4, seed=5, corr=4.0, abl=4)
+    H = mg.Hierarchy(op.assemble_mixed(op.parts_for(med), 0.4), med.shape, 2)
+    return H.K[-1], H.shapes[-1]
+
+
+def test_coarse_dd_one_subdomain_is_exact():
+    K, shape = _coarse_problem()
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(K.shape[0]) + 1j * rng.standard_normal(K.shape[0])
+    x = mg.CoarseDD(K, shape, (1, 1), 2).solve(b)
+    xe = spla.spsolve(K.tocsc(), b)
+    assert np.linalg.norm(x - xe) <= 1e-12 * np.linalg.norm(xe)
+
+
+def test_coarse_dd_last_colour_residual_vanishes():
+    """After the sweep, the residual on the unknowns of the last colour's
+    subdomains is zero: they were just solved exactly and same-colour
+    subdomains lie farther apart than the Galerkin stencil reaches."""
+    K, shape = _coarse_problem()
+    cdd = mg.CoarseDD(K, shape, (2, 2), 2)
+    assert cdd.colours == [0, 1, 2, 3]
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal(K.shape[0]) + 1j * rng.standard_normal(K.shape[0])
+    x = cdd.solve(b)
+    r = b - K @ x
+    last = [idx for c, idx, _ in cdd.subs if c == 3]
+    assert len(last) == 1
+    assert np.abs(r[last[0]]).max() <= 1e-10 * np.abs(b).max()
+    # and the sweep is a contraction on the coarse problem
+    assert np.linalg.norm(r) < 0.75 * np.linalg.norm(b)
+
+
+def test_mg_dd_iterations_close_to_mg_exact():
+    """Sec. 6.2 (Table MG): with 3 levels a DD coarsest solve hardly changes the
+    iteration counts."""
+    med = synth.random_2d(n=64, sigma=0.45, seed=0, corr=8.0, abl=10)
+    parts = op.parts_for(med)
+    K = op.assemble_mixed(parts)
+    q = op.slots_to_dofs(synth.point_rhs(med.shape, med.sources)[0], med.shape)
+    its = []
+    for cdd in (None, ((2, 2), 2)):
+        H = mg.Hierarchy(op.assemble_mixed(parts, 0.2), med.shape, 3, coarse_dd=cdd)
+        _, info = krylov.fgmres(lambda v: K @ v, H.cycle, q)
+        assert info["converged"]
+        its.append(info["iters"])
+    assert its[1] <= its[0] + 3, its
