@@ -103,6 +103,18 @@ OTHER = {
     "c2v": dict(workload=WORKLOAD + "; full (2d+1)^2 cell-block Vanka instead of the economic block",
                 media=lambda: media(), kw=dict(vanka_full=1), rows_l1_bytes=87 * 8 + 24 + 24,
                 kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
+    # the c2 workload with the exact coarsest inverse stored in complex64
+    "c2c": dict(workload=WORKLOAD + "; coarsest inverse stored in complex64 (FP32 accumulation)",
+                media=lambda: media(), kw=dict(coarse_c64=1), rows_l1_bytes=87 * 8 + 24 + 24,
+                kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
+    # MG-DD (Sec. 4): the coarsest grid solved by one multicolour DD sweep
+    "c2dd5": dict(workload=WORKLOAD + "; MG-DD: coarsest 32x32 grid split 2x2 (overlap 2), dense local solves",
+                  media=lambda: media(), kw=dict(coarse_dd=(2, 2, 1), coarse_dd_overlap=2, coarse_c64=1),
+                  rows_l1_bytes=87 * 8 + 24 + 24, kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
+    "c2dd4": dict(workload=WORKLOAD.replace(f"({LEVELS} levels", "(4 levels") +
+                  "; MG-DD: coarsest 64x64 grid split 4x4 (overlap 2), dense local solves",
+                  media=lambda: media(), kw=dict(levels=4, coarse_dd=(4, 4, 1), coarse_dd_overlap=2, coarse_c64=1),
+                  rows_l1_bytes=87 * 8 + 24 + 24, kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
     # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
     "c1": dict(
         workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "

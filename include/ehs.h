@@ -105,6 +105,17 @@ typedef struct {
                             FP64 and stored per colour in the cycle's precision (FP16 /
                             BF16 pairs with coef_half, as the implementation remark of
                             Sec. 4 stores them in half precision) */
+  int coarse_dd[3];      /* MG-DD (Sec. 4): subdomains per axis of the coarsest grid, which is
+                            then solved by one multiplicative sweep of Algorithm DD (colours by
+                            index parity, exact dense local solves on the unknowns inside each
+                            overlapping box; faces on a box surface are Dirichlet) instead of
+                            the exact dense solve; all <= 1: exact.  With precond = DD this
+                            gives DD-MG-DD: every subdomain hierarchy's coarsest grid is split
+                            the same way */
+  int coarse_dd_overlap; /* overlap of the coarsest-grid subdomains in cells (>= 1, at most half
+                            the smallest core) */
+  int coarse_c64;        /* storage of the coarsest inverses for the complex64 cycle: 0 complex
+                            double-float (FP64-class), 1 complex64 (FP32 accumulation) */
 } ehs_opts;
 
 typedef struct {

@@ -53,10 +53,23 @@ struct Level {
   void* tabh = nullptr;       // half-precision copy (FP16 or BF16 pairs) for the complex64 cycle
   double2* inv = nullptr;     // coarsest: [nsets][N][N]
   float4* invdf = nullptr;    // coarsest inverse in complex df64 (used by the complex64 cycle)
+  float2* inv32 = nullptr;    // coarsest inverse in complex64 (complex64 cycle with coarse_c64)
   void* binv[2] = {nullptr, nullptr};  // full Vanka block inverses [prec: 0 double2, 1 float2 or half pairs]
   void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
   int rows_var[2] = {0, 0};      // residual-pass launch shape per precision (setup autotuner)
   double w = 0.5;
+};
+
+// MG-DD coarsest solver (Sec. 4): subdomains of the coarsest grid, their
+// dense local inverses and the per-colour sub-item lists
+struct CoarseDD {
+  int nsub = 0;                 // 0: exact dense coarsest solve
+  int nloc = 0;                 // local dense size (largest subdomain; smaller ones padded)
+  int* d_map = nullptr;         // [nsub][nloc] coarsest slot (comp * ncell + cell) or -1
+  std::vector<std::vector<int>> col_subs;  // subdomains of each colour (2^d colours)
+  std::vector<int*> d_col_subs;
+  std::vector<int*> d_list;     // per colour: expanded sub-item list [items * ncs]
+  void* loc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [prec][r, z] [items * nsub][nloc]
 };
 
 struct Hier {
@@ -67,6 +80,10 @@ struct Hier {
   int nu1 = 1, nu2 = 1, cyc = 1;
   int half = 0;                // Galerkin tables of the complex64 cycle: 0 complex64, 1 FP16, 2 BF16
   int full = 0;                // 1: full cell-block Vanka instead of the economic block
+  int cdd_split[3] = {1, 1, 1};  // MG-DD subdomains per axis of the coarsest grid
+  int cdd_overlap = 2;
+  int coarse_c64 = 0;          // complex64 (1) or double-float (0) coarsest inverses, complex64 cycle
+  CoarseDD cdd;
   bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
@@ -155,6 +172,16 @@ Grid mkgrid(int d, int nx, int ny, int nz) {
   return g;
 }
 
+// Installs the active item list (or none) for the launches in its scope.
+struct SelScope {
+  ItemSel old;
+  SelScope(const int* list, int n) : old(g_sel) { g_sel.list = list; g_sel.n = n; }
+  ~SelScope() { g_sel = old; }
+};
+inline SelScope global_sel(ehs_ctx* c) {
+  return c->act.empty() ? SelScope(nullptr, 0) : SelScope(c->d_act, (int)c->act.size());
+}
+
 // ------------------------------------------------------------ hierarchy
 template <typename T> void autotune_rows(ehs_ctx* c, Hier& H);
 
@@ -225,22 +252,113 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
     if (precs & 1) L.binv[0] = b64;
     else dfree(c, b64);
   }
-  // coarsest: dense FP64 inverse
+  // coarsest: dense FP64 inverse of the whole level, or of every MG-DD subdomain
   Level& C = H.lv[H.nlev - 1];
-  const long long N = (long long)(d + 1) * C.g.ncell;
-  if (N > 16384) throw ArgError("coarsest grid too large for the dense FP64 inverse (use more levels)");
-  double2* M = dalloc<double2>(c, (size_t)H.nsets * N * 2 * N);
-  double2* fb = dalloc<double2>(c, (size_t)H.nsets * (N + 1));
-  int* pv = dalloc<int>(c, H.nsets);
-  launch_dense_assemble(C.g, H.nsets, C.L, C.tab64, M, c->s); cnt(); post();
-  C.inv = dalloc<double2>(c, (size_t)H.nsets * N * N);
-  dense_invert((int)N, H.nsets, M, C.inv, fb, pv, derr, c->s); cnt(4 * N + 1); post();
-  C.invdf = dalloc<float4>(c, (size_t)H.nsets * N * N);
-  launch_d2_to_df((long long)H.nsets * N * N, C.inv, C.invdf, c->s); cnt(); post();
+  const long long NG = (long long)(d + 1) * C.g.ncell;
+  int nloc = (int)NG, nmat = H.nsets;
+  int *d_g2l = nullptr;
+  const bool mgdd = H.cdd_split[0] * H.cdd_split[1] * H.cdd_split[2] > 1;
+  if (mgdd) {
+    CoarseDD& D = H.cdd;
+    std::vector<std::vector<int>> sp(3);
+    for (int k = 0; k < 3; ++k) {
+      const int n = k < d ? C.g.n[k] : 1, ns = k < d ? H.cdd_split[k] : 1;
+      if (ns < 1 || ns > n) throw ArgError("coarse_dd split larger than the coarsest grid");
+      sp[k].push_back(0);
+      for (int q = 0; q < ns; ++q) sp[k].push_back(sp[k].back() + n / ns + (q < n % ns ? 1 : 0));
+      for (int q = 0; q < ns && ns > 1; ++q)
+        if (2 * H.cdd_overlap > sp[k][q + 1] - sp[k][q])
+          throw ArgError("coarse_dd_overlap larger than half a coarsest-grid core");
+    }
+    if (H.cdd_overlap < 1) throw ArgError("coarse_dd_overlap must be >= 1");
+    D.nsub = (d == 3 ? H.cdd_split[2] : 1) * H.cdd_split[1] * H.cdd_split[0];
+    D.col_subs.assign(1 << d, {});
+    std::vector<std::vector<int>> dofs(D.nsub);
+    int sidx = 0;
+    for (int iz = 0; iz < (d == 3 ? H.cdd_split[2] : 1); ++iz)
+      for (int iy = 0; iy < H.cdd_split[1]; ++iy)
+        for (int ix = 0; ix < H.cdd_split[0]; ++ix, ++sidx) {
+          const int id[3] = {ix, iy, iz};
+          int lo[3], hi[3], col = 0;
+          for (int k = 0; k < 3; ++k) {
+            if (k >= d) { lo[k] = 0; hi[k] = 1; continue; }
+            lo[k] = std::max(sp[k][id[k]] - H.cdd_overlap, 0);
+            hi[k] = std::min(sp[k][id[k] + 1] + H.cdd_overlap, C.g.n[k]);
+            col |= (id[k] & 1) << k;
+          }
+          D.col_subs[col].push_back(sidx);
+          // unknowns of the box: pressures of its cells, faces with both cells inside
+          for (int a = 0; a <= d; ++a)
+            for (int z = lo[2]; z < hi[2]; ++z)
+              for (int y = lo[1]; y < hi[1]; ++y)
+                for (int x = lo[0]; x < hi[0]; ++x) {
+                  const int j3[3] = {x, y, z};
+                  if (a < d && j3[a] - 1 < lo[a]) continue;
+                  dofs[sidx].push_back((int)((long long)a * C.g.ncell + cell_index(C.g, j3)));
+                }
+        }
+    nloc = 0;
+    for (auto& v : dofs) nloc = std::max(nloc, (int)v.size());
+    D.nloc = nloc;
+    std::vector<int> map((size_t)D.nsub * nloc, -1), g2l((size_t)D.nsub * NG, -1);
+    for (int q = 0; q < D.nsub; ++q)
+      for (int e = 0; e < (int)dofs[q].size(); ++e) {
+        map[(size_t)q * nloc + e] = dofs[q][e];
+        g2l[(size_t)q * NG + dofs[q][e]] = e;
+      }
+    D.d_map = dalloc<int>(c, map.size());
+    d_g2l = dalloc<int>(c, g2l.size());
+    CK(cudaMemcpyAsync(D.d_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(d_g2l, g2l.data(), g2l.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+    for (int col = 0; col < (1 << d); ++col) {
+      const auto& cs = D.col_subs[col];
+      int* ds = nullptr;
+      int* dl = nullptr;
+      if (!cs.empty()) {
+        ds = dalloc<int>(c, cs.size());
+        CK(cudaMemcpyAsync(ds, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+        dl = dalloc<int>(c, (size_t)H.items * cs.size());
+      }
+      D.d_col_subs.push_back(ds);
+      D.d_list.push_back(dl);
+    }
+    for (int p = 0; p < 2; ++p)
+      if (precs & (1 << p))
+        for (int k = 0; k < 2; ++k)
+          D.loc[p][k] = p == 0 ? (void*)dalloc<double2>(c, (size_t)H.items * D.nsub * nloc)
+                               : (void*)dalloc<float2>(c, (size_t)H.items * D.nsub * nloc);
+    CK(cudaStreamSynchronize(c->s));   // the host arrays above are temporaries
+    nmat = H.nsets * D.nsub;
+  } else if (NG > 16384) {
+    throw ArgError("coarsest grid too large for the dense FP64 inverse (use more levels or coarse_dd)");
+  }
+  if (nloc > 16384) throw ArgError("coarse_dd subdomains too large for dense local inverses");
+  const long long N = nloc;
+  double2* M = dalloc<double2>(c, (size_t)nmat * N * 2 * N);
+  double2* fb = dalloc<double2>(c, (size_t)nmat * (N + 1));
+  int* pv = dalloc<int>(c, nmat);
+  if (mgdd)
+    launch_dense_assemble_sub(C.g, H.nsets, H.cdd.nsub, nloc, C.L, C.tab64, H.cdd.d_map, d_g2l, M, c->s);
+  else
+    launch_dense_assemble(C.g, H.nsets, C.L, C.tab64, M, c->s);
+  cnt(); post();
+  C.inv = dalloc<double2>(c, (size_t)nmat * N * N);
+  dense_invert((int)N, nmat, M, C.inv, fb, pv, derr, c->s); cnt(4 * N + 1); post();
+  if (precs & 2) {
+    if (H.coarse_c64) {
+      C.inv32 = dalloc<float2>(c, (size_t)nmat * N * N);
+      launch_table_cast<float>((long long)nmat * N * N, C.inv, C.inv32, c->s); cnt(); post();
+    } else {
+      C.invdf = dalloc<float4>(c, (size_t)nmat * N * N);
+      launch_d2_to_df((long long)nmat * N * N, C.inv, C.invdf, c->s); cnt(); post();
+    }
+  }
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
   dfree(c, M); dfree(c, fb); dfree(c, pv); dfree(c, derr);
+  if (d_g2l) dfree(c, d_g2l);
+  if (!(precs & 1)) { dfree(c, C.inv); C.inv = nullptr; }
   if (herr & EHS_DEVERR_BOX) throw CudaError("Galerkin stencil fell outside its box");
   if (herr & EHS_DEVERR_SINGULAR) throw ArgError("coarsest Galerkin operator is singular");
   if (precs & 2) autotune_rows<float>(c, H);
@@ -348,6 +466,59 @@ void autotune_rows(ehs_ctx* c, Hier& H) {
   cudaEventDestroy(e1);
 }
 
+// x = K_c^{-1} b through the stored dense inverses of the coarsest level (the
+// whole level, or the MG-DD subdomains: items are then sub-items)
+template <typename T>
+void coarse_gemv(ehs_ctx* c, const Hier& H, const Level& L, int N, int items, const typename CT<T>::type* b,
+                 typename CT<T>::type* x) {
+  if (PT<T>::i == 1) {
+    if (L.inv32)   // complex64 inverse, FP32 accumulation
+      launch_dense_apply_c64(N, items, H.nrhs, L.inv32, (const float2*)b, (float2*)x, c->s);
+    else           // FP64-class (df64) inverse on the FP32 pipe
+      launch_dense_apply_df(N, items, H.nrhs, L.invdf, (const float2*)b, (float2*)x, c->s);
+  } else {
+    launch_dense_apply<T>(N, items, H.nrhs, L.inv, b, x, c->s);
+  }
+  cnt(); post();
+}
+
+// MG-DD coarsest solve (Sec. 4 with Algorithm DD): one multiplicative sweep
+// over the colours from x = 0; before every colour but the first the residual
+// b - K_c x is recomputed, gathered into the colour's subdomains, solved with
+// their dense inverses and scatter-added on the subdomain unknowns.
+template <typename T>
+void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typename CT<T>::type* x) {
+  typedef typename CT<T>::type C;
+  const int l = H.nlev - 1;
+  const Level& L = H.lv[l];
+  CoarseDD& D = H.cdd;
+  const int p = PT<T>::i;
+  const long long NG = (long long)(L.g.d + 1) * L.g.ncell;
+  C* r = (C*)L.ws[p][3];
+  C* rs = (C*)D.loc[p][0];
+  C* zs = (C*)D.loc[p][1];
+  CK(cudaMemsetAsync(x, 0, (size_t)H.items * NG * sizeof(C), c->s));
+  const int nact = (int)sel_items(H.items);
+  const int* act = g_sel.list;
+  bool first = true;
+  for (int col = 0; col < (int)D.col_subs.size(); ++col) {
+    const int ncs = (int)D.col_subs[col].size();
+    if (!ncs) continue;
+    const C* cur = b;
+    if (!first) {
+      level_apply<T>(c, H, l, H.alpha, x, b, r, 1);
+      cur = r;
+    }
+    first = false;
+    launch_expand_items(act, nact, H.nrhs, D.nsub, D.d_col_subs[col], ncs, D.d_list[col], c->s); cnt(); post();
+    SelScope sel(D.d_list[col], nact * ncs);
+    const int items_l = H.items * D.nsub;
+    launch_dd_gather<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, cur, rs, c->s); cnt(); post();
+    coarse_gemv<T>(c, H, L, D.nloc, items_l, rs, zs);
+    launch_dd_scatter<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, zs, x, c->s); cnt(); post();
+  }
+}
+
 template <typename T>
 void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typename CT<T>::type* x,
                bool guess) {
@@ -356,12 +527,8 @@ void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typena
   const int p = PT<T>::i;
   const long long nv = (long long)H.items * (L.g.d + 1) * L.g.ncell;
   if (l == H.nlev - 1) {
-    const int N = (int)((L.g.d + 1) * L.g.ncell);
-    if (p == 1)   // complex64 cycle: FP64-class (df64) inverse on the FP32 pipe
-      launch_dense_apply_df(N, H.items, H.nrhs, L.invdf, (const float2*)b, (float2*)x, c->s);
-    else
-      launch_dense_apply<T>(N, H.items, H.nrhs, L.inv, b, x, c->s);
-    cnt(); post();
+    if (H.cdd.nsub) coarse_dd_solve<T>(c, H, b, x);
+    else coarse_gemv<T>(c, H, L, (int)((L.g.d + 1) * L.g.ncell), H.items, b, x);
     return;
   }
   C* t = (C*)L.ws[p][2];
@@ -409,6 +576,9 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (O->precond != EHS_PRECOND_MG && O->precond != EHS_PRECOND_DD) throw ArgError("bad precond");
   if (O->coef_half < 0 || O->coef_half > 2) throw ArgError("coef_half must be 0, 1 (FP16) or 2 (BF16)");
   if (O->vanka_full != 0 && O->vanka_full != 1) throw ArgError("vanka_full must be 0 or 1");
+  if (O->coarse_c64 != 0 && O->coarse_c64 != 1) throw ArgError("coarse_c64 must be 0 or 1");
+  for (int k = 0; k < 3; ++k)
+    if (O->coarse_dd[k] < 0) throw ArgError("coarse_dd must be >= 0");
 }
 
 void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* rho, long long n) {
@@ -455,15 +625,6 @@ void set_active(ehs_ctx* c, const std::vector<int>& active) {
   CK(cudaStreamSynchronize(c->s));   // the host lists above are temporaries
 }
 
-// Installs the active item list (or none) for the launches in its scope.
-struct SelScope {
-  ItemSel old;
-  SelScope(const int* list, int n) : old(g_sel) { g_sel.list = list; g_sel.n = n; }
-  ~SelScope() { g_sel = old; }
-};
-inline SelScope global_sel(ehs_ctx* c) {
-  return c->act.empty() ? SelScope(nullptr, 0) : SelScope(c->d_act, (int)c->act.size());
-}
 
 }  // namespace
 
@@ -828,6 +989,8 @@ void ehs_default_opts(ehs_opts* o) {
   o->dd_overlap = 4;
   o->dd_pad = 8;
   o->dd_abl_max = 1.0;
+  o->coarse_dd[0] = o->coarse_dd[1] = o->coarse_dd[2] = 1;
+  o->coarse_dd_overlap = 2;
 }
 
 ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* stream, ehs_ctx** out) {
@@ -851,6 +1014,9 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     H.nu1 = opts->nu_pre; H.nu2 = opts->nu_post; H.cyc = opts->cycle;
     H.half = opts->coef_half;
     H.full = opts->vanka_full;
+    for (int k = 0; k < 3; ++k) H.cdd_split[k] = k < prob->dim ? std::max(opts->coarse_dd[k], 1) : 1;
+    H.cdd_overlap = opts->coarse_dd_overlap;
+    H.coarse_c64 = opts->coarse_c64;
     c->n0 = (long long)(c->d + 1) * H.g0.ncell;
     const long long nc = (long long)H.nsets * H.g0.ncell;
     check_media(c, prob->lambda, prob->mu, prob->rho, nc);

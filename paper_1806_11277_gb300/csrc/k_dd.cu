@@ -36,6 +36,16 @@ __global__ void k_dd_scatter(long long nl, int nsub, int nrhs, long long ng, con
   t.y += v.y;
 }
 
+__global__ void k_expand_items(const int* __restrict__ list, int nact, int nrhs, int nsub,
+                               const int* __restrict__ subs, int ncs, int* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nact * ncs) return;
+  const int j = t / ncs, q = t % ncs;
+  const int b = list ? list[j] : j;
+  const int m = b / nrhs, r = b % nrhs;
+  out[t] = (m * nsub + subs[q]) * nrhs + r;
+}
+
 }  // namespace
 
 template <typename T>
@@ -50,6 +60,12 @@ void launch_dd_scatter(long long nl, int items_l, int nsub, int nrhs, long long 
   k_dd_scatter<<<dim3((unsigned)((nl + 255) / 256), sel_items(items_l)), 256, 0, s>>>(nl, nsub, nrhs, ng, map, xs, x,
                                                                                     g_sel.list);
 }
+void launch_expand_items(const int* list, int nact, int nrhs, int nsub, const int* subs, int ncs, int* out,
+                         cudaStream_t s) {
+  const int n = nact * ncs;
+  k_expand_items<<<(n + 127) / 128, 128, 0, s>>>(list, nact, nrhs, nsub, subs, ncs, out);
+}
+
 template void launch_dd_gather<float>(long long, int, int, int, long long, const int*, const float2*, float2*, cudaStream_t);
 template void launch_dd_gather<double>(long long, int, int, int, long long, const int*, const double2*, double2*, cudaStream_t);
 template void launch_dd_scatter<float>(long long, int, int, int, long long, const int*, const float2*, float2*, cudaStream_t);

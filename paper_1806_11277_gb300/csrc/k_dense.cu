@@ -146,6 +146,81 @@ __global__ void k_dense_apply(int N, int nrhs, const double2* __restrict__ inv,
   }
 }
 
+// MG-DD local problems (Sec. 4): row e of local matrix (set, s) is the
+// coarsest-level row of global slot map[s][e], restricted to the columns that
+// are local unknowns of subdomain s (g2l[s][slot] >= 0); padding rows (map -1)
+// are identity rows.  Augmented with the identity like k_dense_assemble.
+template <int D>
+__global__ void k_dense_assemble_sub(Grid g, StencilLayout L, const double2* __restrict__ tab, int nsub,
+                                     int nloc, const int* __restrict__ map, const int* __restrict__ g2l,
+                                     double2* __restrict__ A) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nloc) return;
+  const int ms = blockIdx.y;                 // set * nsub + s
+  const int set = ms / nsub, sub = ms % nsub;
+  const long long NG = (long long)(D + 1) * g.ncell;
+  const double2* ts = tab + (long long)set * L.nslot * g.ncell;
+  double2* row = A + ((long long)ms * nloc + e) * (2 * nloc);
+  for (int j = 0; j < 2 * nloc; ++j) row[j] = make_double2(0, 0);
+  row[nloc + e] = make_double2(1, 0);
+  const int gs = map[(long long)sub * nloc + e];
+  if (gs < 0) { row[e] = make_double2(1, 0); return; }
+  const int* gl = g2l + (long long)sub * NG;
+  const int a = (int)(gs / g.ncell);
+  const long long c = gs % g.ncell;
+  int i[3];
+  cell_coords(g, c, i);
+  for (int q = L.row_first[a]; q < L.row_first[a + 1]; ++q) {
+    const PairBox& P = L.p[q];
+    int sl = P.base;
+    for (int oz = 0; oz < P.ext[2]; ++oz)
+      for (int oy = 0; oy < P.ext[1]; ++oy)
+        for (int ox = 0; ox < P.ext[0]; ++ox, ++sl) {
+          const int j[3] = {i[0] + P.lo[0] + ox, i[1] + P.lo[1] + oy, i[2] + P.lo[2] + oz};
+          bool in = true;
+          for (int k = 0; k < 3; ++k) in = in && j[k] >= 0 && j[k] < g.n[k];
+          if (!in || !slot_valid(P.b, D, j)) continue;
+          const int lc = gl[(long long)P.b * g.ncell + cell_index(g, j)];
+          if (lc < 0) continue;
+          const double2 v = ts[(long long)sl * g.ncell + c];
+          row[lc].x += v.x;
+          row[lc].y += v.y;
+        }
+  }
+}
+
+// x = Ainv r with Ainv stored in complex64 (FP32 accumulation); one warp per
+// row, four independent loads in flight per lane
+__global__ void k_dense_apply_c64(int N, int nrhs, const float2* __restrict__ inv, const float2* __restrict__ r,
+                                  float2* __restrict__ x, const int* __restrict__ il) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  if (warp >= N) return;
+  const float2* row = inv + ((long long)(item / nrhs) * N + warp) * N;
+  const float2* rv = r + (long long)item * N;
+  float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
+  int j = lane;
+  for (; j + 96 < N; j += 128) {
+    const float2 a0 = __ldg(row + j), a1 = __ldg(row + j + 32), a2 = __ldg(row + j + 64), a3 = __ldg(row + j + 96);
+    const float2 b0 = __ldg(rv + j), b1 = __ldg(rv + j + 32), b2 = __ldg(rv + j + 64), b3 = __ldg(rv + j + 96);
+    sx0 = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, sx0)); sy0 = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, sy0));
+    sx1 = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, sx1)); sy1 = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, sy1));
+    sx0 = fmaf(a2.x, b2.x, fmaf(-a2.y, b2.y, sx0)); sy0 = fmaf(a2.x, b2.y, fmaf(a2.y, b2.x, sy0));
+    sx1 = fmaf(a3.x, b3.x, fmaf(-a3.y, b3.y, sx1)); sy1 = fmaf(a3.x, b3.y, fmaf(a3.y, b3.x, sy1));
+  }
+  for (; j < N; j += 32) {
+    const float2 a = __ldg(row + j), b = __ldg(rv + j);
+    sx0 = fmaf(a.x, b.x, fmaf(-a.y, b.y, sx0)); sy0 = fmaf(a.x, b.y, fmaf(a.y, b.x, sy0));
+  }
+  float sx = sx0 + sx1, sy = sy0 + sy1;
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if (lane == 0) x[(long long)item * N + warp] = make_float2(sx, sy);
+}
+
 }  // namespace
 
 void launch_dense_assemble(const Grid& g, int nsets, const StencilLayout& L, const double2* tab,
@@ -174,6 +249,20 @@ void launch_dense_apply(int N, int items, int nrhs, const double2* inv, const ty
   const int wpb = 8;
   dim3 grid((N + wpb - 1) / wpb, sel_items(items));
   k_dense_apply<T><<<grid, 32 * wpb, 0, s>>>(N, nrhs, inv, r, x, g_sel.list);
+}
+
+void launch_dense_assemble_sub(const Grid& g, int nsets, int nsub, int nloc, const StencilLayout& L,
+                               const double2* tab, const int* map, const int* g2l, double2* A, cudaStream_t s) {
+  const dim3 grid((unsigned)((nloc + 127) / 128), nsets * nsub);
+  if (g.d == 2) k_dense_assemble_sub<2><<<grid, 128, 0, s>>>(g, L, tab, nsub, nloc, map, g2l, A);
+  else k_dense_assemble_sub<3><<<grid, 128, 0, s>>>(g, L, tab, nsub, nloc, map, g2l, A);
+}
+
+void launch_dense_apply_c64(int N, int items, int nrhs, const float2* inv, const float2* r, float2* x,
+                            cudaStream_t s) {
+  const int wpb = 8;
+  const dim3 grid((N + wpb - 1) / wpb, sel_items(items));
+  k_dense_apply_c64<<<grid, 32 * wpb, 0, s>>>(N, nrhs, inv, r, x, g_sel.list);
 }
 
 template void launch_dense_apply<float>(int, int, int, const double2*, const float2*, float2*, cudaStream_t);

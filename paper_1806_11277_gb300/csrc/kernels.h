@@ -103,6 +103,26 @@ void dense_invert(int N, int nsets, double2* M /*[nsets][N][2N] augmented*/, dou
 template <typename T>
 void launch_dense_apply(int N, int items, int nrhs, const double2* inv, const typename CT<T>::type* r,
                         typename CT<T>::type* x, cudaStream_t s);
+// MG-DD: local dense matrices of the coarsest-grid subdomains ([nsets*nsub][nloc][2 nloc], augmented)
+void launch_dense_assemble_sub(const Grid& g, int nsets, int nsub, int nloc, const StencilLayout& L,
+                               const double2* tab, const int* map, const int* g2l, double2* A, cudaStream_t s);
+// x = inv r with a complex64 inverse (FP32 accumulation); matrix of item b: inv + (b / nrhs) N^2
+void launch_dense_apply_c64(int N, int items, int nrhs, const float2* inv, const float2* r, float2* x,
+                            cudaStream_t s);
+// sub-item list of MG-DD / DD: out[j * ncs + q] = ((m * nsub) + subs[q]) * nrhs + r for the
+// j-th active item b = m * nrhs + r (all items when list is null)
+void launch_expand_items(const int* list, int nact, int nrhs, int nsub, const int* subs, int ncs, int* out,
+                         cudaStream_t s);
+// gather of global slots into local vectors (map[s][e] = global slot or -1) and
+// scatter-add back; sub-item bl = ((m * nsub) + s) * nrhs + r reads/writes item m * nrhs + r
+template <typename T>
+void launch_dd_gather(long long nl, int items_l, int nsub, int nrhs, long long nglob_item,
+                      const int* map, const typename CT<T>::type* res, typename CT<T>::type* out,
+                      cudaStream_t s);
+template <typename T>
+void launch_dd_scatter(long long nl, int items_l, int nsub, int nrhs, long long nglob_item,
+                       const int* map, const typename CT<T>::type* xs, typename CT<T>::type* x,
+                       cudaStream_t s);
 
 // ---- Krylov (FP64) --------------------------------------------------------
 void launch_cast_c128_c64(long long n, const double2* in, float2* out, cudaStream_t s);

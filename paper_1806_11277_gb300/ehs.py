@@ -36,7 +36,10 @@ class Opts(C.Structure):
                 ("precond", C.c_int), ("prec", C.c_int), ("nrhs", C.c_int), ("dd", C.c_int * 3),
                 ("dd_overlap", C.c_int), ("dd_pad", C.c_int), ("dd_abl_max", C.c_double),
                 ("coef_half", C.c_int),
-                ("vanka_full", C.c_int)]
+                ("vanka_full", C.c_int),
+                ("coarse_dd", C.c_int * 3),
+                ("coarse_dd_overlap", C.c_int),
+                ("coarse_c64", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -101,9 +104,10 @@ def default_opts(**kw):
         if k == "w":
             for j, x in enumerate(v):
                 o.w[j] = x
-        elif k == "dd":
+        elif k in ("dd", "coarse_dd"):
+            arr = getattr(o, k)
             for j, x in enumerate(v):
-                o.dd[j] = x
+                arr[j] = x
         else:
             setattr(o, k, v)
     return o

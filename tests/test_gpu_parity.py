@@ -494,3 +494,88 @@ def test_full_vanka_dd_fgmres():
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
     assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+# ------------------------------------------------------------- MG-DD, DD-MG-DD
+@pytest.mark.parametrize("case,cyc", [("2d", 1), ("2d", 2), ("3d", 1)])
+def test_mgdd_cycle_matches_oracle(case, cyc):
+    """MG-DD (Sec. 4): the coarsest grid solved by one multicolour DD sweep with
+    dense local solves; one cycle against the oracle's CoarseDD."""
+    ehs = _ehs()
+    if case == "2d":
+        meds, levels, split, ov = _media_2d(64, 2), 3, (2, 2, 1), 2
+    else:
+        meds, levels, split, ov = _media_3d(16, 1), 3, (2, 2, 2), 1
+    S = ehs.solver_for(meds, levels=levels, alpha=0.4, cycle=cyc, coarse_dd=split, coarse_dd_overlap=ov)
+    shape = meds[0].shape
+    d = len(shape)
+    b_ = _rand_slots(shape, S.items, 71)
+    for dt, tol in ((torch.complex128, 1e-10), (torch.complex64, 5e-5)):
+        bd = torch.from_numpy(b_).to("cuda", dt)
+        xd = torch.zeros_like(bd)
+        S.vcycle(bd, xd)
+        for it, med in enumerate(meds):
+            H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, levels,
+                             w=[0.75, 0.5, 0.25][:levels - 1], coarse_dd=(split[:d], ov))
+            xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape), gamma=cyc), shape)
+            assert _rel(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _rel(xd[it].cpu().numpy(), xr))
+    S.close()
+
+
+@pytest.mark.parametrize("prec_name,c64inv", [("c128", 0), ("c64", 0), ("c64", 1)])
+def test_mgdd_fgmres_matches_oracle(prec_name, c64inv):
+    ehs = _ehs()
+    prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
+    meds = _media_2d(64, 2)
+    q, u, info = _solve_both(meds, 3, prec, alpha=0.4, cycle=2, coarse_dd=(2, 2, 1), coarse_dd_overlap=2,
+                             coarse_c64=c64inv)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 3, w=[0.75, 0.5], coarse_dd=((2, 2), 2))
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        assert info[it]["converged"]
+        if prec == ehs.EHS_C128:
+            assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
+        else:
+            assert abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_coarse_c64_inverse_fgmres():
+    """Exact coarsest solve with the inverse stored in complex64: same counts as
+    the oracle (+-1) and the same solution."""
+    ehs = _ehs()
+    meds = _media_2d(64, 2)
+    q, u, info = _solve_both(meds, 3, ehs.EHS_C64, coarse_c64=1)
+    for it, med in enumerate(meds):
+        K = _oracle_parts(med)
+        H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, 3)
+        qo = op.slots_to_dofs(q[it], med.shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+        ug = op.slots_to_dofs(u[it], med.shape)
+        assert info[it]["converged"] and abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_dd_mg_dd_fgmres_matches_oracle():
+    """DD-MG-DD (Sec. 4): top-level DD whose subdomain cycles solve their
+    coarsest grids by DD; iteration count and solution as the oracle's."""
+    ehs = _ehs()
+    med = synth.homogeneous_2d()
+    q, u, info = _solve_both([med], 3, ehs.EHS_C128, precond=ehs.EHS_PRECOND_DD, dd=(2, 2, 1),
+                             dd_overlap=4, dd_pad=8, coarse_dd=(2, 2, 1), coarse_dd_overlap=2)
+    D = odd.DD(med, (2, 2), 4, 8, 3, 0.2, coarse_dd=((2, 2), 2))
+    qo = op.slots_to_dofs(q[0], med.shape)
+    xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
+    ug = op.slots_to_dofs(u[0], med.shape)
+    assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
+    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+def test_mgdd_rejects_bad_split():
+    ehs = _ehs()
+    meds = _media_2d(32, 1)
+    with pytest.raises(ehs.EhsError, match="ERR_ARG"):
+        ehs.solver_for(meds, levels=3, coarse_dd=(3, 3, 1), coarse_dd_overlap=2)   # cores of 2-3 cells
