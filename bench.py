@@ -38,24 +38,57 @@ sys.path.insert(0, ROOT)
 METRIC = "elastic Helmholtz solves/s to 1e-6 residual; stencil HBM GB/s vs peak"
 SIGMAS = (0.25, 0.4, 0.45, 0.49)
 N_GRID = 512
-LEVELS = 5
-ALPHA = 0.4
-W_LEVELS = (0.75, 0.5, 0.25, 0.25)
-CYCLE = 2                          # W(1,1), the paper's cycle (Sec. 6)
+# The solver of the 512x512 line: MG-DD (Sec. 4), a 3-level V(1,1) cycle whose
+# 128x128 coarsest grid is solved by one multicolour DD sweep over 8x8
+# overlapping subdomains; 16-bit storage of the Galerkin stencils and of the
+# coarse local inverses (the paper's half-precision inverses, Sec. 4), FP32
+# arithmetic in the cycle, double-float FGMRES.
+LEVELS = 3
+ALPHA = 0.25
+W_LEVELS = (0.75, 0.5)
+CYCLE = 1                          # V(1,1)
+COARSE_DD = (8, 8, 1)
+COARSE_OVERLAP = 3
+COARSE_FMT = 2                     # FP16 pairs
+COEF_HALF = 1                      # FP16 pairs
 WORKLOAD = ("2D heterogeneous media 512x512 (GRF corr 20, Vp 1.5-4.5, rho 1-2.5), Poisson "
-            "0.25/0.4/0.45/0.49, 8 points per S-wavelength, 20-cell ABL; complex64 W(1,1) cycle "
-            f"({LEVELS} levels, alpha {ALPHA}) inside FP64-class (double-float) FGMRES(10) to 1e-6")
-# Galerkin level-1 apply (k_st_rows): 87 complex64 stencil coefficients 696 + x 24 + y 24
-ST_ROWS_L1_BYTES_PER_CELL_C64 = 87 * 8 + 24 + 24
-# DRAM read + write bytes of one k_st_rows<float,2,1> launch of the c2 line, from an
-# ncu capture of this kernel as it stands (set to None whenever the kernel changes)
-ROWS_L1_TRAFFIC_C2 = 190.79e6 + 7.07e6
+            "0.25/0.4/0.45/0.49, 8 points per S-wavelength, 20-cell ABL; MG-DD preconditioner: complex64 "
+            f"V(1,1) cycle ({LEVELS} levels, alpha {ALPHA}), coarsest 128x128 grid solved by one DD sweep over "
+            f"8x8 subdomains (overlap {COARSE_OVERLAP}, dense local inverses), FP16 Galerkin tables and local "
+            "inverses; FP64-class (double-float) FGMRES(10) to 1e-6")
+
+
+def default_kw():
+    """Solver options of the default 512x512 line (the C ABI's ehs_opts fields)."""
+    return dict(levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=1, cycle=CYCLE, coarse_dd=COARSE_DD,
+                coarse_dd_overlap=COARSE_OVERLAP, coarse_fmt=COARSE_FMT, coef_half=COEF_HALF)
+
+
+# Roofline kernel of the default line: the MG-DD coarsest local products (k_dense_apply_v,
+# 35% of the solve in the ncu launch list); per launch (one colour) the live n_s x n_s
+# entries of every subdomain inverse of the colour (4 B each, FP16 pairs) + r and z
+ROOF = "coarse"
+ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 16 subdomain inverses "
+               "x 4 media)")
+# Galerkin level-1 apply (k_st_rows): 87 stencil coefficients (FP16 pairs, 4 B) + x 24 + y 24
+ST_ROWS_L1_BYTES_PER_CELL = 87 * 4 + 24 + 24
+# DRAM read + write bytes of one roofline-kernel launch (one colour) of the default line, from an
+# ncu capture of the kernel as it stands (None whenever the kernel changes)
+ROOF_TRAFFIC_C2 = None
 
 
 def media(seed=0):
     from paper_1806_11277_gb300 import synth
     return [synth.random_2d(n=N_GRID, sigma=s, seed=seed) for s in SIGMAS]
 
+
+_EXACT5W = dict(levels=5, alpha=0.4, w=[0.75, 0.5, 0.25, 0.25], cycle=2, coarse_dd=(1, 1, 1), coarse_fmt=0,
+                coef_half=0)
+_W5 = WORKLOAD.split("; MG-DD")[0] + ("; complex64 W(1,1) cycle (5 levels, alpha 0.4, damping 0.75/0.5/0.25/0.25), "
+                                      "exact dense coarsest 32x32 solve (double-float inverse); FP64-class "
+                                      "(double-float) FGMRES(10) to 1e-6")
+_ROWS_C64 = "k_st_rows<float,float2,2,1> (Galerkin level 1, all rows, complex64 table)"
+_ROWS_H = "k_st_rows<float,__half2,2,1> (Galerkin level 1, all rows, FP16 table)"
 
 # Other workloads (bench.py --config NAME); "c2" above is the default line.
 OTHER = {
@@ -69,7 +102,7 @@ OTHER = {
         media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).layered_3d(
             n=128, seed=0, corr=10.0, abl=16)],
         kw=dict(levels=5, alpha=0.4, w=[0.5, 0.5, 0.2, 0.2], cycle=1, precond=1, dd=(2, 2, 2),
-                dd_overlap=4, dd_pad=8),
+                dd_overlap=4, dd_pad=8, coarse_dd=(1, 1, 1), coarse_fmt=0, coef_half=0),
         roof_level=0, rows_l1_bytes=32 + 16 + 32,
         kernel="k_fine_apply<float,3> (fine K x: x 32 + coefficients 16 + y 32 B per cell)"),
     # batched multi-source 3D: 192^3, 8 x-forces on a surface line in one batch,
@@ -82,46 +115,40 @@ OTHER = {
             n=192, seed=0, corr=10.0, abl=16, nsrc=8)],
         nrhs=8,
         kw=dict(levels=5, alpha=0.4, w=[0.5, 0.5, 0.2, 0.2], cycle=1, precond=1, dd=(3, 3, 2),
-                dd_overlap=4, dd_pad=8, nrhs=8, maxit=800),
+                dd_overlap=4, dd_pad=8, nrhs=8, maxit=800, coarse_dd=(1, 1, 1), coarse_fmt=0, coef_half=0),
         roof_level=0, rows_l1_bytes=32 + 16 + 32,
         kernel="k_fine_apply<float,3> (fine K x: x 32 + coefficients 16 + y 32 B per cell)"),
-    # the c2 workload with FP16 / BF16 storage of the Galerkin stencil tables
-    "c2h": dict(workload=WORKLOAD + "; Galerkin tables stored as FP16 pairs (FP32 accumulation)",
-                media=lambda: media(), kw=dict(coef_half=1), rows_l1_bytes=87 * 4 + 24 + 24,
-                kernel="k_st_rows<float,__half2,2,1> (Galerkin level 1, all rows)"),
-    "c2b": dict(workload=WORKLOAD + "; Galerkin tables stored as BF16 pairs (FP32 accumulation)",
-                media=lambda: media(), kw=dict(coef_half=2), rows_l1_bytes=87 * 4 + 24 + 24,
-                kernel="k_st_rows<float,__nv_bfloat162,2,1> (Galerkin level 1, all rows)"),
-    # the c2 workload in the plain FP64 GPU form: complex128 W-cycle and FP64 Krylov
     "c4b": None,   # filled below: c4 with BF16 Galerkin tables
-    "c2f64": dict(workload=WORKLOAD.replace("complex64 W(1,1)", "complex128 W(1,1)").replace(
+    # the 512x512 workload with the 5-level W(1,1) cycle and the exact dense coarsest solve
+    "c2w5": dict(workload=_W5, media=lambda: media(), kw=dict(_EXACT5W), rows_l1_bytes=87 * 8 + 24 + 24,
+                 kernel=_ROWS_C64),
+    # the default line with complex64 tables and complex64 local inverses (no 16-bit storage)
+    "c2c64": dict(workload=WORKLOAD.replace("FP16 Galerkin tables and local inverses", "complex64 Galerkin "
+                                            "tables and local inverses"),
+                  media=lambda: media(), kw=dict(coarse_fmt=1, coef_half=0), roof="coarse",
+                  kernel="k_dense_apply_v<float2> (MG-DD coarsest local products, complex64 inverses)"),
+    # the default line in the plain FP64 GPU form: complex128 cycle, FP64 inverses, FP64 Krylov
+    "c2f64": dict(workload=WORKLOAD.replace("complex64 V(1,1)", "complex128 V(1,1)").replace(
+                      "FP16 Galerkin tables and local inverses", "FP64 Galerkin tables and local inverses").replace(
                       "FP64-class (double-float) FGMRES", "FP64 FGMRES") + "; plain FP64 GPU form",
-                  media=lambda: media(), kw=dict(prec=0), rows_l1_bytes=87 * 16 + 48 + 48,
-                  kernel="k_st_rows<double,2,1> (Galerkin level 1, all rows)"),
-    # the c2 workload with full cell-block Vanka (closed form on the fine level,
-    # stored complex64 block inverses on the Galerkin levels)
+                  media=lambda: media(), kw=dict(prec=0, coarse_fmt=0, coef_half=0), rows_l1_bytes=87 * 16 + 48 + 48,
+                  kernel="k_st_rows<double,double2,2,1> (Galerkin level 1, all rows)"),
+    # the default line with full cell-block Vanka
     "c2v": dict(workload=WORKLOAD + "; full (2d+1)^2 cell-block Vanka instead of the economic block",
-                media=lambda: media(), kw=dict(vanka_full=1), rows_l1_bytes=87 * 8 + 24 + 24,
-                kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
-    # the c2 workload with the exact coarsest inverse stored in complex64
-    "c2c": dict(workload=WORKLOAD + "; coarsest inverse stored in complex64 (FP32 accumulation)",
-                media=lambda: media(), kw=dict(coarse_c64=1), rows_l1_bytes=87 * 8 + 24 + 24,
-                kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
-    # MG-DD (Sec. 4): the coarsest grid solved by one multicolour DD sweep
-    "c2dd5": dict(workload=WORKLOAD + "; MG-DD: coarsest 32x32 grid split 2x2 (overlap 2), dense local solves",
-                  media=lambda: media(), kw=dict(coarse_dd=(2, 2, 1), coarse_dd_overlap=2, coarse_c64=1),
-                  rows_l1_bytes=87 * 8 + 24 + 24, kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
-    "c2dd4": dict(workload=WORKLOAD.replace(f"({LEVELS} levels", "(4 levels") +
-                  "; MG-DD: coarsest 64x64 grid split 4x4 (overlap 2), dense local solves",
-                  media=lambda: media(), kw=dict(levels=4, coarse_dd=(4, 4, 1), coarse_dd_overlap=2, coarse_c64=1),
-                  rows_l1_bytes=87 * 8 + 24 + 24, kernel="k_st_rows<float,2,1> (Galerkin level 1, all rows)"),
+                media=lambda: media(), kw=dict(vanka_full=1), roof="coarse", kernel=ROOF_KERNEL),
+    # 4-level MG-DD with the W(1,1) cycle (coarsest 64x64 split 4x4)
+    "c2dd4": dict(workload=WORKLOAD.split("; MG-DD")[0] + "; MG-DD: complex64 W(1,1) cycle (4 levels, alpha 0.4), "
+                  "coarsest 64x64 grid split 4x4 (overlap 2), complex64 local inverses; double-float FGMRES(10)",
+                  media=lambda: media(), kw=dict(levels=4, alpha=0.4, w=[0.75, 0.5, 0.25], cycle=2,
+                                                 coarse_dd=(4, 4, 1), coarse_dd_overlap=2, coarse_fmt=1, coef_half=0),
+                  roof="coarse", kernel="k_dense_apply_v<float2> (MG-DD coarsest local products, complex64 inverses)"),
     # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
     "c1": dict(
         workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "
                   "x-force; 3-level V(1,1), alpha 0.2, complex128 FGMRES(10)"),
         media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).homogeneous_2d()],
-        kw=dict(levels=3, alpha=0.2, w=[0.75, 0.5], cycle=1, prec=0),
-        rows_l1_bytes=87 * 16 + 48 + 48, kernel="k_st_rows<double,2,1> (Galerkin level 1, all rows)"),
+        kw=dict(levels=3, alpha=0.2, w=[0.75, 0.5], cycle=1, prec=0, coarse_dd=(1, 1, 1), coarse_fmt=0, coef_half=0),
+        rows_l1_bytes=87 * 16 + 48 + 48, kernel="k_st_rows<double,double2,2,1> (Galerkin level 1, all rows)"),
 }
 
 
@@ -136,6 +163,7 @@ def rhs(meds, nrhs=1):
 
 OTHER["c4b"] = dict(OTHER["c4"], workload=OTHER["c4"]["workload"] + "; Galerkin tables stored as BF16 pairs",
                     kw=dict(OTHER["c4"]["kw"], coef_half=2))
+OTHER["c4"]["kernel"] = OTHER["c4b"]["kernel"] = OTHER["c3"]["kernel"]
 
 
 def peaks():
@@ -201,7 +229,8 @@ def oracle_sample(meds, iters_per_sample, which=0):
     med = meds[which % len(meds)]
     parts = op.parts_for(med)
     K = op.assemble_mixed(parts)
-    H = mg.Hierarchy(op.assemble_mixed(parts, ALPHA), med.shape, LEVELS, w=list(W_LEVELS))
+    H = mg.Hierarchy(op.assemble_mixed(parts, ALPHA), med.shape, LEVELS, w=list(W_LEVELS),
+                     coarse_dd=(COARSE_DD[:2], COARSE_OVERLAP))
     q = op.slots_to_dofs(rhs([med])[0], med.shape)
     t = time.perf_counter()
     _, info = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=CYCLE), q, m=10,
@@ -289,7 +318,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     cfg = OTHER.get(args.config)
     meds = media() if cfg is None else cfg["media"]()
-    kw = dict(levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=ehs.EHS_C64, cycle=CYCLE)
+    kw = default_kw()
     if cfg is not None:
         kw.update(cfg["kw"])
     nsolve = len(meds) * (1 if cfg is None else cfg.get("nrhs", 1))
@@ -303,7 +332,44 @@ def run_gpu(args):
     qd = torch.from_numpy(q_host).to(dev)
     ud = torch.zeros_like(qd)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    def roofline_coarse():
+        # roofline of the dominant kernel of the MG-DD line, the coarsest local products
+        # (k_dense_apply_v): one launch = ehs_coarse_local_apply of one colour (every
+        # subdomain of that colour, every item); each colour timed in turn, one launch per
+        # sample, L2 flushed before each, events on the solver's stream
+        ns, nloc, sizes = S.coarse_dims()
+        c64 = kw["prec"] == ehs.EHS_C64
+        eb = {0: 16, 1: 8, 2: 4, 3: 4}[kw.get("coarse_fmt", 0)] if c64 else 16
+        vb = 8 if c64 else 16
+        nx = kw["coarse_dd"][0]
+        nsets = len(meds)
+        r = torch.randn((S.items, ns, nloc), dtype=torch.complex64 if c64 else torch.complex128, device=dev)
+        for q, n in enumerate(sizes):
+            r[:, q, n:] = 0
+        z = torch.zeros_like(r)
+        cols = {}
+        for q, n in enumerate(sizes):
+            col = (q % nx) % 2 + 2 * ((q // nx) % 2)
+            cols[col] = cols.get(col, 0) + nsets * n * n * eb + S.items * n * 2 * vb
+        kt = {col: [] for col in cols}
+        for rep in range(args.kernel_reps):
+            for col in cols:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                    e0.record(stream)
+                    S.coarse_local_apply(col, r, z)
+                    e1.record(stream)
+                e1.synchronize()
+                kt[col].append(e0.elapsed_time(e1) / 1e3)
+        tsum = sum(statistics.median(kt[col]) for col in cols)
+        bsum = sum(cols.values())
+        return tsum / len(cols), bsum / len(cols), bsum / tsum / 1e9
+
     def roofline():
+        if (cfg is None and ROOF == "coarse") or (cfg is not None and cfg.get("roof") == "coarse"):
+            return roofline_coarse()
         # roofline of the dominant kernel family, the Galerkin-level stencil rows
         # (k_st_rows): one launch = ehs_op_apply on level 1 (all rows, every cell),
         # one launch per sample, L2 flushed before each, events on the solver's stream
@@ -333,7 +399,7 @@ def run_gpu(args):
             kt.append(e0.elapsed_time(e1) / 1e3)
         t_launch = statistics.median(kt)
         peak, peak_kind = peaks()
-        alg = (ST_ROWS_L1_BYTES_PER_CELL_C64 if cfg is None else cfg["rows_l1_bytes"]) * ncell1
+        alg = (ST_ROWS_L1_BYTES_PER_CELL if cfg is None else cfg["rows_l1_bytes"]) * ncell1
         achieved = alg / t_launch / 1e9
         return t_launch, alg, achieved
 
@@ -405,19 +471,25 @@ def run_gpu(args):
                    "grid": list(meds[0].shape), "media": nsolve,
                    "sigmas": list(SIGMAS) if cfg is None else None, "levels": kw["levels"],
                    "alpha": kw["alpha"], "cycle": "W(1,1)" if kw["cycle"] == 2 else "V(1,1)",
-                   "krylov": "FGMRES(10), double-float (FP64-class) vectors and operator", "precond_dtype": "complex64",
+                   "krylov": "FGMRES(10), " + ("double-float (FP64-class)" if kw["prec"] == 1 else "FP64")
+                   + " vectors and operator", "precond_dtype": "complex64" if kw["prec"] == 1 else "complex128",
+                   "coarsest": ("MG-DD %s subdomains, overlap %d" % ("x".join(map(str, kw["coarse_dd"][:2])),
+                                                                   kw.get("coarse_dd_overlap", 2))
+                                if max(kw.get("coarse_dd", (1,))) > 1 else "exact dense inverse"),
+                   "storage": {"galerkin_tables": ["complex", "FP16", "BF16"][kw.get("coef_half", 0)],
+                               "coarsest_inverses": ["double-float", "complex64", "FP16", "BF16"][kw.get("coarse_fmt", 0)]
+                               if kw["prec"] == 1 else "FP64"},
                    "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
         "iters": its, "relres": relres, "setup_s": setup_s,
         "gridpoints_x_iters_per_s": float(np.prod(meds[0].shape) * sum(its) * args.steps * world / total),
         "e2e": {"value": e2e_val, "unit": "solves/s",
                 "h2d_bytes_per_step": int(q_host.nbytes), "d2h_bytes_per_step": int(q_host.nbytes)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "k_st_rows<float,2,1> (Galerkin level 1, all rows)"
-                     if cfg is None else cfg["kernel"],
+        "roofline": {"bound": "hbm", "kernel": ROOF_KERNEL if cfg is None else cfg["kernel"],
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": args.traffic if args.traffic is not None else
-                     (ROWS_L1_TRAFFIC_C2 if cfg is None else None), "alg_bytes_per_launch": alg,
+                     (ROOF_TRAFFIC_C2 if cfg is None else None), "alg_bytes_per_launch": alg,
                      "launch_us": t_launch * 1e6},
         "clocks": clk,
     }

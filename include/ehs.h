@@ -114,8 +114,10 @@ typedef struct {
                             the same way */
   int coarse_dd_overlap; /* overlap of the coarsest-grid subdomains in cells (>= 1, at most half
                             the smallest core) */
-  int coarse_c64;        /* storage of the coarsest inverses for the complex64 cycle: 0 complex
-                            double-float (FP64-class), 1 complex64 (FP32 accumulation) */
+  int coarse_fmt;        /* storage of the coarsest inverses (exact or MG-DD) used by the complex64
+                            cycle: 0 complex double-float (FP64-class), 1 complex64, 2 FP16
+                            pairs, 3 BF16 pairs; products accumulate in FP32 (double-float
+                            for 0); formed in FP64 at setup in every case */
 } ehs_opts;
 
 typedef struct {
@@ -151,6 +153,22 @@ ehs_status ehs_smooth(ehs_ctx* ctx, int level, int nsweeps, int prec, const void
 /* x := one multigrid cycle (Algorithm TwoCycle, recursive) for K_s x = b
  * from a zero initial guess.  Device pointers, fine-grid slot layout. */
 ehs_status ehs_vcycle(ehs_ctx* ctx, int prec, const void* b, void* x);
+
+/* Coarsest-level solve (Algorithm TwoCycle step 3 at the last level): x = K_c^{-1} b through
+   the stored dense inverse (exact), or by the MG-DD sweep of Sec. 4 when opts.coarse_dd splits
+   the coarsest grid.  b, x: device, [items][(d+1) * ncell_c] complex of prec (ehs_level_len of
+   the last level).  MG contexts only (EHS_ERR_ARG otherwise). */
+ehs_status ehs_coarse_solve(ehs_ctx* ctx, int prec, const void* b, void* x);
+/* Shape of the coarsest local solves: nsub subdomains (1 for the exact solve), padded local size
+   nloc (local vectors are [items][nsub][nloc]), and, if sizes is not NULL, the live unknowns of
+   each subdomain (host array of nsub ints).  MG contexts only. */
+ehs_status ehs_coarse_dims(const ehs_ctx* ctx, int* nsub, int* nloc, int* sizes);
+/* One launch of the coarsest local products z_loc = A_s^{-1} r_loc for every subdomain s of
+   colour `colour` (0 .. 2^d - 1; the exact solve has colour 0 only), i.e. step 2 of Algorithm DD
+   on the coarsest grid with the inverses formed at setup.  r_loc, z_loc: device [items][nsub][nloc]
+   complex of prec; entries of other colours' subdomains and of padding rows are left unspecified.
+   The complex64 form reads the inverses in opts.coarse_fmt storage. */
+ehs_status ehs_coarse_local_apply(ehs_ctx* ctx, int prec, int colour, const void* r_loc, void* z_loc);
 
 /* z := one sweep of Algorithm DD on K z = r (global residual recomputed
  * before each colour, subdomain corrections by one multigrid cycle of the

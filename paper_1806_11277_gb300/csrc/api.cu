@@ -53,7 +53,7 @@ struct Level {
   void* tabh = nullptr;       // half-precision copy (FP16 or BF16 pairs) for the complex64 cycle
   double2* inv = nullptr;     // coarsest: [nsets][N][N]
   float4* invdf = nullptr;    // coarsest inverse in complex df64 (used by the complex64 cycle)
-  float2* inv32 = nullptr;    // coarsest inverse in complex64 (complex64 cycle with coarse_c64)
+  void* invlp = nullptr;      // coarsest inverse in complex64 / FP16 / BF16 pairs (coarse_fmt 1..3)
   void* binv[2] = {nullptr, nullptr};  // full Vanka block inverses [prec: 0 double2, 1 float2 or half pairs]
   void* ws[2][4] = {{nullptr}};  // [prec: 0 double, 1 float][b, x, t, r]
   int rows_var[2] = {0, 0};      // residual-pass launch shape per precision (setup autotuner)
@@ -66,9 +66,12 @@ struct CoarseDD {
   int nsub = 0;                 // 0: exact dense coarsest solve
   int nloc = 0;                 // local dense size (largest subdomain; smaller ones padded)
   int* d_map = nullptr;         // [nsub][nloc] coarsest slot (comp * ncell + cell) or -1
+  int* d_sizes = nullptr;       // [nsub] live unknowns of each subdomain (<= nloc)
+  std::vector<int> sizes;
   std::vector<std::vector<int>> col_subs;  // subdomains of each colour (2^d colours)
   std::vector<int*> d_col_subs;
   std::vector<int*> d_list;     // per colour: expanded sub-item list [items * ncs]
+  std::vector<int*> d_list_all; // per colour: the sub-item list with every item active (setup)
   void* loc[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [prec][r, z] [items * nsub][nloc]
 };
 
@@ -82,7 +85,7 @@ struct Hier {
   int full = 0;                // 1: full cell-block Vanka instead of the economic block
   int cdd_split[3] = {1, 1, 1};  // MG-DD subdomains per axis of the coarsest grid
   int cdd_overlap = 2;
-  int coarse_c64 = 0;          // complex64 (1) or double-float (0) coarsest inverses, complex64 cycle
+  int coarse_fmt = 0;          // coarsest inverses of the complex64 cycle: 0 df64, 1 c64, 2 FP16, 3 BF16
   CoarseDD cdd;
   bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
   Coef4<double>* cf64 = nullptr;
@@ -298,8 +301,14 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
                 }
         }
     nloc = 0;
-    for (auto& v : dofs) nloc = std::max(nloc, (int)v.size());
+    for (auto& v : dofs) {
+      nloc = std::max(nloc, (int)v.size());
+      D.sizes.push_back((int)v.size());
+    }
+    nloc = (nloc + 7) / 8 * 8;   // rows start 16-byte aligned for the vectorised local products
     D.nloc = nloc;
+    D.d_sizes = dalloc<int>(c, D.nsub);
+    CK(cudaMemcpyAsync(D.d_sizes, D.sizes.data(), D.nsub * sizeof(int), cudaMemcpyHostToDevice, c->s));
     std::vector<int> map((size_t)D.nsub * nloc, -1), g2l((size_t)D.nsub * NG, -1);
     for (int q = 0; q < D.nsub; ++q)
       for (int e = 0; e < (int)dofs[q].size(); ++e) {
@@ -321,6 +330,16 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
       }
       D.d_col_subs.push_back(ds);
       D.d_list.push_back(dl);
+      int* da = nullptr;
+      if (!cs.empty()) {
+        std::vector<int> all;
+        for (int b = 0; b < H.items; ++b)
+          for (int q : cs) all.push_back(((b / H.nrhs) * D.nsub + q) * H.nrhs + b % H.nrhs);
+        da = dalloc<int>(c, all.size());
+        CK(cudaMemcpyAsync(da, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, c->s));
+        CK(cudaStreamSynchronize(c->s));
+      }
+      D.d_list_all.push_back(da);
     }
     for (int p = 0; p < 2; ++p)
       if (precs & (1 << p))
@@ -345,9 +364,12 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
   C.inv = dalloc<double2>(c, (size_t)nmat * N * N);
   dense_invert((int)N, nmat, M, C.inv, fb, pv, derr, c->s); cnt(4 * N + 1); post();
   if (precs & 2) {
-    if (H.coarse_c64) {
-      C.inv32 = dalloc<float2>(c, (size_t)nmat * N * N);
-      launch_table_cast<float>((long long)nmat * N * N, C.inv, C.inv32, c->s); cnt(); post();
+    if (H.coarse_fmt == 1) {
+      C.invlp = dalloc<float2>(c, (size_t)nmat * N * N);
+      launch_table_cast<float>((long long)nmat * N * N, C.inv, (float2*)C.invlp, c->s); cnt(); post();
+    } else if (H.coarse_fmt >= 2) {
+      C.invlp = dalloc<float>(c, (size_t)nmat * N * N);   // 4 bytes per complex entry
+      launch_table_half((long long)nmat * N * N, C.inv, C.invlp, H.coarse_fmt - 1, c->s); cnt(); post();
     } else {
       C.invdf = dalloc<float4>(c, (size_t)nmat * N * N);
       launch_d2_to_df((long long)nmat * N * N, C.inv, C.invdf, c->s); cnt(); post();
@@ -472,8 +494,9 @@ template <typename T>
 void coarse_gemv(ehs_ctx* c, const Hier& H, const Level& L, int N, int items, const typename CT<T>::type* b,
                  typename CT<T>::type* x) {
   if (PT<T>::i == 1) {
-    if (L.inv32)   // complex64 inverse, FP32 accumulation
-      launch_dense_apply_c64(N, items, H.nrhs, L.inv32, (const float2*)b, (float2*)x, c->s);
+    if (L.invlp)   // complex64 / FP16 / BF16 inverse, FP32 accumulation
+      launch_dense_apply_lp(N, items, H.nrhs, H.cdd.nsub ? H.cdd.nsub : 1, H.cdd.nsub ? H.cdd.d_sizes : nullptr,
+                            L.invlp, H.coarse_fmt, (const float2*)b, (float2*)x, c->s);
     else           // FP64-class (df64) inverse on the FP32 pipe
       launch_dense_apply_df(N, items, H.nrhs, L.invdf, (const float2*)b, (float2*)x, c->s);
   } else {
@@ -576,7 +599,7 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (O->precond != EHS_PRECOND_MG && O->precond != EHS_PRECOND_DD) throw ArgError("bad precond");
   if (O->coef_half < 0 || O->coef_half > 2) throw ArgError("coef_half must be 0, 1 (FP16) or 2 (BF16)");
   if (O->vanka_full != 0 && O->vanka_full != 1) throw ArgError("vanka_full must be 0 or 1");
-  if (O->coarse_c64 != 0 && O->coarse_c64 != 1) throw ArgError("coarse_c64 must be 0 or 1");
+  if (O->coarse_fmt < 0 || O->coarse_fmt > 3) throw ArgError("coarse_fmt must be 0..3");
   for (int k = 0; k < 3; ++k)
     if (O->coarse_dd[k] < 0) throw ArgError("coarse_dd must be >= 0");
 }
@@ -1016,7 +1039,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     H.full = opts->vanka_full;
     for (int k = 0; k < 3; ++k) H.cdd_split[k] = k < prob->dim ? std::max(opts->coarse_dd[k], 1) : 1;
     H.cdd_overlap = opts->coarse_dd_overlap;
-    H.coarse_c64 = opts->coarse_c64;
+    H.coarse_fmt = opts->coarse_fmt;
     c->n0 = (long long)(c->d + 1) * H.g0.ncell;
     const long long nc = (long long)H.nsets * H.g0.ncell;
     check_media(c, prob->lambda, prob->mu, prob->rho, nc);
@@ -1152,6 +1175,65 @@ ehs_status ehs_vcycle(ehs_ctx* c, int prec, const void* b, void* x) {
     if (!b || !x) throw ArgError("null vector");
     if (prec == EHS_C128) cycle_rec<double>(c, c->H, 0, (const double2*)b, (double2*)x, false);
     else cycle_rec<float>(c, c->H, 0, (const float2*)b, (float2*)x, false);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_coarse_solve(ehs_ctx* c, int prec, const void* b, void* x) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!b || !x) throw ArgError("null vector");
+    const int l = c->H.nlev - 1;
+    if (prec == EHS_C128) cycle_rec<double>(c, c->H, l, (const double2*)b, (double2*)x, false);
+    else cycle_rec<float>(c, c->H, l, (const float2*)b, (float2*)x, false);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_coarse_dims(const ehs_ctx* c, int* nsub, int* nloc, int* sizes) {
+  if (!c || !nsub || !nloc) return EHS_ERR_ARG;
+  if (c->H.coef_only) return EHS_ERR_ARG;
+  const Hier& H = c->H;
+  const Level& L = H.lv.back();
+  if (H.cdd.nsub) {
+    *nsub = H.cdd.nsub;
+    *nloc = H.cdd.nloc;
+    if (sizes)
+      for (int q = 0; q < H.cdd.nsub; ++q) sizes[q] = H.cdd.sizes[q];
+  } else {
+    *nsub = 1;
+    *nloc = (int)((L.g.d + 1) * L.g.ncell);
+    if (sizes) sizes[0] = *nloc;
+  }
+  return EHS_OK;
+}
+
+ehs_status ehs_coarse_local_apply(ehs_ctx* c, int prec, int colour, const void* r, void* z) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!r || !z) throw ArgError("null vector");
+    Hier& H = c->H;
+    const Level& L = H.lv.back();
+    CoarseDD& D = H.cdd;
+    if (!D.nsub) {
+      if (colour != 0) throw ArgError("the exact coarsest solve has colour 0 only");
+      const int N = (int)((L.g.d + 1) * L.g.ncell);
+      if (prec == EHS_C128) coarse_gemv<double>(c, H, L, N, H.items, (const double2*)r, (double2*)z);
+      else coarse_gemv<float>(c, H, L, N, H.items, (const float2*)r, (float2*)z);
+      return EHS_OK;
+    }
+    if (colour < 0 || colour >= (int)D.col_subs.size() || D.col_subs[colour].empty())
+      throw ArgError("no coarsest subdomain has this colour");
+    const int ncs = (int)D.col_subs[colour].size();
+    SelScope sel(D.d_list_all[colour], H.items * ncs);   // one launch: the local products alone
+    if (prec == EHS_C128)
+      coarse_gemv<double>(c, H, L, D.nloc, H.items * D.nsub, (const double2*)r, (double2*)z);
+    else
+      coarse_gemv<float>(c, H, L, D.nloc, H.items * D.nsub, (const float2*)r, (float2*)z);
     return EHS_OK;
   });
 }

@@ -4,6 +4,8 @@
 // coarsest LU does).  Boundary slots are identity rows so the dense index is
 // simply comp * ncell + cell.
 #include "kernels.h"
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 namespace ehs {
 namespace {
@@ -189,20 +191,25 @@ __global__ void k_dense_assemble_sub(Grid g, StencilLayout L, const double2* __r
   }
 }
 
-// x = Ainv r with Ainv stored in complex64 (FP32 accumulation); one warp per
-// row, four independent loads in flight per lane
-__global__ void k_dense_apply_c64(int N, int nrhs, const float2* __restrict__ inv, const float2* __restrict__ r,
-                                  float2* __restrict__ x, const int* __restrict__ il) {
+// x = Ainv r with Ainv stored in complex64, FP16 or BF16 pairs (FP32
+// accumulation); one warp per row, four independent loads in flight per lane
+__device__ __forceinline__ float2 ldlp(const float2* p) { return *p; }
+__device__ __forceinline__ float2 ldlp(const __half2* p) { return __half22float2(*p); }
+__device__ __forceinline__ float2 ldlp(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+
+template <typename TI>
+__global__ void k_dense_apply_lp(int N, int nrhs, const TI* __restrict__ inv, const float2* __restrict__ r,
+                                 float2* __restrict__ x, const int* __restrict__ il) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   if (warp >= N) return;
-  const float2* row = inv + ((long long)(item / nrhs) * N + warp) * N;
+  const TI* row = inv + ((long long)(item / nrhs) * N + warp) * N;
   const float2* rv = r + (long long)item * N;
   float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
   int j = lane;
   for (; j + 96 < N; j += 128) {
-    const float2 a0 = __ldg(row + j), a1 = __ldg(row + j + 32), a2 = __ldg(row + j + 64), a3 = __ldg(row + j + 96);
+    const float2 a0 = ldlp(row + j), a1 = ldlp(row + j + 32), a2 = ldlp(row + j + 64), a3 = ldlp(row + j + 96);
     const float2 b0 = __ldg(rv + j), b1 = __ldg(rv + j + 32), b2 = __ldg(rv + j + 64), b3 = __ldg(rv + j + 96);
     sx0 = fmaf(a0.x, b0.x, fmaf(-a0.y, b0.y, sx0)); sy0 = fmaf(a0.x, b0.y, fmaf(a0.y, b0.x, sy0));
     sx1 = fmaf(a1.x, b1.x, fmaf(-a1.y, b1.y, sx1)); sy1 = fmaf(a1.x, b1.y, fmaf(a1.y, b1.x, sy1));
@@ -210,7 +217,7 @@ __global__ void k_dense_apply_c64(int N, int nrhs, const float2* __restrict__ in
     sx1 = fmaf(a3.x, b3.x, fmaf(-a3.y, b3.y, sx1)); sy1 = fmaf(a3.x, b3.y, fmaf(a3.y, b3.x, sy1));
   }
   for (; j < N; j += 32) {
-    const float2 a = __ldg(row + j), b = __ldg(rv + j);
+    const float2 a = ldlp(row + j), b = __ldg(rv + j);
     sx0 = fmaf(a.x, b.x, fmaf(-a.y, b.y, sx0)); sy0 = fmaf(a.x, b.y, fmaf(a.y, b.x, sy0));
   }
   float sx = sx0 + sx1, sy = sy0 + sy1;
@@ -219,6 +226,66 @@ __global__ void k_dense_apply_c64(int N, int nrhs, const float2* __restrict__ in
     sy += __shfl_xor_sync(0xffffffffu, sy, o);
   }
   if (lane == 0) x[(long long)item * N + warp] = make_float2(sx, sy);
+}
+
+// The same product with 16-byte loads: each warp computes R = 4 consecutive
+// rows, so every lane keeps four 16-byte matrix loads in flight and reuses each
+// chunk of r for the four rows (E entries per 16-byte load; N a multiple of 4
+// and of E, so every row starts 16-byte aligned).  Matrix set (item / nrhs) has
+// n = sizes[set % nsub] live rows and columns (MG-DD subdomains smaller than
+// the padded N); columns beyond n hold the zero padding of the identity rows
+// and are skipped, and so are groups of rows at or beyond n (their outputs are
+// never read).
+template <typename TI>
+__global__ void __launch_bounds__(256) k_dense_apply_v(int N, int nrhs, int nsub, const int* __restrict__ sizes,
+                                                       const TI* __restrict__ inv, const float2* __restrict__ r,
+                                                       float2* __restrict__ x, const int* __restrict__ il) {
+  constexpr int E = 16 / (int)sizeof(TI);
+  constexpr int R = 4;
+  const int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R;
+  const int lane = threadIdx.x & 31;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  const int set = item / nrhs;
+  const int n = sizes ? sizes[set % nsub] : N;
+  if (row0 >= n) return;
+  const int nq = (n + E - 1) / E;                  // 16-byte chunks per live row
+  const uint4* m0 = (const uint4*)(inv + ((long long)set * N + row0) * N);
+  const int qs = N / E;                            // chunks per stored row
+  const float4* rv = (const float4*)(r + (long long)item * N);
+  union U { uint4 u; TI t[E]; };
+  float ax[R], ay[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) { ax[k] = 0.f; ay[k] = 0.f; }
+  for (int q = lane; q < nq; q += 32) {
+    U a[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) a[k].u = __ldg(m0 + (long long)k * qs + q);
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+      const float4 b = __ldg(rv + (q * E + e) / 2);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const float2 c0 = ldlp(&a[k].t[e]), c1 = ldlp(&a[k].t[e + 1]);
+        ax[k] = fmaf(c0.x, b.x, fmaf(-c0.y, b.y, ax[k]));
+        ay[k] = fmaf(c0.x, b.y, fmaf(c0.y, b.x, ay[k]));
+        ax[k] = fmaf(c1.x, b.z, fmaf(-c1.y, b.w, ax[k]));
+        ay[k] = fmaf(c1.x, b.w, fmaf(c1.y, b.z, ay[k]));
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      ax[k] += __shfl_xor_sync(0xffffffffu, ax[k], o);
+      ay[k] += __shfl_xor_sync(0xffffffffu, ay[k], o);
+    }
+  if (lane < R) {
+    float vx = ax[0], vy = ay[0];
+#pragma unroll
+    for (int k = 1; k < R; ++k)
+      if (lane == k) { vx = ax[k]; vy = ay[k]; }
+    x[(long long)item * N + row0 + lane] = make_float2(vx, vy);
+  }
 }
 
 }  // namespace
@@ -258,11 +325,28 @@ void launch_dense_assemble_sub(const Grid& g, int nsets, int nsub, int nloc, con
   else k_dense_assemble_sub<3><<<grid, 128, 0, s>>>(g, L, tab, nsub, nloc, map, g2l, A);
 }
 
-void launch_dense_apply_c64(int N, int items, int nrhs, const float2* inv, const float2* r, float2* x,
-                            cudaStream_t s) {
+void launch_dense_apply_lp(int N, int items, int nrhs, int nsub, const int* sizes, const void* inv, int fmt,
+                           const float2* r, float2* x, cudaStream_t s) {
   const int wpb = 8;
   const dim3 grid((N + wpb - 1) / wpb, sel_items(items));
-  k_dense_apply_c64<<<grid, 32 * wpb, 0, s>>>(N, nrhs, inv, r, x, g_sel.list);
+  const int E = fmt >= 2 ? 4 : 2;
+  if (N % 4 == 0 && N % E == 0) {
+    const dim3 gv((N / 4 + wpb - 1) / wpb, sel_items(items));   // a warp per 4 rows
+    if (fmt == 2)
+      k_dense_apply_v<__half2><<<gv, 32 * wpb, 0, s>>>(N, nrhs, nsub, sizes, (const __half2*)inv, r, x, g_sel.list);
+    else if (fmt == 3)
+      k_dense_apply_v<__nv_bfloat162><<<gv, 32 * wpb, 0, s>>>(N, nrhs, nsub, sizes, (const __nv_bfloat162*)inv, r, x,
+                                                              g_sel.list);
+    else
+      k_dense_apply_v<float2><<<gv, 32 * wpb, 0, s>>>(N, nrhs, nsub, sizes, (const float2*)inv, r, x, g_sel.list);
+    return;
+  }
+  if (fmt == 2)
+    k_dense_apply_lp<__half2><<<grid, 32 * wpb, 0, s>>>(N, nrhs, (const __half2*)inv, r, x, g_sel.list);
+  else if (fmt == 3)
+    k_dense_apply_lp<__nv_bfloat162><<<grid, 32 * wpb, 0, s>>>(N, nrhs, (const __nv_bfloat162*)inv, r, x, g_sel.list);
+  else
+    k_dense_apply_lp<float2><<<grid, 32 * wpb, 0, s>>>(N, nrhs, (const float2*)inv, r, x, g_sel.list);
 }
 
 template void launch_dense_apply<float>(int, int, int, const double2*, const float2*, float2*, cudaStream_t);

@@ -106,9 +106,11 @@ void launch_dense_apply(int N, int items, int nrhs, const double2* inv, const ty
 // MG-DD: local dense matrices of the coarsest-grid subdomains ([nsets*nsub][nloc][2 nloc], augmented)
 void launch_dense_assemble_sub(const Grid& g, int nsets, int nsub, int nloc, const StencilLayout& L,
                                const double2* tab, const int* map, const int* g2l, double2* A, cudaStream_t s);
-// x = inv r with a complex64 inverse (FP32 accumulation); matrix of item b: inv + (b / nrhs) N^2
-void launch_dense_apply_c64(int N, int items, int nrhs, const float2* inv, const float2* r, float2* x,
-                            cudaStream_t s);
+// x = inv r with a low-precision inverse, FP32 accumulation; fmt 1 complex64, 2 FP16 pairs,
+// 3 BF16 pairs; matrix of item b: inv + (b / nrhs) N^2 entries.  sizes (device, optional):
+// live size of matrix set s is sizes[s % nsub], the rest identity padding (skipped)
+void launch_dense_apply_lp(int N, int items, int nrhs, int nsub, const int* sizes, const void* inv, int fmt,
+                           const float2* r, float2* x, cudaStream_t s);
 // sub-item list of MG-DD / DD: out[j * ncs + q] = ((m * nsub) + subs[q]) * nrhs + r for the
 // j-th active item b = m * nrhs + r (all items when list is null)
 void launch_expand_items(const int* list, int nact, int nrhs, int nsub, const int* subs, int ncs, int* out,

@@ -39,7 +39,7 @@ class Opts(C.Structure):
                 ("vanka_full", C.c_int),
                 ("coarse_dd", C.c_int * 3),
                 ("coarse_dd_overlap", C.c_int),
-                ("coarse_c64", C.c_int)]
+                ("coarse_fmt", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -49,7 +49,8 @@ class SolveInfo(C.Structure):
 EXPORTS = ["ehs_default_opts", "ehs_create", "ehs_destroy", "ehs_op_apply", "ehs_smooth",
            "ehs_vcycle", "ehs_dd_precond", "ehs_fgmres_solve", "ehs_adjoint_solve", "ehs_items",
            "ehs_level_len", "ehs_level_dims", "ehs_sync", "ehs_kernel_launches", "ehs_last_error",
-           "ehs_fine_smooth_noalloc", "ehs_gradient"]
+           "ehs_fine_smooth_noalloc", "ehs_gradient", "ehs_coarse_solve", "ehs_coarse_dims",
+           "ehs_coarse_local_apply"]
 
 _lib = None
 
@@ -85,6 +86,9 @@ def load(path=LIB_PATH):
     lib.ehs_last_error.restype = C.c_char_p
     lib.ehs_fine_smooth_noalloc.argtypes = [C.POINTER(Problem), i, d, d, d, i, i, vp, vp, vp]
     lib.ehs_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.ehs_coarse_solve.argtypes = [vp, i, vp, vp]
+    lib.ehs_coarse_dims.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
+    lib.ehs_coarse_local_apply.argtypes = [vp, i, i, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)
     _lib = lib
@@ -190,6 +194,22 @@ class Solver:
     def vcycle(self, b, x, prec=None):
         prec = _prec_of(x) if prec is None else prec
         self._check(self.lib.ehs_vcycle(self.ctx, prec, _ptr(b), _ptr(x)))
+
+    def coarse_solve(self, b, x, prec=None):
+        prec = _prec_of(x) if prec is None else prec
+        self._check(self.lib.ehs_coarse_solve(self.ctx, prec, _ptr(b), _ptr(x)))
+
+    def coarse_dims(self):
+        """(nsub, nloc, sizes) of the coarsest local solves (nsub = 1: exact solve)."""
+        ns, nl = C.c_int(), C.c_int()
+        self._check(self.lib.ehs_coarse_dims(self.ctx, C.byref(ns), C.byref(nl), None))
+        sizes = (C.c_int * ns.value)()
+        self._check(self.lib.ehs_coarse_dims(self.ctx, C.byref(ns), C.byref(nl), sizes))
+        return ns.value, nl.value, list(sizes)
+
+    def coarse_local_apply(self, colour, r_loc, z_loc, prec=None):
+        prec = _prec_of(z_loc) if prec is None else prec
+        self._check(self.lib.ehs_coarse_local_apply(self.ctx, prec, colour, _ptr(r_loc), _ptr(z_loc)))
 
     def dd_precond(self, r, z, prec=EHS_C64):
         self._check(self.lib.ehs_dd_precond(self.ctx, prec, _ptr(r), _ptr(z)))
