@@ -95,4 +95,49 @@ __device__ __forceinline__ float2 dfc_to_f2(dfc a) {
 __device__ __forceinline__ dfc dfc_from_d2(double2 z) { return {df_from_d(z.x), df_from_d(z.y)}; }
 __device__ __forceinline__ double2 dfc_to_d2(dfc a) { return make_double2(df_to_d(a.re), df_to_d(a.im)); }
 
+// Compensated sums of products (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, algorithm Dot2): a running FP32 sum s
+// whose TwoSum rounding errors, the TwoProduct errors of each product and the
+// df64 cross terms hi*lo + lo*hi all go into a second FP32 term c, added back
+// once at the end.  The result is as accurate as a sum carried in twice the
+// working precision (the same class as df64), with about a third of the
+// operations of a renormalised df64 multiply-add per term.
+struct dacc {
+  float s, c;
+};
+__device__ __forceinline__ dacc dacc_zero() { return {0.0f, 0.0f}; }
+// a += x * y
+__device__ __forceinline__ void dacc_fma(dacc& a, dfr x, dfr y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float pe = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+  const float t = __fadd_rn(a.s, p);
+  const float bb = __fadd_rn(t, -a.s);
+  const float sg = __fadd_rn(__fadd_rn(a.s, -__fadd_rn(t, -bb)), __fadd_rn(p, -bb));
+  a.s = t;
+  a.c = __fadd_rn(a.c, __fadd_rn(sg, pe));
+}
+// a -= x * y
+__device__ __forceinline__ void dacc_fms(dacc& a, dfr x, dfr y) { dacc_fma(a, df_neg(x), y); }
+__device__ __forceinline__ dfr dacc_val(dacc a) { return df_two_sum(a.s, a.c); }
+
+struct dcacc {
+  dacc re, im;
+};
+__device__ __forceinline__ dcacc dcacc_zero() { return {dacc_zero(), dacc_zero()}; }
+// a += conj(x) * y
+__device__ __forceinline__ void dcacc_cfma(dcacc& a, dfc x, dfc y) {
+  dacc_fma(a.re, x.re, y.re);
+  dacc_fma(a.re, x.im, y.im);
+  dacc_fma(a.im, x.re, y.im);
+  dacc_fms(a.im, x.im, y.re);
+}
+// a += x * y
+__device__ __forceinline__ void dcacc_fma(dcacc& a, dfc x, dfc y) {
+  dacc_fma(a.re, x.re, y.re);
+  dacc_fms(a.re, x.im, y.im);
+  dacc_fma(a.im, x.re, y.im);
+  dacc_fma(a.im, x.im, y.re);
+}
+__device__ __forceinline__ dfc dcacc_val(dcacc a) { return {dacc_val(a.re), dacc_val(a.im)}; }
+
 }  // namespace ehs

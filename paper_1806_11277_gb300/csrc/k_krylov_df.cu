@@ -66,61 +66,73 @@ template <int NV>
 __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const float4* __restrict__ V,
                                                 const float4* __restrict__ w, float4* part, int nblk, const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
-  dfc acc[NV];
+  dcacc acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = dfc_zero();
+  for (int i = 0; i < NV; ++i) acc[i] = dcacc_zero();
   const float4* wv = w + (long long)item * n;
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
     const dfc we = dfc_ld(wv + e);
 #pragma unroll
-    for (int i = 0; i < NV; ++i)
-      acc[i] = dfc_add(acc[i], dfc_cmul(dfc_ld(V + ((long long)i * items + item) * n + e), we));
+    for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], dfc_ld(V + ((long long)i * items + item) * n + e), we);
   }
-  block_store_df(acc, NV, part, item, nblk);
+  dfc out[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = dcacc_val(acc[i]);
+  block_store_df(out, NV, part, item, nblk);
 }
 
-// w -= sum_i V_i h_i; optional partial dots of V with the new w and |w|^2
+// w -= sum_i V_i h_i; optional partial dots of V with the new w and |w|^2.
+// h sits in shared memory and the dot pass re-reads V_i (an L1 hit: the block
+// read it a moment earlier), which keeps the kernel at two blocks per SM.
 template <int NV>
-__global__ void __launch_bounds__(KB) k_mupdate_df(long long n, int items, const float4* __restrict__ V,
-                                                   const float4* __restrict__ h, float4* __restrict__ w,
-                                                   float4* part, int nblk, int dot, float2* nrm_part, const int* __restrict__ il) {
+__global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, const float4* __restrict__ V,
+                                                      const float4* __restrict__ h, float4* __restrict__ w,
+                                                      float4* part, int nblk, int dot, float2* nrm_part,
+                                                      const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
-  dfc hh[NV];
+  __shared__ float4 hs[NV];
+  if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
+  __syncthreads();
+  dcacc acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) hh[i] = dfc_ld(h + (long long)item * NV + i);
-  dfc acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = dfc_zero();
-  dfr nacc = df_zero();
+  for (int i = 0; i < NV; ++i) acc[i] = dcacc_zero();
+  dacc nacc = dacc_zero();
   float4* wv = w + (long long)item * n;
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
-    dfc we = dfc_ldv(wv + e);
-    dfc vv[NV];
+    dcacc sv = dcacc_zero();
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
-      we = dfc_sub(we, dfc_mul(vv[i], hh[i]));
+      const float4 hv = hs[i];
+      dcacc_fma(sv, dfc_ld(V + ((long long)i * items + item) * n + e), dfc{{hv.x, hv.y}, {hv.z, hv.w}});
     }
+    const dfc we = dfc_sub(dfc_ldv(wv + e), dcacc_val(sv));
     dfc_st(wv + e, we);
     if (dot) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] = dfc_add(acc[i], dfc_cmul(vv[i], we));
+      for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], dfc_ld(V + ((long long)i * items + item) * n + e), we);
     }
-    nacc = df_add(nacc, df_add(df_mul(we.re, we.re), df_mul(we.im, we.im)));
+    dacc_fma(nacc, we.re, we.re);
+    dacc_fma(nacc, we.im, we.im);
   }
-  if (dot) block_store_df(acc, NV, part, item, nblk);
-  if (nrm_part) block_store_norm(nacc, nrm_part, item, nblk);
+  if (dot) {
+    dfc out[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = dcacc_val(acc[i]);
+    block_store_df(out, NV, part, item, nblk);
+  }
+  if (nrm_part) block_store_norm(dacc_val(nacc), nrm_part, item, nblk);
 }
 
 __global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2* part, int nblk, const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   const float4* wv = w + (long long)item * n;
-  dfr nacc = df_zero();
+  dacc nacc = dacc_zero();
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
     const dfc we = dfc_ld(wv + e);
-    nacc = df_add(nacc, df_add(df_mul(we.re, we.re), df_mul(we.im, we.im)));
+    dacc_fma(nacc, we.re, we.re);
+    dacc_fma(nacc, we.im, we.im);
   }
-  block_store_norm(nacc, part, item, nblk);
+  block_store_norm(dacc_val(nacc), part, item, nblk);
 }
 
 // one warp per output; writes the df64 value and its double copy for the host
