@@ -73,8 +73,9 @@ ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one col
 # Galerkin level-1 apply (k_st_rows): 87 stencil coefficients (FP16 pairs, 4 B) + x 24 + y 24
 ST_ROWS_L1_BYTES_PER_CELL = 87 * 4 + 24 + 24
 # DRAM read + write bytes of one roofline-kernel launch (one colour) of the default line, from an
-# ncu capture of the kernel as it stands (None whenever the kernel changes)
-ROOF_TRAFFIC_C2 = None
+# ncu capture of the kernel as it stands (None whenever the kernel changes): mean of 7 warm
+# launches, profiles/k_dense_apply_v_mgdd_512x512.md
+ROOF_TRAFFIC_C2 = 450.84e6 + 5.88e6
 
 
 def media(seed=0):
@@ -332,11 +333,12 @@ def run_gpu(args):
     qd = torch.from_numpy(q_host).to(dev)
     ud = torch.zeros_like(qd)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    roof_note = []
+
     def roofline_coarse():
         # roofline of the dominant kernel of the MG-DD line, the coarsest local products
         # (k_dense_apply_v): one launch = ehs_coarse_local_apply of one colour (every
-        # subdomain of that colour, every item); each colour timed in turn, one launch per
-        # sample, L2 flushed before each, events on the solver's stream
+        # subdomain of that colour, every item); events on the solver's stream
         ns, nloc, sizes = S.coarse_dims()
         c64 = kw["prec"] == ehs.EHS_C64
         eb = {0: 16, 1: 8, 2: 4, 3: 4}[kw.get("coarse_fmt", 0)] if c64 else 16
@@ -351,20 +353,26 @@ def run_gpu(args):
         for q, n in enumerate(sizes):
             col = (q % nx) % 2 + 2 * ((q // nx) % 2)
             cols[col] = cols.get(col, 0) + nsets * n * n * eb + S.items * n * 2 * vb
-        kt = {col: [] for col in cols}
+        # Every launch reads more than L2 holds (the colour's inverses, ~445 MB), so no
+        # flush is needed between them: per sample the four colours run back to back
+        # between one pair of events, queued behind a read-only 512 MiB pass (which
+        # leaves L2 clean and keeps host launch gaps outside the events).
+        kt = []
         for rep in range(args.kernel_reps):
-            for col in cols:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(stream):
-                    flush.fill_(1)
-                    e0.record(stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.sum()
+                e0.record(stream)
+                for col in cols:
                     S.coarse_local_apply(col, r, z)
-                    e1.record(stream)
-                e1.synchronize()
-                kt[col].append(e0.elapsed_time(e1) / 1e3)
-        tsum = sum(statistics.median(kt[col]) for col in cols)
+                e1.record(stream)
+            e1.synchronize()
+            kt.append(e0.elapsed_time(e1) / 1e3)
+        tsum = statistics.median(kt)
         bsum = sum(cols.values())
+        roof_note.append("the %d colour launches back to back per event pair (each reads > L2), median of %d "
+                         "samples; per-launch time = sample / %d" % (len(cols), args.kernel_reps, len(cols)))
         return tsum / len(cols), bsum / len(cols), bsum / tsum / 1e9
 
     def roofline():
@@ -490,7 +498,9 @@ def run_gpu(args):
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": args.traffic if args.traffic is not None else
                      (ROOF_TRAFFIC_C2 if cfg is None else None), "alg_bytes_per_launch": alg,
-                     "launch_us": t_launch * 1e6},
+                     "launch_us": t_launch * 1e6,
+                     "timing": roof_note[-1] if roof_note else
+                     "one launch per event pair, queued behind a 512 MiB L2-flushing write"},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu and cfg is None:
