@@ -452,8 +452,9 @@ void level_sweep(ehs_ctx* c, const Hier& H, int l, const typename CT<T>::type* b
 }
 
 // Setup autotuner: times every residual-pass launch shape of each smoothed
-// Galerkin level (its working precision and table format, on the level's own
-// buffers) and keeps the fastest.  Runs at setup, outside any capture.
+// Galerkin level, and of the coarsest level under MG-DD (its working precision
+// and table format, on the level's own buffers) and keeps the fastest.  Runs
+// at setup, outside any capture.
 template <typename T>
 void autotune_rows(ehs_ctx* c, Hier& H) {
   typedef typename CT<T>::type C;
@@ -461,7 +462,9 @@ void autotune_rows(ehs_ctx* c, Hier& H) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int l = 1; l + 1 < H.nlev; ++l) {
+  // smoothed Galerkin levels, and the coarsest level when the MG-DD sweep takes residuals there
+  const int ltop = H.cdd.nsub ? H.nlev : H.nlev - 1;
+  for (int l = 1; l < ltop; ++l) {
     Level& L = H.lv[l];
     int fmt = 0;
     const void* tab = tabp<T>(H, L, &fmt);
