@@ -510,8 +510,9 @@ void coarse_gemv(ehs_ctx* c, const Hier& H, const Level& L, int N, int items, co
 
 // MG-DD coarsest solve (Sec. 4 with Algorithm DD): one multiplicative sweep
 // over the colours from x = 0; before every colour but the first the residual
-// b - K_c x is recomputed, gathered into the colour's subdomains, solved with
-// their dense inverses and scatter-added on the subdomain unknowns.
+// b - K_c x is recomputed at the colour's subdomain unknowns (fused with their
+// gather), solved with the subdomains' dense inverses and scatter-added on the
+// subdomain unknowns.
 template <typename T>
 void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typename CT<T>::type* x) {
   typedef typename CT<T>::type C;
@@ -520,7 +521,6 @@ void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typenam
   CoarseDD& D = H.cdd;
   const int p = PT<T>::i;
   const long long NG = (long long)(L.g.d + 1) * L.g.ncell;
-  C* r = (C*)L.ws[p][3];
   C* rs = (C*)D.loc[p][0];
   C* zs = (C*)D.loc[p][1];
   CK(cudaMemsetAsync(x, 0, (size_t)H.items * NG * sizeof(C), c->s));
@@ -530,16 +530,18 @@ void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typenam
   for (int col = 0; col < (int)D.col_subs.size(); ++col) {
     const int ncs = (int)D.col_subs[col].size();
     if (!ncs) continue;
-    const C* cur = b;
-    if (!first) {
-      level_apply<T>(c, H, l, H.alpha, x, b, r, 1);
-      cur = r;
-    }
-    first = false;
     launch_expand_items(act, nact, H.nrhs, D.nsub, D.d_col_subs[col], ncs, D.d_list[col], c->s); cnt(); post();
     SelScope sel(D.d_list[col], nact * ncs);
     const int items_l = H.items * D.nsub;
-    launch_dd_gather<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, cur, rs, c->s); cnt(); post();
+    if (first) {   // x = 0: the residual is b
+      launch_dd_gather<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, b, rs, c->s);
+    } else {       // b - K_c x at the colour's box unknowns only, straight into the local vectors
+      int fmt = 0;
+      const void* tab = tabp<T>(H, L, &fmt);
+      launch_st_resid_gather<T>(L.g, items_l, H.nrhs, D.nsub, D.nloc, D.d_map, L.L, tab, fmt, x, b, rs, c->s);
+    }
+    cnt(); post();
+    first = false;
     coarse_gemv<T>(c, H, L, D.nloc, items_l, rs, zs);
     launch_dd_scatter<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, zs, x, c->s); cnt(); post();
   }

@@ -540,6 +540,42 @@ __global__ void __launch_bounds__(128) k_st_vupd_full(Grid g, int nrhs, const TI
   }
 }
 
+// MG-DD colour residual fused with its gather: local unknown e of sub-item bl
+// (= ((m * nsub) + s) * nrhs + r) receives (b - K_c x) at coarsest slot
+// map[s][e] of item m * nrhs + r, or 0 on padding (map -1); only the rows of
+// the colour's subdomains are evaluated.
+template <typename T, typename TT, int D, int LV>
+__global__ void __launch_bounds__(128) k_st_resid_gather(Grid g, int nrhs, int nsub, int nloc,
+                                                         const int* __restrict__ map, const TT* __restrict__ tab,
+                                                         const typename CT<T>::type* __restrict__ x,
+                                                         const typename CT<T>::type* __restrict__ b,
+                                                         typename CT<T>::type* __restrict__ out,
+                                                         const int* __restrict__ il) {
+  typedef typename CT<T>::type Cx;
+  constexpr StencilLayout L = level_layout(D, LV);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nloc) return;
+  const int bl = il ? il[blockIdx.y] : blockIdx.y;
+  const int r = bl % nrhs, s = (bl / nrhs) % nsub, m = bl / (nrhs * nsub);
+  const long long N = g.ncell;
+  const int gs = map[(long long)s * nloc + e];
+  Cx v = czero<Cx>();
+  if (gs >= 0) {
+    const int a = (int)(gs / N);
+    const long long c = gs % N;
+    const long long vo = (long long)(m * nrhs + r) * (D + 1) * N;
+    const TT* ts = tab + (long long)m * L.nslot * N;
+    int i[3];
+    cell_coords(g, c, i);
+    if (a == 0) v = st_row_ct<T, TT, D, LV, 0>(g, ts, c, i, x + vo);
+    else if (a == 1) v = st_row_ct<T, TT, D, LV, 1>(g, ts, c, i, x + vo);
+    else if (a == 2) v = st_row_ct<T, TT, D, LV, 2>(g, ts, c, i, x + vo);
+    else if constexpr (D == 3) v = st_row_ct<T, TT, D, LV, 3>(g, ts, c, i, x + vo);
+    v = csub(__ldg(b + vo + gs), v);
+  }
+  out[(long long)bl * nloc + e] = v;
+}
+
 inline dim3 grid1(long long n, int items, int bs) { return dim3((unsigned)((n + bs - 1) / bs), items, 1); }
 
 }  // namespace
@@ -669,6 +705,36 @@ __global__ void k_table_half(long long n, const double2* __restrict__ in, void* 
   if (fmt == 1) ((__half2*)out)[i] = __floats2half2_rn((float)v.x, (float)v.y);
   else ((__nv_bfloat162*)out)[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
 }
+template <typename T, typename TT>
+static void resid_gather_t(const Grid& g, int items_l, int nrhs, int nsub, int nloc, const int* map, int v,
+                           const TT* tab, const typename CT<T>::type* x, const typename CT<T>::type* b,
+                           typename CT<T>::type* out, cudaStream_t s) {
+  const dim3 gr((unsigned)((nloc + 127) / 128), sel_items(items_l));
+  if (g.d == 2) {
+    if (v == 1) k_st_resid_gather<T, TT, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+    else k_st_resid_gather<T, TT, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+  } else {
+    if (v == 1) k_st_resid_gather<T, TT, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+    else k_st_resid_gather<T, TT, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+  }
+}
+
+template <typename T>
+void launch_st_resid_gather(const Grid& g, int items_l, int nrhs, int nsub, int nloc, const int* map,
+                            const StencilLayout& L, const void* tab, int fmt, const typename CT<T>::type* x,
+                            const typename CT<T>::type* b, typename CT<T>::type* out, cudaStream_t s) {
+  const int v = layout_variant(L, g.d);
+  if constexpr (sizeof(T) == 4) {
+    if (fmt == 1)
+      return resid_gather_t<T, __half2>(g, items_l, nrhs, nsub, nloc, map, v, (const __half2*)tab, x, b, out, s);
+    if (fmt == 2)
+      return resid_gather_t<T, __nv_bfloat162>(g, items_l, nrhs, nsub, nloc, map, v, (const __nv_bfloat162*)tab, x, b,
+                                               out, s);
+  }
+  resid_gather_t<T, typename CT<T>::type>(g, items_l, nrhs, nsub, nloc, map, v, (const typename CT<T>::type*)tab, x,
+                                          b, out, s);
+}
+
 void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaStream_t s) {
   k_table_half<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out, fmt);
 }
@@ -715,6 +781,9 @@ void launch_st_vanka_full(const Grid& g, int items, int nrhs, const StencilLayou
 
 #define INST(T)                                                                                   \
   template void launch_table_cast<T>(long long, const double2*, CT<T>::type*, cudaStream_t);       \
+  template void launch_st_resid_gather<T>(const Grid&, int, int, int, int, const int*, const StencilLayout&,   \
+                                          const void*, int, const CT<T>::type*, const CT<T>::type*,          \
+                                          CT<T>::type*, cudaStream_t);                                       \
   template void launch_st_apply<T>(const Grid&, int, int, const StencilLayout&, const void*, int,   \
                                    const CT<T>::type*, const CT<T>::type*, CT<T>::type*, int, int,  \
                                    cudaStream_t);                                                   \

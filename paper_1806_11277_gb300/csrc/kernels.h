@@ -87,6 +87,13 @@ void launch_st_vanka_full(const Grid& g, int items, int nrhs, const StencilLayou
                           const typename CT<T>::type* xi, typename CT<T>::type* xo, typename CT<T>::type* rbuf,
                           int var, cudaStream_t s);
 
+// MG-DD: colour residual b - A x of a Galerkin level evaluated only at the local
+// unknowns of the listed sub-items, written as their local vectors (map as launch_dd_gather)
+template <typename T>
+void launch_st_resid_gather(const Grid& g, int items_l, int nrhs, int nsub, int nloc, const int* map,
+                            const StencilLayout& L, const void* tab, int fmt, const typename CT<T>::type* x,
+                            const typename CT<T>::type* b, typename CT<T>::type* out, cudaStream_t s);
+
 // ---- transfer -------------------------------------------------------------
 template <typename T>
 void launch_restrict(const Grid& gf, const Grid& gc, int items, const typename CT<T>::type* rf,
