@@ -132,6 +132,7 @@ struct ehs_ctx {
   double2* dd_r = nullptr;
   int nblk = 1;
   double* hpin = nullptr;    // pinned host scratch
+  double2* hstep = nullptr;  // pinned host copies of one Arnoldi step: h1 [items][12], h2 [items][12], norms
   // CUDA graphs of the preconditioner application, one per Krylov direction j
   // (the input/output pointers differ per j), captured on a private stream
   bool use_graphs = true;
@@ -892,8 +893,7 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
   A.set_b(c->hpin);
   CK(cudaMemsetAsync(c->xq, 0, nall * sizeof(float4), s));
   CK(cudaMemcpyAsync(c->rq, c->qq, nall * sizeof(float4), cudaMemcpyDeviceToDevice, s));
-  std::vector<double2> h1((size_t)items * (m + 1)), h2((size_t)items * (m + 1)), yh;
-  std::vector<double> hn(items);
+  std::vector<double2> yh;
   while (!A.all_done() && !A.maxed()) {
     A.start_cycle();
     set_active(c, A.active);
@@ -919,11 +919,13 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
       launch_mupdate_df(n, items, nv, c->Vq, c->h2q, c->wq, nullptr, nblk, 0, c->npq, s);
       launch_reduce_norm_df(items, nblk, c->npq, c->nrm, c->invq, s);
       cnt(7); post();
-      CK(cudaMemcpyAsync(h1.data(), c->hhost, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(h2.data(), c->hhost + (size_t)items * 12, (size_t)items * nv * sizeof(double2),
-                         cudaMemcpyDeviceToHost, s));
-      sync_read(c, hn.data(), c->nrm, items * sizeof(double));
-      if (!A.step(j, h1.data(), h2.data(), hn.data())) break;
+      // one round trip into pinned memory: h1, h2 (the reduce kernels' double copies) and the norms
+      double2* ph1 = c->hstep;
+      double2* ph2 = c->hstep + (size_t)items * 12;
+      double* phn = (double*)(c->hstep + (size_t)items * 24);
+      CK(cudaMemcpyAsync(ph1, c->hhost, (size_t)items * 24 * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      sync_read(c, phn, c->nrm, items * sizeof(double));
+      if (!A.step(j, ph1, ph2, phn)) break;
       set_active(c, A.active);
       SelScope sel2 = global_sel(c);
       launch_scale_df(n, items, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n, s); cnt(); post();
@@ -1107,6 +1109,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
       c->hhost = dalloc<double2>(c, (size_t)items * 24);
     }
     CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));
+    CK(cudaMallocHost((void**)&c->hstep, (size_t)items * 25 * sizeof(double2)));
     CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     c->pg.assign(m, nullptr);
     c->pg_nodes.assign(m, 0);
@@ -1137,6 +1140,7 @@ ehs_status ehs_destroy(ehs_ctx* c) {
   for (void* p : c->allocs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
+  if (c->hstep) cudaFreeHost(c->hstep);
   delete c;
   return EHS_OK;
 }
