@@ -837,8 +837,7 @@ ehs_status fgmres_c128(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info*
   A.set_b(c->hpin);
   CK(cudaMemsetAsync(u, 0, (size_t)items * n * sizeof(double2), s));
   CK(cudaMemcpyAsync(c->rd, q, (size_t)items * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  std::vector<double2> h1((size_t)items * (m + 1)), h2((size_t)items * (m + 1)), yh;
-  std::vector<double> hn(items);
+  std::vector<double2> yh;
   while (!A.all_done() && !A.maxed()) {
     CK(cudaMemcpyAsync(c->nrm, A.beta.data(), items * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_scale_inv(n, items, c->rd, c->nrm, c->V, s); cnt(); post();
@@ -859,10 +858,13 @@ ehs_status fgmres_c128(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info*
       launch_mupdate(n, items, nv, c->V, c->y, c->w, nullptr, nblk, 0, c->npart, s);
       launch_reduce_norm(items, nblk, c->npart, c->nrm, s);
       cnt(7); post();
-      CK(cudaMemcpyAsync(h1.data(), c->hd, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(h2.data(), c->y, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      sync_read(c, hn.data(), c->nrm, items * sizeof(double));
-      if (!A.step(j, h1.data(), h2.data(), hn.data())) break;
+      double2* ph1 = c->hstep;                         // pinned: no pageable copies
+      double2* ph2 = c->hstep + (size_t)items * 12;
+      double* phn = (double*)(c->hstep + (size_t)items * 24);
+      CK(cudaMemcpyAsync(ph1, c->hd, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(ph2, c->y, (size_t)items * nv * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      sync_read(c, phn, c->nrm, items * sizeof(double));
+      if (!A.step(j, ph1, ph2, phn)) break;
       launch_scale_inv(n, items, c->w, c->nrm, c->V + (size_t)(j + 1) * items * n, s); cnt(); post();
     }
     A.solve_y(yh);
