@@ -3,9 +3,11 @@
 Workload (one step): four 512 x 512 heterogeneous media (smooth Gaussian
 random fields, correlation 20 cells, Vp in [1.5, 4.5], rho in [1, 2.5]) with
 Poisson ratios 0.25 / 0.4 / 0.45 / 0.49, 8 points per shortest S-wavelength,
-20-cell absorbing layer, one x-force each; a complex64 multigrid V-cycle
-preconditions an FP64 FGMRES(10) to 1e-6 relative residual.  The four media
-are one batched context, so one step is four solves.
+20-cell absorbing layer, one x-force each; an MG-DD preconditioner (a
+complex64 3-level V-cycle whose coarsest grid is solved by one DD sweep over
+8 x 8 subdomains) inside an FP64-class (double-float) FGMRES(10) to 1e-6
+relative residual.  The four media are one batched context, so one step is
+four solves.
 
 Timing: W warm-up steps, then K steps timed with CUDA events on the solver's
 stream, L2 flushed (a 512 MiB write) between steps outside the events;
@@ -65,8 +67,8 @@ def default_kw():
 
 
 # Roofline kernel of the default line: the MG-DD coarsest local products (k_dense_apply_v,
-# 35% of the solve in the ncu launch list); per launch (one colour) the live n_s x n_s
-# entries of every subdomain inverse of the colour (4 B each, FP16 pairs) + r and z
+# the largest share of the solve, 26% of the ncu launch list); per launch (one colour) the
+# live n_s x n_s entries of every subdomain inverse of the colour (4 B each, FP16 pairs) + r and z
 ROOF = "coarse"
 ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 16 subdomain inverses "
                "x 4 media)")
@@ -516,6 +518,21 @@ def run_gpu(args):
             "value": cpu_val, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
             "sample": (f"{args.cpu_iters} oracle FGMRES iterations on each of the 4 media; "
                        f"seconds/iteration x mean iterations per solve ({mean_iters:.1f}, {src})")}
+    if rank == 0 and world == 1 and not args.no_cpu and args.config == "c1":
+        # the 64x64 case is small enough for whole oracle solves (3-level V(1,1), alpha 0.2)
+        from oracle import krylov, multigrid as mg, operators as op
+        med = meds[0]
+        parts = op.parts_for(med)
+        K = op.assemble_mixed(parts)
+        H = mg.Hierarchy(op.assemble_mixed(parts, kw["alpha"]), med.shape, kw["levels"], w=list(kw["w"]))
+        qo = op.slots_to_dofs(q_host[0], med.shape)
+        t = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+        cpu_val = reps / (time.perf_counter() - t)
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": f"{reps} whole oracle solves of the 64x64 case (hierarchy built beforehand)"}
     S.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
