@@ -166,6 +166,20 @@ def rhs(meds, nrhs=1):
 
 OTHER["c4b"] = dict(OTHER["c4"], workload=OTHER["c4"]["workload"] + "; Galerkin tables stored as BF16 pairs",
                     kw=dict(OTHER["c4"]["kw"], coef_half=2))
+# DD-MG-DD (Sec. 4, the paper's 3D method): the same top-level DD, 4-level V(1,1) cycles per subdomain
+# whose coarsest grids are themselves split 2x2x1 (overlap 2, FP16 local inverses), alpha 0.5
+_DDMGDD = dict(levels=4, alpha=0.5, w=[0.5, 0.5, 0.2], coarse_dd=(2, 2, 1), coarse_dd_overlap=2, coarse_fmt=2,
+               coef_half=1)
+OTHER["c3dd"] = dict(OTHER["c3"], workload=OTHER["c3"]["workload"].replace(
+    "with one complex64 5-level V(1,1) cycle per subdomain (damping 0.5/0.5/0.2/0.2)",
+    "with one complex64 4-level V(1,1) cycle per subdomain (damping 0.5/0.5/0.2, alpha 0.5) whose coarsest "
+    "grid is split 2x2x1 (DD-MG-DD, overlap 2, FP16 local inverses and tables)"),
+    kw=dict(OTHER["c3"]["kw"], **_DDMGDD))
+OTHER["c4dd"] = dict(OTHER["c4"], workload=OTHER["c4"]["workload"].replace(
+    "one complex64 5-level V(1,1) per subdomain",
+    "one complex64 4-level V(1,1) per subdomain (alpha 0.5) whose coarsest grid is split 2x2x1 (DD-MG-DD, "
+    "overlap 2, FP16 local inverses and tables)"),
+    kw=dict(OTHER["c4"]["kw"], **_DDMGDD))
 OTHER["c4"]["kernel"] = OTHER["c4b"]["kernel"] = OTHER["c3"]["kernel"]
 
 
