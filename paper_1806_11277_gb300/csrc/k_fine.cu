@@ -250,6 +250,141 @@ __global__ void k_fine_vanka(Grid g, int nrhs, const Coef4<T>* __restrict__ cf, 
   }
 }
 
+// The same economic half-sweep for 2D complex64, staged through shared memory:
+// a CTA owns a VT_X x VT_Y tile of cells of one item, loads u_0, u_1, p and
+// the coefficients of the tile plus a 2-cell halo once (coalesced), and each
+// thread relaxes the colour cell of one x-pair from shared memory.  Outside
+// the grid the displacements read 0 (the Dirichlet slots and the implicit high
+// boundary faces) and the coefficients repeat the nearest cell (the clamped
+// edge averages), so the rows need no per-load bounds checks; the arithmetic
+// is that of k_fine_vanka term by term.
+constexpr int VT_X = 32, VT_Y = 8, VT_H = 2;
+constexpr int VS_X = VT_X + 2 * VT_H, VS_Y = VT_Y + 2 * VT_H;
+
+// asynchronous global -> shared copies (cp.async): all of a thread's staging
+// loads are in flight at once; nbytes = 0 fills the destination with zeros
+// (the source address is then not read, but is kept valid all the same)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int nbytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(VT_X * VT_Y / 2) k_fine_vanka_tile(Grid g, int nrhs, const Coef4<float>* __restrict__ cf,
+                                                                     FineP<float> P, float wu, float wp, int colour,
+                                                                     const float2* __restrict__ b,
+                                                                     const float2* __restrict__ xi,
+                                                                     float2* __restrict__ xo, const int* __restrict__ il) {
+  __shared__ __align__(16) float2 xs[3][VS_Y][VS_X];
+  __shared__ __align__(16) float4 cs[VS_Y][VS_X];
+  const int item = il ? il[blockIdx.z] : blockIdx.z;
+  const long long N = g.ncell;
+  const int nx = g.n[0], ny = g.n[1];
+  const long long vo = (long long)item * 3 * N;
+  const float4* cfs = reinterpret_cast<const float4*>(cf + (long long)(item / nrhs) * N);
+  const float2* x = xi + vo;
+  const int x0 = blockIdx.x * VT_X - VT_H, y0 = blockIdx.y * VT_Y - VT_H;
+  for (int idx = threadIdx.x; idx < VS_X * VS_Y; idx += blockDim.x) {
+    const int lx = idx % VS_X, ly = idx / VS_X;
+    const int gx = x0 + lx, gy = y0 + ly;
+    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const int cx = min(max(gx, 0), nx - 1), cy = min(max(gy, 0), ny - 1);
+    const long long gc = (long long)cy * nx + cx;                  // a valid address in every case
+    cp_async8(&xs[0][ly][lx], x + gc, (in && gx >= 1) ? 8 : 0);    // u_0 slot 0 is a boundary face
+    cp_async8(&xs[1][ly][lx], x + N + gc, (in && gy >= 1) ? 8 : 0);  // u_1 slot 0 likewise
+    cp_async8(&xs[2][ly][lx], x + 2 * N + gc, in ? 8 : 0);
+    cp_async16(&cs[ly][lx], cfs + gc);                              // clamped: the edge averages' rule
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int t = threadIdx.x;
+  int lx = 2 * (t % (VT_X / 2)), ly = t / (VT_X / 2);
+  int i0 = blockIdx.x * VT_X + lx, i1 = blockIdx.y * VT_Y + ly;
+  if (((i0 + i1) & 1) != colour) { ++lx; ++i0; }
+  const int sx = lx + VT_H, sy = ly + VT_H;                        // the colour cell in shared memory
+  const int ox = ((lx & 1) ? lx - 1 : lx + 1) + VT_H;              // the other cell of the pair
+  const long long c = (long long)i1 * nx + i0;
+  const long long co = (long long)i1 * nx + (((i0 & 1) ? i0 - 1 : i0 + 1));
+  const float2* bb = b + vo;
+  float2* xout = xo + vo;
+  xout[2 * N + co] = xs[2][sy][ox];
+  const float4 cc = cs[sy][sx];
+  // row of u_k at the face whose high cell is (ax, ay) (smem coordinates), diagonal in *dg
+  auto row_u = [&](int k, int ax, int ay, float2* dg) -> float2 {
+    const int ex = k == 0, ey = k == 1;
+    const float4 c0 = cs[ay][ax], c1 = cs[ay - ey][ax - ex];
+    const float2 xc = xs[k][ay][ax];
+    const float2 xp = xs[k][ay + ey][ax + ex], xm = xs[k][ay - ey][ax - ex];
+    float wsum = c0.x + c1.x;
+    float2 nb = cadd(cscale(xp, c0.x), cscale(xm, c1.x));
+    const int jx = 1 - ex, jy = 1 - ey;                             // the tangential direction
+    const float base = c0.x + c1.x;
+    const float wpl = 0.25f * (base + cs[ay + jy][ax + jx].x + cs[ay + jy - ey][ax + jx - ex].x);
+    const float wmi = 0.25f * (base + cs[ay - jy][ax - jx].x + cs[ay - jy - ey][ax - jx - ex].x);
+    wsum += wpl + wmi;
+    nb = cfma(make_float2(wpl, 0.f), xs[k][ay + jy][ax + jx], nb);
+    nb = cfma(make_float2(wmi, 0.f), xs[k][ay - jy][ax - jx], nb);
+    const float rf = 0.5f * (c0.z + c1.z), gf = 0.5f * (c0.w + c1.w);
+    const float2 d = make_float2(wsum * P.h2inv - rf, gf + P.alpha * rf);
+    *dg = d;
+    float2 y = csub(cmul(d, xc), cscale(nb, P.h2inv));
+    return cadd(y, cscale(csub(xs[2][ay][ax], xs[2][ay - ey][ax - ex]), P.hinv));
+  };
+  const int ic[2] = {i0, i1}, nn[2] = {nx, ny};
+  float2 r[5], dg[4], g_[4];
+  bool ok[4];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const long long sk = k == 0 ? 1 : nx;
+    ok[k] = ic[k] >= 1;
+    if (ok[k]) r[k] = csub(__ldg(bb + (long long)k * N + c), row_u(k, sx, sy, &dg[k]));
+    else { r[k] = make_float2(0.f, 0.f); dg[k] = make_float2(1.f, 0.f); }
+    g_[k] = make_float2(P.hinv, 0.f);
+    ok[2 + k] = ic[k] + 1 < nn[k];
+    if (ok[2 + k]) r[2 + k] = csub(__ldg(bb + (long long)k * N + c + sk), row_u(k, sx + (k == 0), sy + (k == 1), &dg[2 + k]));
+    else { r[2 + k] = make_float2(0.f, 0.f); dg[2 + k] = make_float2(1.f, 0.f); }
+    g_[2 + k] = make_float2(-P.hinv, 0.f);
+  }
+  {   // pressure row: -kap p + (div u) / h
+    float2 y = cscale(xs[2][sy][sx], -cc.y);
+    float2 sdiv = make_float2(0.f, 0.f);
+    sdiv = cadd(sdiv, xs[0][sy][sx]);
+    sdiv = csub(sdiv, xs[0][sy][sx + 1]);
+    sdiv = cadd(sdiv, xs[1][sy][sx]);
+    sdiv = csub(sdiv, xs[1][sy + 1][sx]);
+    r[4] = csub(__ldg(bb + 2 * N + c), cadd(y, cscale(sdiv, P.hinv)));
+  }
+  float2 sch = make_float2(-cc.y, 0.f);
+  float2 rp = r[4];
+  float2 dinv[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (!ok[a]) continue;
+    dinv[a] = cinv(dg[a]);
+    const float2 gd = cmul(g_[a], dinv[a]);
+    sch = csub(sch, cmul(gd, g_[a]));
+    rp = csub(rp, cmul(gd, r[a]));
+  }
+  const float2 dp = cmul(rp, cinv(sch));
+  xout[2 * N + c] = cfma(make_float2(wp, 0.f), dp, xs[2][sy][sx]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (!ok[a]) continue;
+    const int k = a % 2;
+    const long long idx = (long long)k * N + c + (a >= 2 ? (k == 0 ? 1 : nx) : 0);
+    const float2 xv = xs[k][sy + (a >= 2 && k == 1)][sx + (a >= 2 && k == 0)];
+    const float2 du = cmul(csub(r[a], cmul(g_[a], dp)), dinv[a]);
+    xout[idx] = cfma(make_float2(wu, 0.f), du, xv);
+  }
+}
+
 __device__ __forceinline__ double abl_ramp(const Grid& g, const int i[3], int L) {
   if (L <= 0) return 0.0;
   double r = 0.0;
@@ -432,6 +567,13 @@ void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
                        const typename CT<T>::type* b, const typename CT<T>::type* xi,
                        typename CT<T>::type* xo, cudaStream_t s, int full) {
   const FineP<T> P = mkP<T>(h, alpha);
+  if constexpr (sizeof(T) == 4) {
+    if (g.d == 2 && !full && g.n[0] % VT_X == 0 && g.n[1] % VT_Y == 0) {   // shared-memory tiles
+      const dim3 gt(g.n[0] / VT_X, g.n[1] / VT_Y, sel_items(items));
+      k_fine_vanka_tile<<<gt, VT_X * VT_Y / 2, 0, s>>>(g, nrhs, cf, P, wu, wp, colour, b, xi, xo, g_sel.list);
+      return;
+    }
+  }
   const long long np = g.ncell / 2;
   const dim3 gr((unsigned)((np + 127) / 128), sel_items(items));
   if (g.d == 2) {
