@@ -166,6 +166,20 @@ def rhs(meds, nrhs=1):
 
 OTHER["c4b"] = dict(OTHER["c4"], workload=OTHER["c4"]["workload"] + "; Galerkin tables stored as BF16 pairs",
                     kw=dict(OTHER["c4"]["kw"], coef_half=2))
+# adjoint-state gradient (FWI) workload: 256x256, 16 sources, 200 receivers; one step = forward
+# solves of the 16 sources, receiver residual against data of the blob-perturbed true model,
+# adjoint solves, fused gradient (solves/s counts forward and adjoint solves)
+OTHER["c5"] = dict(
+    workload=("2D adjoint-state gradient: 256x256 random medium (Poisson 0.45, GRF corr 20), 16 x-forces and "
+              "200 u_x receivers on the line y = ABL+2, data from the true model (+5% Gaussian blob of "
+              "radius 20 cells); one step = 16 forward solves + receiver residual + 16 adjoint solves + fused "
+              "dJ/d(lambda, mu, rho); MG-DD preconditioner (3-level complex64 V(1,1), alpha 0.25, 64x64 "
+              "coarsest grid split 4x4, overlap 3, FP16 tables and local inverses), double-float FGMRES(10)"),
+    media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).fwi_2d()[0]],
+    nrhs=16, fwi=True,
+    kw=dict(nrhs=16, coarse_dd=(4, 4, 1)), roof="coarse",
+    kernel="k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 4 subdomain inverses x 16 sources)")
+
 # DD-MG-DD (Sec. 4, the paper's 3D method): the same top-level DD, 4-level V(1,1) cycles per subdomain
 # whose coarsest grids are themselves split 2x2x1 (overlap 2, FP16 local inverses), alpha 0.5
 _DDMGDD = dict(levels=4, alpha=0.5, w=[0.5, 0.5, 0.2], coarse_dd=(2, 2, 1), coarse_dd_overlap=2, coarse_fmt=2,
@@ -347,6 +361,9 @@ def run_gpu(args):
     if cfg is not None:
         kw.update(cfg["kw"])
     nsolve = len(meds) * (1 if cfg is None else cfg.get("nrhs", 1))
+    fwi = cfg is not None and cfg.get("fwi", False)
+    if fwi:
+        nsolve *= 2                       # forward and adjoint solves per step
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         S = ehs.solver_for(meds, stream=stream.cuda_stream, **kw)
@@ -444,6 +461,31 @@ def run_gpu(args):
     def step():
         return S.fgmres_solve(qd, ud)
 
+    if fwi:
+        # observed data: the same sources solved in the true (blob-perturbed) model, before timing
+        from paper_1806_11277_gb300 import synth
+        _, true_med, (ry, rx) = synth.fwi_2d()
+        with torch.cuda.stream(stream):
+            St = ehs.solver_for([true_med], stream=stream.cuda_stream, **kw)
+        dobs = torch.zeros_like(qd)
+        St.fgmres_solve(qd, dobs)
+        St.close()
+        ryd = torch.as_tensor(ry, device=dev)
+        rxd = torch.as_tensor(rx, device=dev)
+        d_rec = dobs[:, 0, ryd, rxd].clone()
+        gsrc = torch.zeros_like(qd)
+        wd = torch.zeros_like(qd)
+        grads = [torch.empty((len(meds),) + tuple(meds[0].shape), dtype=torch.float64, device=dev) for _ in range(3)]
+
+        def step():
+            with torch.cuda.stream(stream):
+                info_f = S.fgmres_solve(qd, ud)
+                # J = 1/2 sum |u_x(receivers) - d|^2: the adjoint source is the receiver residual
+                gsrc[:, 0, ryd, rxd] = ud[:, 0, ryd, rxd] - d_rec
+                S.adjoint_solve(gsrc, wd)
+                S.gradient(ud, wd, grads)
+            return info_f
+
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize()
@@ -483,11 +525,25 @@ def run_gpu(args):
     q_pin = torch.from_numpy(q_host).pin_memory().numpy()
     u_pin = torch.zeros(q_host.shape, dtype=torch.complex128).pin_memory().numpy()
     e2e_t = []
+    h2d, d2h = int(q_host.nbytes), int(q_host.nbytes)
+    if fwi:
+        q_src = torch.from_numpy(q_host).pin_memory()
+        g_host = [torch.empty(g.shape, dtype=g.dtype).pin_memory() for g in grads]
+        d2h = int(sum(g.numel() * 8 for g in grads))
     for _ in range(max(1, min(args.steps, 3))):
         flush.fill_(1)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        S.fgmres_solve(q_pin, u_pin)
+        if fwi:    # sources in from pinned host memory, gradient back out
+            with torch.cuda.stream(stream):
+                qd.copy_(q_src, non_blocking=True)
+            step()
+            with torch.cuda.stream(stream):
+                for gh, g in zip(g_host, grads):
+                    gh.copy_(g, non_blocking=True)
+            stream.synchronize()
+        else:
+            S.fgmres_solve(q_pin, u_pin)
         e2e_t.append(time.perf_counter() - t)
     e2e_val = nsolve * world / (sum(e2e_t) / len(e2e_t))
 
@@ -515,7 +571,7 @@ def run_gpu(args):
         "iters": its, "relres": relres, "setup_s": setup_s,
         "gridpoints_x_iters_per_s": float(np.prod(meds[0].shape) * sum(its) * args.steps * world / total),
         "e2e": {"value": e2e_val, "unit": "solves/s",
-                "h2d_bytes_per_step": int(q_host.nbytes), "d2h_bytes_per_step": int(q_host.nbytes)},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": ROOF_KERNEL if cfg is None else cfg["kernel"],
                      "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -114,6 +114,28 @@ def random_2d(n=512, sigma=0.25, seed=0, corr=20.0, ppw=8.0, abl=20, h=1.0,
     return Medium(lam, mu, rho, omega, h, abl, src, name=f"rand{n}_s{sigma}_seed{seed}")
 
 
+def fwi_2d(n=256, sigma=0.45, seed=0, nsrc=16, nrec=200, blob=0.05, radius=20.0, corr=20.0, ppw=8.0, abl=20):
+    """Adjoint-state gradient workload: a base medium (``random_2d``) with
+    ``nsrc`` x-forces on the line y = abl + 2, x evenly spaced over the
+    interior; the true medium scales the wave speeds by (1 + blob * b), b a
+    Gaussian bump of ``radius`` cells at the centre (lambda and mu scale by
+    (1 + blob * b)^2, rho unchanged); ``nrec`` receivers (u_x faces) on the same
+    line.  Returns (base, true, receivers) with receivers as (y, x) index
+    arrays."""
+    base = random_2d(n=n, sigma=sigma, seed=seed, corr=corr, ppw=ppw, abl=abl)
+    lo, hi = abl + 2, n - abl - 2
+    xs = np.linspace(lo, hi, nsrc).round().astype(int)
+    base.sources = [(0, (abl + 2, int(x))) for x in xs]
+    yy, xx = np.indices(base.shape)
+    bump = np.exp(-((yy - n / 2) ** 2 + (xx - n / 2) ** 2) / (2.0 * radius ** 2))
+    f = (1.0 + blob * bump) ** 2
+    true = Medium(base.lam * f, base.mu * f, base.rho.copy(), base.omega, base.h, base.abl_cells,
+                  list(base.sources), name=base.name + "_true")
+    rx = np.linspace(lo, hi, nrec).round().astype(int)
+    ry = np.full(nrec, abl + 2)
+    return base, true, (ry, rx)
+
+
 def layered_3d(n=128, seed=0, corr=10.0, ppw=8.0, abl=16, h=1.0, nlayers=5,
                sigma_range=(0.25, 0.45), pert=0.1, nsrc=1):
     """3D layered medium: 5 horizontal layers in z with Vp 1.5 .. 4.5, each
