@@ -177,6 +177,13 @@ class Solver:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def level_shape(self, level):
         n = (C.c_int * 3)()
         self._check(self.lib.ehs_level_dims(self.ctx, level, C.byref(n)))
