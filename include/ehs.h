@@ -160,12 +160,12 @@ ehs_status ehs_vcycle(ehs_ctx* ctx, int prec, const void* b, void* x);
    the last level).  MG contexts only (EHS_ERR_ARG otherwise). */
 ehs_status ehs_coarse_solve(ehs_ctx* ctx, int prec, const void* b, void* x);
 /* Shape of the coarsest local solves: nsub subdomains (1 for the exact solve), padded local size
-   nloc (local vectors are [items][nsub][nloc]), and, if sizes is not NULL, the live unknowns of
+   nloc (local vectors are [nmedia][nsub][nrhs][nloc]), and, if sizes is not NULL, the live unknowns of
    each subdomain (host array of nsub ints).  MG contexts only. */
 ehs_status ehs_coarse_dims(const ehs_ctx* ctx, int* nsub, int* nloc, int* sizes);
 /* One launch of the coarsest local products z_loc = A_s^{-1} r_loc for every subdomain s of
    colour `colour` (0 .. 2^d - 1; the exact solve has colour 0 only), i.e. step 2 of Algorithm DD
-   on the coarsest grid with the inverses formed at setup.  r_loc, z_loc: device [items][nsub][nloc]
+   on the coarsest grid with the inverses formed at setup.  r_loc, z_loc: device [nmedia][nsub][nrhs][nloc]
    complex of prec; entries of other colours' subdomains and of padding rows are left unspecified.
    The complex64 form reads the inverses in opts.coarse_fmt storage. */
 ehs_status ehs_coarse_local_apply(ehs_ctx* ctx, int prec, int colour, const void* r_loc, void* z_loc);

@@ -647,3 +647,50 @@ def test_dd_mg_dd_3d_fgmres_matches_oracle():
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
     assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+
+
+@pytest.mark.parametrize("fmt", [1, 2])
+def test_mgdd_multi_rhs_local_products(fmt):
+    """Five sources per medium share each MG-DD subdomain inverse: every
+    source's local solve (local vectors in [nmedia][nsub][nrhs][nloc] order)
+    equals the dense solve of its subdomain matrix, and FGMRES keeps the
+    oracle's iteration counts (+-1) and solutions for every source."""
+    ehs = _ehs()
+    meds = _media_2d(64, 1)
+    nrhs = 5
+    S = ehs.solver_for(meds, levels=3, alpha=0.4, nrhs=nrhs, coarse_dd=(2, 2, 1), coarse_dd_overlap=2,
+                       coarse_fmt=fmt)
+    ns, nloc, sizes = S.coarse_dims()
+    rng = np.random.default_rng(8)
+    shp = (1, ns, nrhs, nloc)                  # local vectors: [nmedia][nsub][nrhs][nloc]
+    rl = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    for s_, n in enumerate(sizes):
+        rl[:, s_, :, n:] = 0
+    rld = torch.from_numpy(rl).to("cuda", torch.complex64)
+    H = mg.Hierarchy(_oracle_parts(meds[0], 0.4), meds[0].shape, 3, w=[0.75, 0.5], coarse_dd=((2, 2), 2))
+    Kc = H.K[-1].tocsc()
+    tol = 2e-5 if fmt == 1 else 3e-3
+    for col in range(4):
+        zd = torch.zeros_like(rld)
+        S.coarse_local_apply(col, rld, zd, prec=ehs.EHS_C64)
+        z = zd.cpu().numpy()
+        for p_, (c_, idx, _) in enumerate(H.cdd.subs):
+            if c_ != col:
+                continue
+            ix, iy = divmod(p_, 2)
+            s_ = iy * 2 + ix
+            A = Kc[idx][:, idx].toarray()
+            for it in range(nrhs):
+                ze = np.linalg.solve(A, rl[0, s_, it, :idx.size])
+                err = np.linalg.norm(z[0, s_, it, :idx.size] - ze) / np.linalg.norm(ze)
+                assert err <= tol, (col, it, s_, err)
+    S.close()
+    q, u, info = _solve_both(meds, 3, ehs.EHS_C64, nrhs=nrhs, alpha=0.4, coarse_dd=(2, 2, 1),
+                             coarse_dd_overlap=2, coarse_fmt=fmt)
+    K = _oracle_parts(meds[0])
+    for it in range(nrhs):
+        qo = op.slots_to_dofs(q[it], meds[0].shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+        ug = op.slots_to_dofs(u[it], meds[0].shape)
+        assert info[it]["converged"] and abs(info[it]["iters"] - io["iters"]) <= 1, (it, info[it], io["iters"])
+        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
