@@ -28,3 +28,19 @@ def test_bench_configs_are_complete():
         assert cfg is not None, name
         assert {"workload", "media", "kw", "kernel"} <= set(cfg), name
         assert cfg.get("roof") == "coarse" or "rows_l1_bytes" in cfg, name
+
+
+def test_fwi_workload_generator():
+    """The gradient line's inputs: 16 x-forces and 200 distinct receivers on the
+    line y = ABL + 2 inside the interior; the true model scales lambda and mu
+    by (1 + 0.05 b)^2 with b a unit Gaussian bump, rho unchanged."""
+    import numpy as np
+    from paper_1806_11277_gb300 import synth
+    base, true, (ry, rx) = synth.fwi_2d()
+    n, abl = base.shape[0], base.abl_cells
+    assert len(base.sources) == 16 and all(k == 0 and idx[0] == abl + 2 for k, idx in base.sources)
+    assert len(set(rx.tolist())) == 200 and (ry == abl + 2).all()
+    assert rx.min() >= abl and rx.max() < n - abl
+    f = true.lam / base.lam
+    assert np.allclose(true.mu / base.mu, f) and np.array_equal(true.rho, base.rho)
+    assert 1.0 <= f.min() and abs(f.max() - 1.05 ** 2) < 1e-3
