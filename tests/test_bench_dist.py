@@ -45,3 +45,33 @@ def test_reference_arm_only_rank0_prints(tmp_path, monkeypatch, capsys):
         steps, warmup, ref_iters, gpus = 1, 0, 1, 2
     assert bench.run_reference(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_contract(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the keys the
+    benchmark contract asks for (on small 64x64 media so that the oracle runs
+    in seconds; the solver options are the default line's, with a coarsest
+    split that fits the smaller grid)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1806_11277_gb300 import synth
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(bench, "media", lambda seed=0: [synth.random_2d(n=64, sigma=s, seed=seed, corr=6.0, abl=8)
+                                                       for s in bench.SIGMAS])
+    monkeypatch.setattr(bench, "COARSE_DD", (2, 2, 1))
+    monkeypatch.setattr(bench, "COARSE_OVERLAP", 1)
+    monkeypatch.setattr(bench, "_ORACLE_CACHE", {})
+
+    class A:
+        steps, warmup, ref_iters, gpus = 2, 1, 2, 1
+    assert bench.run_reference(A()) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == "solves/s"
+    assert j["higher_is_better"] is True and j["value"] > 0 and j["steps"] == 2 and j["warmup"] == 1
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == j["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert j["e2e"] == {"value": j["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert j["config"]["workload"] == bench.WORKLOAD
