@@ -336,3 +336,21 @@ def test_mg_dd_iterations_close_to_mg_exact():
         assert info["converged"]
         its.append(info["iters"])
     assert its[1] <= its[0] + 3, its
+
+
+def test_coarse_dd_3d_exact_and_last_colour():
+    """3D coarse DD: one subdomain is the exact solve; with a 2x2x2 split (8
+    colours) the last colour's box unknowns carry no residual after the sweep."""
+    med = synth.layered_3d(n=16, seed=2, corr=3.0, abl=3)
+    H = mg.Hierarchy(op.assemble_mixed(op.parts_for(med), 0.5), med.shape, 2)
+    K, shape = H.K[-1], H.shapes[-1]
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(K.shape[0]) + 1j * rng.standard_normal(K.shape[0])
+    xe = spla.spsolve(K.tocsc(), b)
+    x1 = mg.CoarseDD(K, shape, (1, 1, 1), 1).solve(b)
+    assert np.linalg.norm(x1 - xe) <= 1e-12 * np.linalg.norm(xe)
+    cdd = mg.CoarseDD(K, shape, (2, 2, 2), 1)
+    assert cdd.colours == list(range(8))
+    r = b - K @ cdd.solve(b)
+    last = [idx for c, idx, _ in cdd.subs if c == 7]
+    assert len(last) == 1 and np.abs(r[last[0]]).max() <= 1e-10 * np.abs(b).max()
