@@ -61,3 +61,30 @@ def test_create_rejects_bad_arguments_before_any_launch(lib_path):
     st = lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx))
     assert st == 1 and not ctx.value
     assert b"dim" in lib.ehs_last_error(None)
+
+
+@pytest.mark.parametrize("field,value,msg", [("levels", 1, "levels"), ("restart", 20, "restart"),
+                                             ("cycle", 3, "cycle"), ("coef_half", 3, "coef_half"),
+                                             ("vanka_full", 2, "vanka_full"), ("coarse_fmt", 7, "coarse_fmt"),
+                                             ("prec", 5, "prec"), ("tol", 0.0, "tol")])
+def test_create_rejects_bad_options_before_any_device_work(lib_path, field, value, msg):
+    """ehs_create validates its arguments on the host first: a bad option is
+    EHS_ERR_ARG with a message, whether or not a GPU is present."""
+    import ctypes as C
+    import numpy as np
+    from paper_1806_11277_gb300 import ehs
+    lib = ehs.load(lib_path)
+    n = 32
+    lam = np.full(n * n, 2.0)
+    mu = np.ones(n * n)
+    rho = np.ones(n * n)
+    p = ehs.Problem()
+    p.dim, p.h, p.omega, p.nmedia = 2, 1.0, 0.6, 1
+    p.n[0], p.n[1], p.n[2] = n, n, 1
+    p.lam, p.mu, p.rho = lam.ctypes.data, mu.ctypes.data, rho.ctypes.data
+    p.abl_cells, p.abl_max, p.gamma_add = 4, 1.0, 0.03
+    o = ehs.default_opts(**{field: value})
+    ctx = C.c_void_p()
+    st = lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx))
+    assert st == 1 and not ctx.value
+    assert msg in lib.ehs_last_error(None).decode()
