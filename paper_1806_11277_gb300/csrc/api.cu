@@ -608,6 +608,17 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (O->coarse_fmt < 0 || O->coarse_fmt > 3) throw ArgError("coarse_fmt must be 0..3");
   for (int k = 0; k < 3; ++k)
     if (O->coarse_dd[k] < 0) throw ArgError("coarse_dd must be >= 0");
+  // MG-DD on the global hierarchy: the coarsest grid is known here (DD contexts split the
+  // coarsest grids of their subdomain hierarchies, checked when those are built)
+  if (O->precond == EHS_PRECOND_MG && (O->coarse_dd[0] > 1 || O->coarse_dd[1] > 1 || (P->dim == 3 && O->coarse_dd[2] > 1))) {
+    if (O->coarse_dd_overlap < 1) throw ArgError("coarse_dd_overlap must be >= 1");
+    for (int k = 0; k < P->dim; ++k) {
+      const int nc = P->n[k] >> (O->levels - 1), ns = std::max(O->coarse_dd[k], 1);
+      if (ns > nc) throw ArgError("coarse_dd split larger than the coarsest grid");
+      if (ns > 1 && 2 * O->coarse_dd_overlap > nc / ns)
+        throw ArgError("coarse_dd_overlap larger than half a coarsest-grid core");
+    }
+  }
 }
 
 void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* rho, long long n) {

@@ -88,3 +88,25 @@ def test_create_rejects_bad_options_before_any_device_work(lib_path, field, valu
     st = lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx))
     assert st == 1 and not ctx.value
     assert msg in lib.ehs_last_error(None).decode()
+
+
+@pytest.mark.parametrize("split,overlap,msg", [((9, 9, 1), 1, "split larger"), ((4, 4, 1), 2, "overlap larger"),
+                                               ((2, 2, 1), 0, "overlap must")])
+def test_create_rejects_bad_coarse_split_on_host(lib_path, split, overlap, msg):
+    """MG-DD options are checked against the coarsest grid (32x32 / 2^2 = 8x8
+    here) before any device work."""
+    import ctypes as C
+    import numpy as np
+    from paper_1806_11277_gb300 import ehs
+    lib = ehs.load(lib_path)
+    n = 32
+    arrs = [np.full(n * n, 2.0), np.ones(n * n), np.ones(n * n)]
+    p = ehs.Problem()
+    p.dim, p.h, p.omega, p.nmedia = 2, 1.0, 0.6, 1
+    p.n[0], p.n[1], p.n[2] = n, n, 1
+    p.lam, p.mu, p.rho = (a.ctypes.data for a in arrs)
+    p.abl_cells, p.abl_max, p.gamma_add = 4, 1.0, 0.03
+    o = ehs.default_opts(levels=3, coarse_dd=split, coarse_dd_overlap=overlap)
+    ctx = C.c_void_p()
+    assert lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx)) == 1
+    assert msg in lib.ehs_last_error(None).decode()
