@@ -6,7 +6,11 @@
 * Vanka: the economic block has the sparsity the paper counts (13 nonzeros
   in 2D, 19 in 3D; Sec. 3), a full update with w = 1 zeroes the cell's block
   residual, and the LFA smoothing factors printed in Sec. 5.4 are
-  reproduced from stencil values read out of the assembled operator,
+  reproduced from stencil values read out of the assembled operator, and
+  the LFA symbol equals what a brute-force lexicographic sweep does to a
+  plane wave away from the boundaries,
+* the shift has the sign of the physical attenuation (the other sign does
+  not converge),
 * FGMRES reaches the exact (dense) solution on tiny grids,
 * DD with one subdomain and an exact local solve is the exact solve,
 * the V-cycle contracts as a stand-alone iteration and the FGMRES
@@ -354,3 +358,58 @@ def test_coarse_dd_3d_exact_and_last_colour():
     r = b - K @ cdd.solve(b)
     last = [idx for c, idx, _ in cdd.subs if c == 7]
     assert len(last) == 1 and np.abs(r[last[0]]).max() <= 1e-10 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("wu,wp", [(0.75, 0.75), (0.85, 0.65)])
+def test_lex_vanka_sweep_matches_lfa_symbol(wu, wp):
+    """Brute-force cross-check of the LFA (Sec. 5) against the oracle's own
+    relaxation: one lexicographic economic Vanka sweep with zero right-hand
+    side, applied to a plane-wave error E phi_theta on a 40 x 40 constant-
+    coefficient grid, leaves amplitudes S(theta) E at cells far from the
+    boundaries (the start-up transient of the sweep has decayed there).  The
+    symbol is built from stencil bookkeeping, the sweep from the assembled
+    sparse operator, so a wrong block, damping or update order in either one
+    fails."""
+    h, omega, gamma, lam, mu, rho = 1 / 128, 80.0, 0.2, 500.0, 1.0, 1.0
+    n = 40
+    shape = (n, n)
+    parts = op.Parts(*(np.full(shape, v) for v in (lam, mu, rho, gamma * omega)), omega, h)
+    K = op.assemble_mixed(parts)
+    lv = mg.Level(K, shape, wu, economic=True, wu=wu, wp=wp)
+    s = lfa.stencil_values(h, omega, gamma, lam, mu, rho)
+    rng = np.random.default_rng(0)
+    j, i = np.mgrid[0:n, 0:n]
+    for theta in ((2.0, 0.3), (-1.2, 2.5), (np.pi, np.pi), (0.4, 1.9)):
+        ph = lambda X, Y: np.exp(0.5j * (theta[0] * X + theta[1] * Y))    # half-cell units
+        E = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        sl = np.stack([E[0] * ph(2 * i, 2 * j + 1),          # u on the low x face
+                       E[1] * ph(2 * i + 1, 2 * j),          # v on the low y face
+                       E[2] * ph(2 * i + 1, 2 * j + 1)])     # p at the centre
+        sl[0][:, 0] = 0
+        sl[1][0, :] = 0
+        x = op.slots_to_dofs(sl, shape)
+        a = op.dofs_to_slots(lv.relax_lex(np.zeros_like(x), x), shape)
+        want = lfa.symbol(theta, s, wu, wu, wp) @ E
+        for cj, ci in ((20, 20), (26, 18), (28, 28)):
+            got = np.array([a[0][cj, ci] / ph(2 * ci, 2 * cj + 1), a[1][cj, ci] / ph(2 * ci + 1, 2 * cj),
+                            a[2][cj, ci] / ph(2 * ci + 1, 2 * cj + 1)])
+            scale = np.maximum(np.abs(want), np.abs(E))      # p is on another scale than u, v
+            assert np.all(np.abs(got - want) <= 1e-4 * scale), (theta, (cj, ci), got, want)
+
+
+def test_shift_sign_same_as_attenuation_converges():
+    """Sign of the shift (eq. shift against the physical mass of Sec. 2.1):
+    with the artificial attenuation added with the sign of the physical one
+    the MG-preconditioned FGMRES converges quickly; with the opposite sign it
+    does not converge within four times as many iterations."""
+    med = synth.random_2d(n=64, sigma=0.4, seed=0, corr=8.0, abl=10)
+    parts = op.parts_for(med)
+    K = op.assemble_mixed(parts)
+    q = op.slots_to_dofs(synth.point_rhs(med.shape, med.sources)[0], med.shape)
+    its = {}
+    for a in (0.2, -0.2):
+        H = mg.Hierarchy(op.assemble_mixed(parts, a), med.shape, 3)
+        _, info = krylov.fgmres(lambda v: K @ v, H.cycle, q, maxit=60)
+        its[a] = (info["converged"], info["iters"])
+    assert its[0.2][0] and its[0.2][1] <= 15, its
+    assert not its[-0.2][0], its
