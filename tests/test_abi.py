@@ -110,3 +110,36 @@ def test_create_rejects_bad_coarse_split_on_host(lib_path, split, overlap, msg):
     ctx = C.c_void_p()
     assert lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx)) == 1
     assert msg in lib.ehs_last_error(None).decode()
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """The ctypes mirrors of ehs_problem, ehs_opts and ehs_solve_info have the
+    size and field offsets that a C compiler gives the header's structs, so
+    every option reaches the library in the field it names."""
+    import ctypes as C
+    import shutil
+    from paper_1806_11277_gb300 import ehs
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    rename = {"lam": "lambda"}
+    structs = {"ehs_problem": ehs.Problem, "ehs_opts": ehs.Opts, "ehs_solve_info": ehs.SolveInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ehs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            cf = rename.get(f, f)
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
