@@ -44,3 +44,28 @@ def test_fwi_workload_generator():
     f = true.lam / base.lam
     assert np.allclose(true.mu / base.mu, f) and np.array_equal(true.rho, base.rho)
     assert 1.0 <= f.min() and abs(f.max() - 1.05 ** 2) < 1e-3
+
+
+def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
+    """The bench's clock record (median SM clock under load, max clock, active
+    throttle reasons) from the nvidia-smi CSV it samples, with a stand-in
+    nvidia-smi on PATH: 'Not Active' is not a reason, N/A rows are skipped."""
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '1980, 2070, 1390.5, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]'\n"
+                    "echo '2040, 2070, 1200.0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    s = bench.ClockSampler(0)
+    s.start()
+    import time
+    t0 = time.time()
+    while len(s.rows) < 4 and time.time() - t0 < 20:
+        time.sleep(0.05)
+    rec = s.stop()
+    assert rec["sm_mhz"] == 2040.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
