@@ -69,3 +69,28 @@ def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
     rec = s.stop()
     assert rec["sm_mhz"] == 2040.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
     assert rec["reasons"] == ["sw_power_cap"]
+
+
+def test_every_bench_config_passes_host_validation():
+    """Every bench workload (the default line and each --config) gets past
+    ehs_create's host-side checks of its options against its grid (levels,
+    MG-DD split and overlap, formats): on a host without a GPU the create call
+    then stops at its first CUDA call (EHS_ERR_CUDA), never at EHS_ERR_ARG."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("with a GPU present the create call would build the full hierarchy")
+    import bench
+    from paper_1806_11277_gb300 import build, ehs
+    try:
+        ehs.load(build.build())
+    except FileNotFoundError:
+        pytest.skip("nvcc not available")
+    cases = {"c2": (bench.media, {})}
+    cases.update({k: (v["media"], v["kw"]) for k, v in bench.OTHER.items()})
+    for name, (mk, over) in cases.items():
+        kw = bench.default_kw()
+        kw.update(over)
+        with pytest.raises(ehs.EhsError) as e:
+            ehs.solver_for(mk(), **kw)
+        assert e.value.status == 2, (name, str(e.value))
