@@ -16,6 +16,15 @@ earlier in the lexicographic order; the update equation
 is then written in amplitudes, which gives one linear relation per local DOF.
 The operator stencil values are passed in, so a caller can take them from
 an assembled matrix.
+
+Red-black order (the order the solver uses; Sec. 5 analyses only the
+lexicographic one): a half-step relaxes every cell of one colour from one
+residual, so a plane wave theta mixes only with theta + (pi, pi).  The 6 x 6
+symbol of a red-black sweep is obtained by applying both half-steps to the
+two harmonics on the infinite grid, cell by cell, and reading the new
+amplitudes back at two cells of opposite colour; the smoothing factor takes
+the high harmonics of each pair.  Either block (economic or full) can be
+analysed.
 """
 from __future__ import annotations
 
@@ -144,4 +153,105 @@ def mu_loc(s, wu, wv=None, wp=None, nsamp=63):
                 continue
             S = symbol((t1, t2), s, wu, wv, wp, B)
             best = max(best, np.max(np.abs(np.linalg.eigvals(S))))
+    return best
+
+
+def full_block(s):
+    """Full (2d+1)^2 cell block: every coupling among the cell's five DOFs."""
+    B = np.zeros((5, 5), dtype=np.complex128)
+    for a, (ca, pa) in enumerate(LOCAL):
+        for (cb, off, val) in row_stencil(ca, s):
+            pb = (pa[0] + off[0], pa[1] + off[1])
+            for b, (cl, pl) in enumerate(LOCAL):
+                if cl == cb and pl == pb:
+                    B[a, b] += val
+    return B
+
+
+# ------------------------------------------------------------ red-black
+# Cells (i, j) have centres at half-unit position (2i+1, 2j+1) and colour
+# (i + j) mod 2 (0 = red, relaxed first).  A red-black half-step updates all
+# cells of one colour at once from one residual, so the pair of harmonics
+# theta and theta + (pi, pi) spans an invariant space: the amplitudes are
+# A = [u, v, p of phi_theta, u, v, p of phi_(theta+(pi,pi))].
+_TYPES = ("u", "v", "p")
+
+
+def _dof_pos(t, i, j):
+    """Half-unit position of the type-t DOF that belongs to cell (i, j) on its low side."""
+    return {"u": (2 * i, 2 * j + 1), "v": (2 * i + 1, 2 * j), "p": (2 * i + 1, 2 * j + 1)}[t]
+
+
+def _owners_rb(t, i, j):
+    """(cell, local index) pairs owning the type-t DOF of cell (i, j)."""
+    if t == "u":
+        return [((i - 1, j), 1), ((i, j), 0)]
+    if t == "v":
+        return [((i, j - 1), 3), ((i, j), 2)]
+    return [((i, j), 4)]
+
+
+def _half_step_rb(theta, s, W, Binv, colour, A):
+    t1, t2 = theta
+    ph = lambda X, sh: np.exp(0.5j * ((t1 + sh * np.pi) * X[0] + (t2 + sh * np.pi) * X[1]))
+
+    def err(t, X):
+        k = _TYPES.index(t)
+        return A[k] * ph(X, 0) + A[3 + k] * ph(X, 1)
+
+    def delta(ci, cj):
+        cx, cy = 2 * ci + 1, 2 * cj + 1
+        r = np.zeros(5, dtype=np.complex128)
+        for a, (ca, pa) in enumerate(LOCAL):
+            for (cb, off, val) in row_stencil(ca, s):
+                r[a] -= val * err(cb, (cx + pa[0] + off[0], cy + pa[1] + off[1]))
+        return W * (Binv @ r)
+
+    out = np.zeros(6, dtype=np.complex128)
+    for k, t in enumerate(_TYPES):
+        rows, rhs = [], []
+        for q in (0, 1):                        # two cells of opposite colour parity
+            X = _dof_pos(t, q, 0)
+            v = err(t, X)
+            for (ci, cj), a in _owners_rb(t, q, 0):
+                if (ci + cj) % 2 == colour:
+                    v += delta(ci, cj)[a]
+            rows.append([ph(X, 0), ph(X, 1)])
+            rhs.append(v)
+        out[k], out[3 + k] = np.linalg.solve(np.array(rows), np.array(rhs))
+    return out
+
+
+def symbol_rb(theta, s, wu, wv, wp, B=None):
+    """6 x 6 amplification matrix of one red-black sweep (red, then black) on the
+    harmonic pair theta, theta + (pi, pi)."""
+    B = economic_block(s) if B is None else B
+    Binv = np.linalg.inv(B)
+    W = np.array([wu, wu, wv, wv, wp])
+    S = []
+    for colour in (0, 1):
+        M = np.zeros((6, 6), dtype=np.complex128)
+        for col in range(6):
+            e = np.zeros(6, dtype=np.complex128)
+            e[col] = 1.0
+            M[:, col] = _half_step_rb(theta, s, W, Binv, colour, e)
+        S.append(M)
+    return S[1] @ S[0]
+
+
+def mu_loc_rb(s, wu, wv=None, wp=None, nsamp=32, B=None):
+    """Smoothing factor of one red-black sweep: over theta in the low box, the
+    largest spectral radius of the sweep restricted to the high harmonics of the
+    pairs (theta, theta + (pi, pi)) (theta low, so only its partner is high)
+    and (theta + (pi, 0), theta + (0, pi)) (both high)."""
+    wv = wu if wv is None else wv
+    wp = wu if wp is None else wp
+    th = -np.pi / 2 + np.pi * (np.arange(nsamp) + 0.5) / nsamp
+    best = 0.0
+    for t1 in th:
+        for t2 in th:
+            S = symbol_rb((t1, t2), s, wu, wv, wp, B)
+            best = max(best, np.max(np.abs(np.linalg.eigvals(S[3:, 3:]))))
+            S2 = symbol_rb((t1 + np.pi, t2), s, wu, wv, wp, B)
+            best = max(best, np.max(np.abs(np.linalg.eigvals(S2))))
     return best

@@ -8,7 +8,8 @@
   residual, and the LFA smoothing factors printed in Sec. 5.4 are
   reproduced from stencil values read out of the assembled operator, and
   the LFA symbol equals what a brute-force lexicographic sweep does to a
-  plane wave away from the boundaries,
+  plane wave away from the boundaries, and the two-harmonic red-black symbol
+  equals what the oracle's red-black sweep does to a plane-wave pair,
 * the shift has the sign of the physical attenuation (the other sign does
   not converge),
 * FGMRES reaches the exact (dense) solution on tiny grids,
@@ -413,3 +414,37 @@ def test_shift_sign_same_as_attenuation_converges():
         its[a] = (info["converged"], info["iters"])
     assert its[0.2][0] and its[0.2][1] <= 15, its
     assert not its[-0.2][0], its
+
+
+@pytest.mark.parametrize("economic", [True, False])
+def test_rb_vanka_sweep_matches_two_harmonic_symbol(economic):
+    """Red-black order couples theta with theta + (pi, pi): one red-black sweep
+    of the oracle's `Level` (economic or full block, single or component
+    damping) applied to a plane-wave pair equals the 6 x 6 two-harmonic symbol
+    at every cell far enough from the boundary that neither half-step sees it
+    (each half-step reaches two cells); the agreement is exact up to rounding."""
+    h, omega, gamma, lam, mu, rho = 1 / 128, 80.0, 0.2, 500.0, 1.0, 1.0
+    n = 20
+    shape = (n, n)
+    parts = op.Parts(*(np.full(shape, v) for v in (lam, mu, rho, gamma * omega)), omega, h)
+    K = op.assemble_mixed(parts)
+    s = lfa.stencil_values(h, omega, gamma, lam, mu, rho)
+    B = None if economic else lfa.full_block(s)
+    j, i = np.mgrid[0:n, 0:n]
+    pos = [(2 * i, 2 * j + 1), (2 * i + 1, 2 * j), (2 * i + 1, 2 * j + 1)]     # u, v, p (half units)
+    rng = np.random.default_rng(0)
+    for wu, wp in ((0.75, 0.75), (0.85, 0.65)):
+        lv = mg.Level(K, shape, wu, economic=economic, wu=wu, wp=wp)
+        for theta in ((2.0, 0.3), (-1.2, 2.5), (0.1, -0.2)):
+            ph = lambda X, Y, sh: np.exp(0.5j * ((theta[0] + sh * np.pi) * X + (theta[1] + sh * np.pi) * Y))
+            A = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+            sl = np.stack([A[k] * ph(*pos[k], 0) + A[3 + k] * ph(*pos[k], 1) for k in range(3)])
+            sl[0][:, 0] = 0
+            sl[1][0, :] = 0
+            x = op.slots_to_dofs(sl, shape)
+            got = op.dofs_to_slots(lv.relax_rb(np.zeros_like(x), x), shape)
+            Aw = lfa.symbol_rb(theta, s, wu, wu, wp, B) @ A
+            sl_w = np.stack([Aw[k] * ph(*pos[k], 0) + Aw[3 + k] * ph(*pos[k], 1) for k in range(3)])
+            inner = (slice(None), slice(6, n - 6), slice(6, n - 6))
+            scale = np.abs(sl_w[inner]).max(axis=(1, 2), keepdims=True)       # per component
+            assert np.all(np.abs(got[inner] - sl_w[inner]) <= 1e-11 * scale), (wu, wp, theta)
