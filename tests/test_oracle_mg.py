@@ -448,3 +448,17 @@ def test_rb_vanka_sweep_matches_two_harmonic_symbol(economic):
             inner = (slice(None), slice(6, n - 6), slice(6, n - 6))
             scale = np.abs(sl_w[inner]).max(axis=(1, 2), keepdims=True)       # per component
             assert np.all(np.abs(got[inner] - sl_w[inner]) <= 1e-11 * scale), (wu, wp, theta)
+
+
+def test_rb_smoothing_factor_orders_the_measured_choices():
+    """The red-black smoothing factors behind three measured choices (Sec. 5.4
+    parameters, coarse theta sampling): at w = 0.75 the economic block smooths
+    better than the full block, the component damping (0.85, 0.65) that Sec.
+    5.4 finds best for lexicographic order is worse in red-black order, and the
+    economic red-black sweep diverges at w = 1."""
+    s = lfa.stencil_values(1 / 128, 80.0, 0.2, 500.0, 1.0, 1.0)
+    econ = lfa.mu_loc_rb(s, 0.75, nsamp=12)
+    full = lfa.mu_loc_rb(s, 0.75, nsamp=12, B=lfa.full_block(s))
+    comp = lfa.mu_loc_rb(s, 0.85, 0.85, 0.65, nsamp=12)
+    assert econ < full < comp < 1.0, (econ, full, comp)
+    assert lfa.mu_loc_rb(s, 1.0, nsamp=12) > 1.0
