@@ -224,7 +224,10 @@ ehs_status ehs_fine_smooth_noalloc(const ehs_problem* prob, int nrhs, double alp
                                    double wp, int nsweeps, int prec, const void* b, void* x,
                                    void* stream);
 
-/* Sizes: items of a vector batch, complex values per item at level l. */
+/* Sizes: items of a vector batch (0 for a NULL context), complex values per item at level l
+   (-1 for a NULL context or a level out of range), and the cells per axis of level l written to
+   the host array n[3] (returns 0; -1 and nothing written for a NULL context or n, or a level out
+   of range). */
 int ehs_items(const ehs_ctx* ctx);
 long long ehs_level_len(const ehs_ctx* ctx, int level);
 int ehs_level_dims(const ehs_ctx* ctx, int level, int n[3]);

@@ -1308,7 +1308,7 @@ long long ehs_level_len(const ehs_ctx* c, int level) {
   return (long long)(c->d + 1) * c->H.lv[level].g.ncell;
 }
 int ehs_level_dims(const ehs_ctx* c, int level, int n[3]) {
-  if (!c || level < 0 || level >= (int)c->H.lv.size()) return -1;
+  if (!c || !n || level < 0 || level >= (int)c->H.lv.size()) return -1;
   for (int k = 0; k < 3; ++k) n[k] = c->H.lv[level].g.n[k];
   return 0;
 }

@@ -143,3 +143,29 @@ def test_binding_structs_match_the_c_layout(tmp_path):
         assert got[(cname, "sizeof")] == C.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_null_context_is_an_argument_error_everywhere(lib_path):
+    """Every entry point answers a NULL context as the header states (EHS_ERR_ARG,
+    -1 or 0), without touching a device."""
+    import ctypes as C
+    from paper_1806_11277_gb300 import ehs
+    lib = ehs.load(lib_path)
+    buf = C.c_void_p(1)                        # never dereferenced: the context check comes first
+    assert lib.ehs_destroy(None) == 0
+    assert lib.ehs_items(None) == 0
+    assert lib.ehs_level_len(None, 0) == -1
+    n3 = (C.c_int * 3)()
+    assert lib.ehs_level_dims(None, 0, n3) == -1
+    assert lib.ehs_sync(None) == 1
+    assert lib.ehs_op_apply(None, 0, 0, 1, buf, buf) == 1
+    assert lib.ehs_smooth(None, 0, 1, 1, buf, buf) == 1
+    assert lib.ehs_vcycle(None, 1, buf, buf) == 1
+    assert lib.ehs_coarse_solve(None, 1, buf, buf) == 1
+    assert lib.ehs_coarse_local_apply(None, 1, 0, buf, buf) == 1
+    assert lib.ehs_dd_precond(None, 1, buf, buf) == 1
+    assert lib.ehs_fgmres_solve(None, buf, buf, None) == 1
+    assert lib.ehs_adjoint_solve(None, buf, buf, None) == 1
+    assert lib.ehs_gradient(None, buf, buf, None, None, None) == 1
+    a, b = C.c_int(), C.c_int()
+    assert lib.ehs_coarse_dims(None, C.byref(a), C.byref(b), None) == 1
