@@ -134,7 +134,11 @@ void ehs_default_opts(ehs_opts* o);
  * and the DD subdomain hierarchies when opts->precond is DD) for every
  * medium.  stream: a cudaStream_t (NULL = legacy default stream).
  * Returns EHS_ERR_ARG for invalid sizes or media (rho <= 0, mu < 0,
- * lambda + mu <= 0, non-finite omega, n not divisible). */
+ * lambda + mu <= 0, non-finite omega, n not divisible), for options out of
+ * range, and for a coarsest level whose dense inverse (the whole level, or
+ * every MG-DD box) would exceed 16384 unknowns; options and sizes are checked
+ * on the host before any device work, the media values after they are read.
+ * On failure *out is NULL and ehs_last_error(NULL) holds the reason. */
 ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* stream, ehs_ctx** out);
 ehs_status ehs_destroy(ehs_ctx* ctx);
 

@@ -619,6 +619,37 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
         throw ArgError("coarse_dd_overlap larger than half a coarsest-grid core");
     }
   }
+  // dense inverses of the global coarsest level: the whole level, or every MG-DD box
+  if (O->precond == EHS_PRECOND_MG) {
+    int nc[3] = {1, 1, 1}, ns[3] = {1, 1, 1};
+    long long cells = 1;
+    for (int k = 0; k < P->dim; ++k) {
+      nc[k] = P->n[k] >> (O->levels - 1);
+      ns[k] = std::max(O->coarse_dd[k], 1);
+      cells *= nc[k];
+    }
+    if (ns[0] * ns[1] * ns[2] == 1) {
+      if ((P->dim + 1) * cells > 16384)
+        throw ArgError("coarsest grid too large for the dense FP64 inverse (use more levels or coarse_dd)");
+    } else {
+      long long big = 0;   // unknowns of the largest box: its pressures and the faces with both cells inside
+      int id[3];
+      for (id[2] = 0; id[2] < ns[2]; ++id[2])
+        for (id[1] = 0; id[1] < ns[1]; ++id[1])
+          for (id[0] = 0; id[0] < ns[0]; ++id[0]) {
+            long long ext[3] = {1, 1, 1};
+            for (int k = 0; k < P->dim; ++k) {
+              const int lo0 = id[k] * (nc[k] / ns[k]) + std::min(id[k], nc[k] % ns[k]);
+              const int hi0 = lo0 + nc[k] / ns[k] + (id[k] < nc[k] % ns[k] ? 1 : 0);
+              ext[k] = std::min(hi0 + O->coarse_dd_overlap, nc[k]) - std::max(lo0 - O->coarse_dd_overlap, 0);
+            }
+            long long nbox = ext[0] * ext[1] * ext[2];
+            for (int a = 0; a < P->dim; ++a) nbox += ext[0] * ext[1] * ext[2] / ext[a] * (ext[a] - 1);
+            big = std::max(big, nbox);
+          }
+      if ((big + 7) / 8 * 8 > 16384) throw ArgError("coarse_dd subdomains too large for dense local inverses");
+    }
+  }
 }
 
 void check_media(ehs_ctx* c, const double* lam, const double* mu, const double* rho, long long n) {

@@ -169,3 +169,38 @@ def test_null_context_is_an_argument_error_everywhere(lib_path):
     assert lib.ehs_gradient(None, buf, buf, None, None, None) == 1
     a, b = C.c_int(), C.c_int()
     assert lib.ehs_coarse_dims(None, C.byref(a), C.byref(b), None) == 1
+
+
+@pytest.mark.parametrize("n,levels,split,overlap,msg", [
+    (512, 2, (1, 1, 1), 2, "coarsest grid too large"),      # 256^2 coarsest: 196608 unknowns
+    (256, 2, (1, 1, 1), 2, "coarsest grid too large"),      # 128^2 coarsest: 49152 unknowns
+    (512, 2, (2, 2, 1), 1, "subdomains too large"),         # boxes of 129^2 cells
+    (128, 3, (1, 1, 1), 2, None),                           # 32^2 coarsest: 3072 unknowns
+    (512, 3, (8, 8, 1), 3, None),                           # boxes of at most 22^2 cells: 1408 unknowns
+])
+def test_create_checks_dense_inverse_sizes_on_host(lib_path, n, levels, split, overlap, msg):
+    """The coarsest level's dense inverses (the whole level, or every MG-DD box)
+    are limited to 16384 unknowns; a hierarchy beyond that is EHS_ERR_ARG from
+    the host-side checks, before any device work.  Accepted cases go on to the
+    device (EHS_ERR_CUDA on a host without a GPU)."""
+    import ctypes as C
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if msg is None and torch.cuda.is_available():
+        pytest.skip("with a GPU present an accepted case would build the full hierarchy")
+    from paper_1806_11277_gb300 import ehs
+    lib = ehs.load(lib_path)
+    arrs = [np.full(n * n, 2.0), np.ones(n * n), np.ones(n * n)]
+    p = ehs.Problem()
+    p.dim, p.h, p.omega, p.nmedia = 2, 1.0, 0.6, 1
+    p.n[0], p.n[1], p.n[2] = n, n, 1
+    p.lam, p.mu, p.rho = (a.ctypes.data for a in arrs)
+    p.abl_cells, p.abl_max, p.gamma_add = 8, 1.0, 0.03
+    o = ehs.default_opts(levels=levels, coarse_dd=split, coarse_dd_overlap=overlap)
+    ctx = C.c_void_p()
+    st = lib.ehs_create(C.byref(p), C.byref(o), None, C.byref(ctx))
+    assert not ctx.value
+    if msg is None:
+        assert st == 2, lib.ehs_last_error(None)
+    else:
+        assert st == 1 and msg in lib.ehs_last_error(None).decode()
