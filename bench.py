@@ -554,7 +554,9 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64+c128", "data": "synthetic",
+        # arithmetic of the path: complex64 preconditioner with a double-float (FP32-pair) Krylov
+        # solve in the mixed form, complex128 everywhere in the plain FP64 form
+        "dtype": "c128" if kw.get("prec", 1) == 0 else "c64+df64", "data": "synthetic",
         "config": {"name": args.config, "workload": WORKLOAD if cfg is None else cfg["workload"],
                    "grid": list(meds[0].shape), "media": nsolve,
                    "sigmas": list(SIGMAS) if cfg is None else None, "levels": kw["levels"],
