@@ -462,3 +462,28 @@ def test_rb_smoothing_factor_orders_the_measured_choices():
     comp = lfa.mu_loc_rb(s, 0.85, 0.85, 0.65, nsamp=12)
     assert econ < full < comp < 1.0, (econ, full, comp)
     assert lfa.mu_loc_rb(s, 1.0, nsamp=12) > 1.0
+
+
+def test_fgmres_is_flexible():
+    """With a preconditioner that changes at every application (a different
+    random diagonal scaling each call), the iterate must be built from the
+    stored preconditioned directions Z (flexible GMRES): the true residual of
+    the returned x equals the Arnoldi estimate, reaches the tolerance, and x
+    is the dense solution.  A right-preconditioned GMRES update through V
+    would leave a true residual far from its estimate."""
+    rng = np.random.default_rng(8)
+    n = 60
+    A = np.diag(np.linspace(1, 30, n)) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    d = np.diag(A)
+
+    def precond(v):
+        return v / d * (1 + 0.5 * rng.random(n))          # a new scaling every call
+
+    # one Arnoldi cycle (no restart to hide a wrong update behind a recomputed residual)
+    x, info = krylov.fgmres(lambda v: A @ v, precond, b, m=60, tol=1e-10, maxit=60)
+    true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    est = info["history"][-1]
+    assert info["converged"] and true <= 1e-10 and info["iters"] < 60
+    assert abs(true - est) <= 1e-12 + 1e-3 * est
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-8 * np.linalg.norm(x)
