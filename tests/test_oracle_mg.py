@@ -470,7 +470,8 @@ def test_fgmres_is_flexible():
     stored preconditioned directions Z (flexible GMRES): the true residual of
     the returned x equals the Arnoldi estimate, reaches the tolerance, and x
     is the dense solution.  A right-preconditioned GMRES update through V
-    would leave a true residual far from its estimate."""
+    (a new preconditioner application to V y) leaves a true residual far from
+    its estimate, which this single-cycle run exposes."""
     rng = np.random.default_rng(8)
     n = 60
     A = np.diag(np.linspace(1, 30, n)) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
