@@ -488,3 +488,39 @@ def test_fgmres_is_flexible():
     assert info["converged"] and true <= 1e-10 and info["iters"] < 60
     assert abs(true - est) <= 1e-12 + 1e-3 * est
     assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-8 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("shape", [(16, 24), (8, 8, 8)])
+def test_coarse_grid_correction_is_a_galerkin_projection(shape):
+    """Algorithm TwoCycle without smoothing: x = P K_c^{-1} P^T b with
+    K_c = P^T K_s P leaves a residual that the restriction annihilates,
+    P^T (b - K_s x) = 0, and a second correction changes nothing."""
+    d = len(shape)
+    med = (synth.random_2d(n=shape[0], nx=shape[1], sigma=0.4, seed=5, corr=3.0, abl=3) if d == 2
+           else synth.layered_3d(n=shape[0], seed=5, corr=2.0, abl=2))
+    Ks = op.assemble_mixed(op.parts_for(med), 0.25).tocsr()
+    H = mg.Hierarchy(Ks, med.shape, 2)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(Ks.shape[0]) + 1j * rng.standard_normal(Ks.shape[0])
+    x = H.cycle(b, nu1=0, nu2=0)
+    r = b - Ks @ x
+    assert np.linalg.norm(H.P[0].T @ r) <= 1e-10 * np.linalg.norm(H.P[0].T @ b)
+    x2 = x + H.cycle(r, nu1=0, nu2=0)
+    assert np.linalg.norm(x2 - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_w_cycle_equals_v_cycle_on_two_levels_only():
+    """Reading of the cycle: the level above the coarsest calls the coarsest
+    solve once per visit, so with two levels W(1,1) is V(1,1); with three
+    levels the W-cycle visits level 1 twice and differs."""
+    med = synth.random_2d(n=32, sigma=0.4, seed=6, corr=4.0, abl=4)
+    Ks = op.assemble_mixed(op.parts_for(med), 0.25).tocsr()
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(Ks.shape[0]) + 1j * rng.standard_normal(Ks.shape[0])
+    H2 = mg.Hierarchy(Ks, med.shape, 2)
+    assert np.array_equal(H2.cycle(b, gamma=1), H2.cycle(b, gamma=2))
+    H3 = mg.Hierarchy(Ks, med.shape, 3)
+    v, w = H3.cycle(b, gamma=1), H3.cycle(b, gamma=2)
+    assert np.linalg.norm(v - w) > 1e-3 * np.linalg.norm(v)
+    # the W-cycle is the better level-1 solve: smaller residual of the shifted system
+    assert np.linalg.norm(b - Ks @ w) < np.linalg.norm(b - Ks @ v)
