@@ -524,3 +524,48 @@ def test_w_cycle_equals_v_cycle_on_two_levels_only():
     assert np.linalg.norm(v - w) > 1e-3 * np.linalg.norm(v)
     # the W-cycle is the better level-1 solve: smaller residual of the shifted system
     assert np.linalg.norm(b - Ks @ w) < np.linalg.norm(b - Ks @ v)
+
+
+def test_prolongation_3d_reproduces_constants_and_lines():
+    """The 3D transfer is the tensor product of the same 1D rules: p keeps
+    constants everywhere and linear fields away from the boundary; each u_k is
+    exact for a field linear in its own direction (vertex-like rule) and for a
+    field linear across it away from the boundary (cell-like rule)."""
+    cs = (4, 6, 8)                                   # (n_z, n_y, n_x)
+    fs = tuple(2 * c for c in cs)
+    P = mg.prolongation(cs)
+
+    def up(xc):
+        return op.dofs_to_slots(P @ op.slots_to_dofs(xc, cs), fs).real
+
+    xc = np.zeros((4,) + cs); xc[3] = 1.0
+    assert np.allclose(up(xc)[3], 1.0)
+    Z = np.arange(cs[0]) + 0.5
+    xc = np.zeros((4,) + cs); xc[3] = np.broadcast_to(Z[:, None, None], cs)
+    Zf = (np.arange(fs[0]) + 0.5) / 2
+    assert np.allclose(up(xc)[3][1:-1], np.broadcast_to(Zf[:, None, None], fs)[1:-1])
+    for k in range(3):                               # u_k, numpy axis a = 2 - k
+        a = 2 - k
+        # linear in its own direction: face position j (coarse) -> j / 2 (fine), interior faces
+        sh = [1, 1, 1]; sh[a] = cs[a]
+        xc = np.zeros((4,) + cs); xc[k] = np.broadcast_to((np.arange(cs[a]) * 1.0).reshape(sh), cs)
+        sl = [slice(None)] * 3; sl[a] = 0
+        xc[k][tuple(sl)] = 0.0
+        got = up(xc)[k]
+        shf = [1, 1, 1]; shf[a] = fs[a]
+        want = np.broadcast_to((np.arange(fs[a]) / 2.0).reshape(shf), fs)
+        inner = [slice(1, -1)] * 3
+        inner[a] = slice(1, fs[a] - 1)               # the last fine face averages with the zero boundary face
+        assert np.allclose(got[tuple(inner)], want[tuple(inner)]), k
+        # linear across it (along another axis b), away from the boundary
+        b = (a + 1) % 3
+        shb = [1, 1, 1]; shb[b] = cs[b]
+        xc = np.zeros((4,) + cs)
+        xc[k] = np.broadcast_to(((np.arange(cs[b]) + 0.5)).reshape(shb), cs).copy()
+        xc[k][tuple(sl)] = 0.0
+        got = up(xc)[k]
+        shfb = [1, 1, 1]; shfb[b] = fs[b]
+        want = np.broadcast_to(((np.arange(fs[b]) + 0.5) / 2).reshape(shfb), fs)
+        inner = [slice(2, -2)] * 3
+        inner[a] = slice(2, fs[a] - 2)
+        assert np.allclose(got[tuple(inner)], want[tuple(inner)]), (k, b)
