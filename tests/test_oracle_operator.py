@@ -184,3 +184,58 @@ def test_gamma_profile():
     assert np.isclose(g[6, 3], 0.05 + omega * (1 / L) ** 2)  # innermost layer cell
     assert np.isclose(g[1, 2], 0.05 + omega * (3 / L) ** 2)  # corner: max over directions
     assert np.allclose(g, g[::-1, ::-1])
+
+
+def test_schur_complement_is_displacement_operator_3d():
+    """Eliminating p from the 3D mixed system gives H^e = S + grad D(lambda+mu) div."""
+    shape = (6, 7, 8)
+    rng = np.random.default_rng(12)
+    lam = 2 + rng.random(shape); mu = 0.5 + rng.random(shape); rho = 1 + rng.random(shape)
+    parts = op.Parts(lam, mu, rho, op.gamma_profile(shape, 0.7, 2), 0.7, 1.0)
+    K = op.assemble_mixed(parts, 0.2)
+    He = op.assemble_displacement(parts, 0.2)
+    nu = He.shape[0]
+    A, B, C = K[:nu, :nu], K[:nu, nu:], K[nu:, nu:]
+    S = A - B @ sp.diags(1.0 / C.diagonal()) @ B.T
+    assert abs(S - He).max() <= 1e-12 * abs(He).max()
+
+
+def test_manufactured_solution_second_order_3d():
+    """3D manufactured solution (Dirichlet-compatible sines, smooth lambda, mu,
+    rho, no attenuation): the displacement error falls at second order."""
+    sympy = pytest.importorskip("sympy")
+    x, y, z = sympy.symbols("x y z")
+    pi, s = sympy.pi, sympy.sin
+    u = [s(pi * x) * s(pi * y) ** 2 * s(pi * z) ** 2,
+         s(pi * x) ** 2 * s(pi * y) * s(pi * z) ** 2,
+         s(pi * x) ** 2 * s(pi * y) ** 2 * s(pi * z)]
+    X = (x, y, z)
+    lam_e, mu_e, rho_e = 2 + x * y * z, 1 + x ** 2 / 2 + z / 4, 1 + y / 4
+    om = 2.0
+    div = sum(sympy.diff(u[k], X[k]) for k in range(3))
+    f = [-(sympy.diff((lam_e + mu_e) * div, X[k]) + sum(sympy.diff(mu_e * sympy.diff(u[k], X[j]), X[j])
+                                                      for j in range(3))) - om ** 2 * rho_e * u[k]
+         for k in range(3)]
+    F = [sympy.lambdify(X, e, "numpy") for e in f]
+    U = [sympy.lambdify(X, e, "numpy") for e in u]
+    Cf = [sympy.lambdify(X, e, "numpy") for e in (lam_e, mu_e, rho_e)]
+    errs = []
+    for n in (8, 16, 32):
+        h = 1.0 / n
+        shape = (n, n, n)
+        zc, yc, xc = np.meshgrid(*[(np.arange(n) + 0.5) * h] * 3, indexing="ij")
+        lam, mu, rho = [np.broadcast_to(c(xc, yc, zc), shape).astype(float) for c in Cf]
+        He = op.assemble_displacement(op.Parts(lam, mu, rho, np.zeros(shape), om, h)).real.tocsr()
+        fs = np.zeros((4,) + shape)
+        us = np.zeros((4,) + shape)
+        for k in range(3):
+            Xk, Yk, Zk = _face_positions(shape, k, h)
+            fs[k] = F[k](Xk, Yk, Zk)
+            us[k] = U[k](Xk, Yk, Zk)
+        fv = op.slots_to_dofs(fs, shape)[:He.shape[0]].real
+        ue = op.slots_to_dofs(us, shape)[:He.shape[0]].real
+        uh, info = spla.cg(He, fv, rtol=1e-12, maxiter=20000)   # SPD at this omega
+        assert info == 0
+        errs.append(np.sqrt(np.mean((uh - ue) ** 2)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert abs(orders[-1] - 2.0) < 0.2, (errs, orders)
