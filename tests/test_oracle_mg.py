@@ -75,15 +75,17 @@ def test_economic_block_sparsity(shape, nnz):
     assert np.count_nonzero(Bf) > nnz
 
 
-def test_full_vanka_zeroes_cell_residual():
-    med = synth.random_2d(n=16, sigma=0.45, seed=3, corr=3.0, abl=3)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_full_vanka_zeroes_cell_residual(dim):
+    med = (synth.random_2d(n=16, sigma=0.45, seed=3, corr=3.0, abl=3) if dim == 2
+           else synth.layered_3d(n=8, seed=3, corr=2.0, abl=2))
     Ks = op.assemble_mixed(op.parts_for(med), 0.2)
     lv = mg.Level(Ks, med.shape, 1.0, economic=False)
     rng = np.random.default_rng(0)
     n = Ks.shape[0]
     b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    for c in (0, 37, 100, 255):
+    for c in (0, 37, 100, 255, 511)[:4 if dim == 2 else 5]:
         x1 = lv._update_cells(x.copy(), b - Ks @ x, np.array([c]))
         I = lv.dofs[c][lv.valid[c]]
         r1 = (b - Ks @ x1)[I]
