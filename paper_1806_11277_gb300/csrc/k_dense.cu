@@ -3,6 +3,13 @@
 // the stored inverse (Algorithm TwoCycle step 3 solved exactly, as the paper's
 // coarsest LU does).  Boundary slots are identity rows so the dense index is
 // simply comp * ncell + cell.
+//
+// MG-DD (Sec. 4): the same machinery for the subdomains of the coarsest grid.
+// Each box's local matrix (the coarsest operator restricted to the box
+// unknowns, padded with identity rows to nloc) is assembled from the stencil
+// table and inverted in FP64 together with the others; per colour one launch
+// multiplies every subdomain's stored inverse (double-float, complex64, FP16
+// or BF16 pairs) with its local residuals, skipping the padding rows.
 #include "kernels.h"
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
