@@ -9,7 +9,9 @@ off-by-one in the overlap or the padding, or a misplaced absorbing ramp fails:
 * the padding holds a clamped copy of the medium and gamma grows by
   omega * dd_abl_max * (depth / pad)^2, reaching omega * dd_abl_max at the
   outer cell; no padding on sides at the domain boundary;
-* every padded extent is a multiple of the coarsening factor 2^(levels-1).
+* every padded extent is a multiple of the coarsening factor 2^(levels-1);
+* with exact subdomain solves the iteration count rises as the domain is
+  split more aggressively (the trend of Table DDexact).
 """
 import itertools
 
@@ -98,3 +100,25 @@ def test_padding_medium_and_absorbing_ramp():
         if sd.pad_hi[0]:
             row = extra[-1, xlo:xlo + nx]
             assert np.allclose(row, med.omega * DD_ABL, rtol=1e-14)
+
+
+def test_exact_dd_deteriorates_with_aggressive_splitting():
+    """The trend of Table DDexact (exact subdomain solves with absorbing
+    interface padding): on a shallow, wide 2D model at 12 points per
+    S-wavelength the FGMRES count grows with every halving of the subdomains
+    along x, and the 16 x 1 split needs several times the 2 x 1 count (the
+    paper: 28 -> 130 on its smallest grid)."""
+    from oracle import krylov
+    ny, nx = 32, 128
+    med = synth.random_2d(n=ny, nx=nx, sigma=0.3, seed=0, corr=8.0, abl=8, ppw=12.0)
+    med.sources = [(0, (ny // 2, nx // 2))]
+    K = op.assemble_mixed(op.parts_for(med))
+    q = op.slots_to_dofs(synth.point_rhs(med.shape, med.sources)[0], med.shape)
+    its = []
+    for sx in (2, 4, 8, 16):
+        D = dd.DD(med, (1, sx), 4, 8, 2, 0.05, local="exact")
+        _, info = krylov.fgmres(lambda v: K @ v, D.apply, q, maxit=300)
+        assert info["converged"], sx
+        its.append(info["iters"])
+    assert all(a < b for a, b in zip(its, its[1:])), its
+    assert its[-1] >= 4 * its[0], its
