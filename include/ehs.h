@@ -54,9 +54,11 @@ typedef enum {
   EHS_ERR_OOM = 3,        /* device allocation failed */
   EHS_ERR_NOCONV = 4,     /* maxit reached before tol */
   EHS_ERR_BREAKDOWN = 5,  /* Arnoldi breakdown before tol */
-  EHS_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+  EHS_ERR_TIMEOUT = 6,    /* reserved for a bounded device wait that gives up; no kernel of this
+                             version waits on another, so no call returns it */
   EHS_ERR_NONFINITE = 7,  /* NaN / Inf in a residual norm or a pivot */
-  EHS_ERR_UNSUPPORTED = 8 /* option combination not built */
+  EHS_ERR_UNSUPPORTED = 8 /* reserved for an option combination that is not built; this version
+                             rejects unknown option values with EHS_ERR_ARG instead */
 } ehs_status;
 
 typedef enum { EHS_C128 = 0, EHS_C64 = 1 } ehs_prec;
