@@ -271,11 +271,22 @@ def oracle_sample(meds, iters_per_sample, which=0):
         q = op.slots_to_dofs(rhs([med])[0], med.shape)
         _ORACLE_CACHE[k] = (K, H, q)
     K, H, q = _ORACLE_CACHE[k]
-    t = time.perf_counter()
+    t, c = time.perf_counter(), time.process_time()
     _, info = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=CYCLE), q, m=10,
                             maxit=iters_per_sample, tol=1e-30)
     dt = time.perf_counter() - t
+    _CPU_METER["wall"] += dt
+    _CPU_METER["cpu"] += time.process_time() - c
     return dt / max(1, info["iters"]), info["iters"]
+
+
+# wall and process CPU seconds of the timed oracle work (all threads of the process)
+_CPU_METER = {"wall": 0.0, "cpu": 0.0}
+
+
+def cores_used(meter):
+    """Threads the timed oracle work kept busy on average: process CPU time / wall time."""
+    return max(1, int(round(meter["cpu"] / meter["wall"]))) if meter["wall"] > 0 else 1
 
 
 def oracle_iteration_counts():
@@ -305,6 +316,8 @@ def run_reference(args):
     iters = oracle_iteration_counts()
     per = []
     for s in range(args.warmup + args.steps):
+        if s == args.warmup:
+            _CPU_METER.update(wall=0.0, cpu=0.0)
         t_it, n_it = oracle_sample(meds, args.ref_iters, which=s)
         if s >= args.warmup:
             per.append((s % len(meds), t_it))
@@ -317,7 +330,8 @@ def run_reference(args):
         "ms_per_step": t_iter * args.ref_iters * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "media": len(SIGMAS)},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores_used(_CPU_METER),
+                         "threads_available": cpu_threads(), "kind": "oracle",
                          "sample": (f"{args.ref_iters} oracle FGMRES iterations per step on one medium "
                                     f"(media cycled), seconds/iteration x the oracle's own mean iteration "
                                     f"count per solve ({mean_iters}) from tests/golden/c2_oracle_iters.json")},
@@ -588,6 +602,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu and cfg is None:
         iters_o = oracle_iteration_counts()
         t_it = []
+        _CPU_METER.update(wall=0.0, cpu=0.0)
         for s in range(len(SIGMAS)):
             ti, _ = oracle_sample(meds, args.cpu_iters, which=s)
             t_it.append(ti)
@@ -595,7 +610,8 @@ def run_gpu(args):
         src = "tests/golden/c2_oracle_iters.json" if iters_o else "this run's GPU counts"
         cpu_val = 1.0 / (float(np.mean(t_it)) * mean_iters)
         line["cpu_baseline"] = {
-            "value": cpu_val, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+            "value": cpu_val, "unit": "solves/s", "cores": cores_used(_CPU_METER),
+            "threads_available": cpu_threads(), "kind": "oracle",
             "sample": (f"{args.cpu_iters} oracle FGMRES iterations on each of the 4 media; "
                        f"seconds/iteration x mean iterations per solve ({mean_iters:.1f}, {src})")}
     if rank == 0 and world == 1 and not args.no_cpu and args.config == "c1":
@@ -606,12 +622,15 @@ def run_gpu(args):
         K = op.assemble_mixed(parts)
         H = mg.Hierarchy(op.assemble_mixed(parts, kw["alpha"]), med.shape, kw["levels"], w=list(kw["w"]))
         qo = op.slots_to_dofs(q_host[0], med.shape)
-        t = time.perf_counter()
+        t, c = time.perf_counter(), time.process_time()
         reps = 3
         for _ in range(reps):
             krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
-        cpu_val = reps / (time.perf_counter() - t)
-        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+        wall = time.perf_counter() - t
+        meter = {"wall": wall, "cpu": time.process_time() - c}
+        cpu_val = reps / wall
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": cores_used(meter),
+                                "threads_available": cpu_threads(), "kind": "oracle",
                                 "sample": f"{reps} whole oracle solves of the 64x64 case (hierarchy built beforehand)"}
     S.close()
     if rank == 0:
