@@ -122,3 +122,16 @@ def test_exact_dd_deteriorates_with_aggressive_splitting():
         its.append(info["iters"])
     assert all(a < b for a, b in zip(its, its[1:])), its
     assert its[-1] >= 4 * its[0], its
+
+
+def test_near_equal_splits_agree():
+    """Both DD layers split an axis the same way: nearly equal consecutive
+    parts, the larger ones first, covering the axis exactly."""
+    from oracle import multigrid as mg
+    for n in range(1, 70):
+        for s in range(1, min(n, 17) + 1):
+            e = dd.split_axis(n, s)
+            assert list(e) == list(mg.near_equal_edges(n, s))
+            sizes = np.diff(e)
+            assert e[0] == 0 and e[-1] == n and sizes.max() - sizes.min() <= 1
+            assert np.all(np.diff(sizes) <= 0)
