@@ -571,3 +571,30 @@ def test_prolongation_3d_reproduces_constants_and_lines():
         inner = [slice(2, -2)] * 3
         inner[a] = slice(2, fs[a] - 2)
         assert np.allclose(got[tuple(inner)], want[tuple(inner)]), (k, b)
+
+
+def test_full_vanka_cycles_match_fig_comptime():
+    """The paper's constant-coefficient experiment (Fig. CompTime, Sec. 6.1)
+    with its stated defaults: W(1,1) red-black full Vanka (damping 0.75, 0.5,
+    0.25), the shift 0.4 it gives for four levels, flexible GMRES(5), 20-cell
+    absorbing layer, source in the middle of the top row.  The level count is
+    not printed; with four levels the oracle's cycle counts are within 15 % of
+    the printed ones (tests/golden/comptime_full_vanka.txt)."""
+    import os
+    gold = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "comptime_full_vanka.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                lam, cyc, tol = line.split()
+                gold.append((float(lam), int(cyc), float(tol)))
+    ny, nx, omega = 128, 256, 3 * np.pi
+    h = 2 * np.pi / omega / 10
+    for lam, cyc, tol in gold:
+        med = synth.constant_2d(ny, nx, lam, 1.0, 1.0, omega, 20, h=h, sources=[(0, (0, nx // 2))])
+        parts = op.parts_for(med)
+        K = op.assemble_mixed(parts)
+        q = op.slots_to_dofs(synth.point_rhs(med.shape, med.sources)[0], med.shape)
+        H = mg.Hierarchy(op.assemble_mixed(parts, 0.4), med.shape, 4, w=[0.75, 0.5, 0.25], economic=False)
+        _, info = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), q, m=5, maxit=200)
+        assert info["converged"]
+        assert abs(info["iters"] - cyc) <= tol * cyc, (lam, info["iters"], cyc)
