@@ -141,6 +141,19 @@ def test_lfa_smoothing_factor_matches_paper():
     assert abs(lfa.mu_loc(s, 0.85, 0.85, 0.65) - v) <= tol
 
 
+def test_lfa_smoothing_factor_squared_matches_table():
+    """The mu_loc^2 row of Table rho_cf_comparison (Sec. 5.4): at h = 1/1024 the
+    smoothing factor depends on the points per wavelength and barely on gamma."""
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "lfa_mu2_table.txt")) as f:
+        rows = [tuple(map(float, l.split())) for l in f if l.strip() and not l.startswith("#")]
+    h = 1 / 1024
+    for ppw, gam, want, tol in rows:
+        omega = 2 * np.pi / (ppw * h)                   # S-wavelength 2 pi / omega with Vs = 1
+        s = lfa.stencil_values(h, omega, gam, 500.0, 1.0, 1.0)
+        assert abs(lfa.mu_loc(s, 0.75, nsamp=63) ** 2 - want) <= tol, (ppw, gam)
+
+
 def test_fgmres_tiny_grid_matches_dense_solve():
     for n, levels in ((4, 2), (8, 3)):
         med = synth.homogeneous_2d(n=n, abl=1, ppw=6.0)
