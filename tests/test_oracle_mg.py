@@ -131,12 +131,18 @@ def test_lfa_smoothing_factor_matches_paper():
     perm = [0, 2, 1, 3, 4]                   # oracle order (uL, vB, uR, vT, p) -> LFA order
     assert np.allclose(Be[np.ix_(perm, perm)], lfa.economic_block(s), rtol=1e-12)
     gold = _golden("lfa_smoothing_factor.txt")
-    ws = [0.65, 0.7, 0.73, 0.75, 0.8]
-    mus = [lfa.mu_loc(s, w, nsamp=63) for w in ws]
+    # single damping sampled every 0.01 over [0.62, 0.80]; the optimum is the vertex of
+    # the parabola through the smallest sample and its two neighbours
+    ws = np.round(np.arange(0.62, 0.805, 0.01), 2)
+    mus = np.array([lfa.mu_loc(s, w, nsamp=63) for w in ws])
+    i = int(np.argmin(mus))
+    assert 0 < i < len(ws) - 1                             # an interior minimum
+    m0, m1, m2 = mus[i - 1], mus[i], mus[i + 1]
+    w_opt = ws[i] + 0.01 * 0.5 * (m0 - m2) / (m0 - 2 * m1 + m2)
     v, tol = gold["mu_loc_single_w"]
-    assert abs(min(mus) - v) <= tol                        # eq. muloc_results, one damping
+    assert abs(mus.min() - v) <= tol                       # eq. muloc_results, one damping
     v, tol = gold["optimal_w"]
-    assert abs(ws[int(np.argmin(mus))] - v) <= tol         # optimum near 0.73 (Sec. 5.4)
+    assert abs(w_opt - v) <= tol, w_opt                    # optimum near 0.73 (Sec. 5.4)
     v, tol = gold["mu_loc_wu085_wp065"]
     assert abs(lfa.mu_loc(s, 0.85, 0.85, 0.65) - v) <= tol
 
