@@ -4,12 +4,15 @@ coarsest solve over 8 x 8 subdomains, FP16 tables and local inverses,
 double-float FGMRES).
 
 The oracle's full solves take minutes, so the per-medium iteration counts it
-produced are stored in tests/golden/c2_oracle_iters.json (written by
-tests/golden/make_c2_oracle_iters.py, which calls only oracle/); the GPU
-counts must match them (+-2: the complex64 cycle with FP16 tables and
-local inverses against the FP64 oracle).  The true
-residual of every GPU solution is recomputed with the oracle's own assembled
-complex128 operator, and sampled operator rows are compared element-wise.
+produced are stored in tests/golden/c2_oracle_iters.json and its solutions at
+1088 sampled DOFs per medium in tests/golden/c2_oracle_samples.json (both
+written by tests/golden/make_c2_oracle_iters.py, which calls only oracle/).
+The GPU counts must match them (+-2: the complex64 cycle with FP16 tables and
+local inverses against the FP64 oracle), the GPU solution must lie within
+1e-5 of the oracle's at every sampled DOF (relative to the largest entry of
+the oracle's solution), the true residual of every GPU solution is
+recomputed with the oracle's own assembled complex128 operator, and sampled
+operator rows are compared element-wise.
 """
 import json
 import os
@@ -29,6 +32,7 @@ def test_bench_workload_iterations_and_residuals():
     import bench
     from paper_1806_11277_gb300 import ehs
     gold = json.load(open(os.path.join(HERE, "golden", "c2_oracle_iters.json")))
+    smp = json.load(open(os.path.join(HERE, "golden", "c2_oracle_samples.json")))["media"]
     kw = bench.default_kw()
     assert gold["levels"] == kw["levels"] and gold["alpha"] == kw["alpha"] and gold["w"] == kw["w"]
     assert gold["cycle"] == ("W(1,1)" if kw["cycle"] == 2 else "V(1,1)")
@@ -47,6 +51,14 @@ def test_bench_workload_iterations_and_residuals():
         qo = op.slots_to_dofs(q[it], med.shape)
         uo = op.slots_to_dofs(u[it], med.shape)
         assert np.linalg.norm(qo - K @ uo) / np.linalg.norm(qo) <= 1e-6
+        # the solution against the FP64 oracle's at the stored DOFs
+        m = smp[it]
+        assert m["sigma"] == bench.SIGMAS[it] and m["ndof"] == uo.size
+        idx = np.asarray(m["idx"])
+        ref = np.asarray(m["re"]) + 1j * np.asarray(m["im"])
+        err = np.abs(uo[idx] - ref).max() / m["maxabs"]
+        assert err <= 1e-5, (it, err)
+        assert np.linalg.norm(uo) == pytest.approx(m["norm2"], rel=1e-5)
     # sampled rows of the FP64 operator at full size
     rng = np.random.default_rng(3)
     x = (rng.standard_normal(q.shape) + 1j * rng.standard_normal(q.shape))

@@ -1,6 +1,9 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI.
 
-Tolerances (relative, 2-norm over all items unless stated):
+Every comparison is element-wise: max_i |got_i - ref_i| / max_i |ref_i| over
+the whole vector (boundary faces, absorbing layer and subdomain overlaps
+included), so an error confined to a few rows is not diluted by the norm of
+the rest.  Tolerances:
 * operator apply: 1e-12 in complex128, 1e-5 in complex64;
 * one relaxation sweep / one cycle: 1e-11 in complex128 (a few operator
   applications deep), 1e-5 in complex64;
@@ -45,8 +48,11 @@ def _media_3d(n=16, nmed=1):
     return [synth.layered_3d(n=n, seed=i, corr=3.0, abl=3) for i in range(nmed)]
 
 
-def _rel(a, b):
-    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+def _err(a, b):
+    """Element-wise error of a against the reference b: max |a - b| / max |b|."""
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.abs(a - b).max() / np.abs(b).max())
 
 
 def _oracle_parts(med, alpha=0.0):
@@ -70,7 +76,7 @@ def test_op_apply_fine(case, shifted):
             K = _oracle_parts(med, 0.2 if shifted else 0.0)
             xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), shape)
             ye = op.dofs_to_slots(K @ xe, shape)
-            assert _rel(y[b], ye) <= tol, (prec, b, _rel(y[b], ye))
+            assert _err(y[b], ye) <= tol, (prec, b, _err(y[b], ye))
     S.close()
 
 
@@ -91,7 +97,7 @@ def test_galerkin_levels_match_oracle(case):
                 S.op_apply(xd, yd, level=l)
                 xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), tuple(shp[2:]))
                 ye = op.dofs_to_slots(H.K[l] @ xe, tuple(shp[2:]))
-                assert _rel(yd[b].cpu().numpy(), ye) <= tol, (l, dt, _rel(yd[b].cpu().numpy(), ye))
+                assert _err(yd[b].cpu().numpy(), ye) <= tol, (l, dt, _err(yd[b].cpu().numpy(), ye))
     S.close()
 
 
@@ -116,7 +122,7 @@ def test_smooth_matches_oracle(case):
                 xe = op.slots_to_dofs(torch.from_numpy(x_[it]).to(dt).numpy().astype(np.complex128), gshape)
                 xr = op.dofs_to_slots(H.relax(l, be, xe), gshape)
                 got = xd[it].cpu().numpy()
-                assert _rel(got, xr) <= tol, (l, dt, it, _rel(got, xr))
+                assert _err(got, xr) <= tol, (l, dt, it, _err(got, xr))
     S.close()
 
 
@@ -135,7 +141,7 @@ def test_vcycle_matches_oracle(case, levels):
             H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels,
                              w=[0.75, 0.5, 0.25, 0.25, 0.25][:levels - 1])
             xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape)), shape)
-            assert _rel(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _rel(xd[it].cpu().numpy(), xr))
+            assert _err(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _err(xd[it].cpu().numpy(), xr))
     S.close()
 
 
@@ -181,7 +187,7 @@ def test_fgmres_matches_oracle_2d(prec_name):
             assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
         else:
             assert abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
 
 
 def test_fgmres_config1_host_buffers():
@@ -197,20 +203,27 @@ def test_fgmres_config1_host_buffers():
     xe = spla.spsolve(K.tocsc(), qo)
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"]
-    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
-    assert np.linalg.norm(ug - xe) / np.linalg.norm(xe) <= 1e-5
+    assert _err(ug, xo) <= 1e-5
+    assert _err(ug, xe) <= 1e-5
 
 
 def test_fgmres_multi_rhs_3d():
+    """Two sources of one 3D medium in one batch (complex64 cycle): each source's
+    iteration count within 1 of the oracle's, its true residual <= 1e-6 and its
+    solution within 1e-5 of the oracle's, element by element."""
     ehs = _ehs()
     meds = _media_3d(16, 1)
     q, u, info = _solve_both(meds, 3, ehs.EHS_C64, nrhs=2)
     K = _oracle_parts(meds[0])
+    H = mg.Hierarchy(_oracle_parts(meds[0], 0.2), meds[0].shape, 3)
     for it in range(2):
         qo = op.slots_to_dofs(q[it], meds[0].shape)
         ug = op.slots_to_dofs(u[it], meds[0].shape)
+        xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
         assert np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo) <= 1e-6
         assert info[it]["converged"]
+        assert abs(info[it]["iters"] - io["iters"]) <= 1, (it, info[it], io["iters"])
+        assert _err(ug, xo) <= 1e-5, (it, _err(ug, xo))
 
 
 def test_adjoint_solve():
@@ -243,7 +256,7 @@ def test_dd_precond_matches_oracle(prec_name):
     zd = torch.zeros_like(rd)
     S.dd_precond(rd, zd, prec=prec)
     zo = op.dofs_to_slots(D.apply(op.slots_to_dofs(r[0], med.shape)), med.shape)
-    assert _rel(zd[0].cpu().numpy(), zo) <= tol
+    assert _err(zd[0].cpu().numpy(), zo) <= tol
     S.close()
 
 
@@ -257,7 +270,7 @@ def test_dd_fgmres_iterations_match_oracle():
     xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"]
-    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+    assert _err(ug, xo) <= 1e-5
 
 
 def test_invalid_arguments_rejected():
@@ -304,7 +317,7 @@ def test_wcycle_matches_oracle(case):
             H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, levels,
                              w=[0.75, 0.5, 0.25][:levels - 1])
             xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape), gamma=2), shape)
-            assert _rel(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _rel(xd[it].cpu().numpy(), xr))
+            assert _err(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _err(xd[it].cpu().numpy(), xr))
     S.close()
 
 
@@ -319,7 +332,7 @@ def test_fgmres_wcycle_iterations_match_oracle():
         xo, io = krylov.fgmres(lambda v: K @ v, lambda v: H.cycle(v, gamma=2), qo, m=10)
         ug = op.slots_to_dofs(u[it], med.shape)
         assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
 
 
 def test_dd_fgmres_batched_media_compaction():
@@ -335,7 +348,7 @@ def test_dd_fgmres_batched_media_compaction():
         xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
         ug = op.slots_to_dofs(u[it], med.shape)
         assert abs(info[it]["iters"] - io["iters"]) <= 1, (it, info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
     assert info[0]["iters"] != info[1]["iters"]
 
 
@@ -357,7 +370,7 @@ def test_half_tables_operator(fmt, tol):
             S.op_apply(xd, yd, level=l)
             xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), tuple(shp[2:]))
             ye = op.dofs_to_slots(H.K[l] @ xe, tuple(shp[2:]))
-            err = _rel(yd[b].cpu().numpy(), ye)
+            err = _err(yd[b].cpu().numpy(), ye)
             assert err <= tol, (fmt, l, err)
     S.close()
 
@@ -378,7 +391,7 @@ def test_half_tables_fgmres(fmt):
         ug = op.slots_to_dofs(u[it], med.shape)
         assert info[it]["converged"] and np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo) <= 1e-6
         assert abs(info[it]["iters"] - io["iters"]) <= 2, (fmt, it, info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
@@ -403,7 +416,7 @@ def test_galerkin_rows_launch_shapes_agree(variant, monkeypatch):
                     S.op_apply(xd, yd, level=l)
                     xe = op.slots_to_dofs(xd[b].cpu().numpy().astype(np.complex128), tuple(shp[2:]))
                     ye = op.dofs_to_slots(H.K[l] @ xe, tuple(shp[2:]))
-                    assert _rel(yd[b].cpu().numpy(), ye) <= tol, (variant, fmt, l, dt)
+                    assert _err(yd[b].cpu().numpy(), ye) <= tol, (variant, fmt, l, dt)
         S.close()
     # a full solve with this launch shape keeps the oracle's iteration counts
     q, u, info = _solve_both(meds, 4, ehs.EHS_C64, alpha=0.4, cycle=2)
@@ -436,7 +449,7 @@ def test_full_vanka_smooth_matches_oracle(case):
                 be = op.slots_to_dofs(bd[it].cpu().numpy().astype(np.complex128), gshape)
                 xe = op.slots_to_dofs(torch.from_numpy(x_[it]).to(dt).numpy().astype(np.complex128), gshape)
                 xr = op.dofs_to_slots(H.relax(l, be, xe), gshape)
-                assert _rel(xd[it].cpu().numpy(), xr) <= tol, (l, dt, it, _rel(xd[it].cpu().numpy(), xr))
+                assert _err(xd[it].cpu().numpy(), xr) <= tol, (l, dt, it, _err(xd[it].cpu().numpy(), xr))
     S.close()
 
 
@@ -456,7 +469,7 @@ def test_full_vanka_half_inverses(fmt, tol):
     S.smooth(bd, xd, level=1, nsweeps=1)
     H = mg.Hierarchy(_oracle_parts(meds[0], 0.2), meds[0].shape, 3, economic=False)
     xr = op.dofs_to_slots(H.relax(1, op.slots_to_dofs(b_[0], gshape), op.slots_to_dofs(x_[0], gshape)), gshape)
-    err = _rel(xd[0].cpu().numpy(), xr)
+    err = _err(xd[0].cpu().numpy(), xr)
     assert err <= tol, err
     S.close()
 
@@ -478,7 +491,7 @@ def test_full_vanka_fgmres_matches_oracle(prec_name):
             assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
         else:
             assert abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
 
 
 def test_full_vanka_dd_fgmres():
@@ -493,7 +506,7 @@ def test_full_vanka_dd_fgmres():
     xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
-    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+    assert _err(ug, xo) <= 1e-5
 
 
 # ------------------------------------------------------------- MG-DD, DD-MG-DD
@@ -518,7 +531,7 @@ def test_mgdd_cycle_matches_oracle(case, cyc):
             H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, levels,
                              w=[0.75, 0.5, 0.25][:levels - 1], coarse_dd=(split[:d], ov))
             xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape), gamma=cyc), shape)
-            assert _rel(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _rel(xd[it].cpu().numpy(), xr))
+            assert _err(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _err(xd[it].cpu().numpy(), xr))
     S.close()
 
 
@@ -542,7 +555,7 @@ def test_mgdd_fgmres_matches_oracle(prec_name, fmt):
             assert info[it]["iters"] == io["iters"], (info[it], io["iters"])
         else:
             assert abs(info[it]["iters"] - io["iters"]) <= (1 if fmt < 2 else 2), (info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
 
 
 def test_coarse_fmt_inverse_fgmres():
@@ -558,7 +571,7 @@ def test_coarse_fmt_inverse_fgmres():
         xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
         ug = op.slots_to_dofs(u[it], med.shape)
         assert info[it]["converged"] and abs(info[it]["iters"] - io["iters"]) <= 1, (info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
 
 
 def test_dd_mg_dd_fgmres_matches_oracle():
@@ -573,7 +586,7 @@ def test_dd_mg_dd_fgmres_matches_oracle():
     xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
-    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+    assert _err(ug, xo) <= 1e-5
 
 
 def test_mgdd_rejects_bad_split():
@@ -618,7 +631,7 @@ def test_coarse_solve_and_local_apply(split, fmt, tol):
         H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 3, w=[0.75, 0.5],
                          coarse_dd=((split[0], split[1]), 2) if cdd else None)
         xr = op.dofs_to_slots(H.coarse_solve(op.slots_to_dofs(b_[it], cshape)), cshape)
-        assert _rel(xd[it].cpu().numpy(), xr) <= tol, (it, _rel(xd[it].cpu().numpy(), xr))
+        assert _err(xd[it].cpu().numpy(), xr) <= tol, (it, _err(xd[it].cpu().numpy(), xr))
         Kc = H.K[-1].tocsc()
         if not cdd:
             continue
@@ -629,7 +642,7 @@ def test_coarse_solve_and_local_apply(split, fmt, tol):
             assert sizes[s_] == idx.size
             ze = np.linalg.solve(Kc[idx][:, idx].toarray(), rl[it, s_, :idx.size])
             got = zs[col][it, s_, :idx.size]
-            assert np.linalg.norm(got - ze) <= tol * np.linalg.norm(ze), (it, s_, np.linalg.norm(got - ze) / np.linalg.norm(ze))
+            assert _err(got, ze) <= tol, (it, s_, _err(got, ze))
     S.close()
 
 
@@ -646,7 +659,7 @@ def test_dd_mg_dd_3d_fgmres_matches_oracle():
     xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
     ug = op.slots_to_dofs(u[0], med.shape)
     assert info[0]["iters"] == io["iters"], (info[0], io["iters"])
-    assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+    assert _err(ug, xo) <= 1e-5
 
 
 @pytest.mark.parametrize("fmt", [1, 2])
@@ -682,7 +695,7 @@ def test_mgdd_multi_rhs_local_products(fmt):
             A = Kc[idx][:, idx].toarray()
             for it in range(nrhs):
                 ze = np.linalg.solve(A, rl[0, s_, it, :idx.size])
-                err = np.linalg.norm(z[0, s_, it, :idx.size] - ze) / np.linalg.norm(ze)
+                err = _err(z[0, s_, it, :idx.size], ze)
                 assert err <= tol, (col, it, s_, err)
     S.close()
     q, u, info = _solve_both(meds, 3, ehs.EHS_C64, nrhs=nrhs, alpha=0.4, coarse_dd=(2, 2, 1),
@@ -693,4 +706,80 @@ def test_mgdd_multi_rhs_local_products(fmt):
         xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
         ug = op.slots_to_dofs(u[it], meds[0].shape)
         assert info[it]["converged"] and abs(info[it]["iters"] - io["iters"]) <= 1, (it, info[it], io["iters"])
-        assert np.linalg.norm(ug - xo) / np.linalg.norm(xo) <= 1e-5
+        assert _err(ug, xo) <= 1e-5
+
+
+# ------------------------------------------ uneven DD subdomains (shape groups)
+# Algorithm DD (Sec. 2.3) on splits whose subdomains of one colour have different
+# padded shapes, so that the library batches each colour as several shape groups
+# (one hierarchy per group).  The geometry of both cases is checked on the CPU in
+# tests/test_oracle_dd.py (test_uneven_parity_splits_have_several_shape_groups).
+UNEVEN_2D = dict(split=(3, 3, 1), osplit=(3, 3), overlap=2, pad=4)
+UNEVEN_3D = dict(split=(3, 3, 2), osplit=(2, 3, 3), overlap=3, pad=4)
+
+
+def _med_uneven_2d():
+    """44 x 32 cells (non-square), 4-cell absorbing layer."""
+    return synth.random_2d(n=32, nx=44, sigma=0.4, seed=3, corr=6.0, abl=4)
+
+
+def _med_uneven_3d():
+    """28 x 28 x 16 cells: the top 16 layers of a 28^3 layered medium, two x-forces."""
+    m = synth.layered_3d(n=28, seed=1, corr=4.0, abl=4)
+    sl = slice(0, 16)
+    return synth.Medium(m.lam[sl].copy(), m.mu[sl].copy(), m.rho[sl].copy(), m.omega, m.h, m.abl_cells,
+                        [(0, (6, 14, 10)), (0, (6, 14, 17))], name="layered28x28x16")
+
+
+def _uneven(case):
+    if case == "2d":
+        return _med_uneven_2d(), UNEVEN_2D, 0.2, [0.75, 0.5], 1
+    return _med_uneven_3d(), UNEVEN_3D, 0.5, [0.5, 0.5], 2
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_dd_uneven_split_apply_matches_oracle(case):
+    """One sweep of Algorithm DD over an uneven split (several shape groups per
+    colour): complex128 within 1e-10, complex64 within 5e-5 of the oracle."""
+    ehs = _ehs()
+    med, g, alpha, w, _ = _uneven(case)
+    D = odd.DD(med, g["osplit"], g["overlap"], g["pad"], 3, alpha, w=w)
+    r = _rand_slots(med.shape, 1, 19)
+    zo = op.dofs_to_slots(D.apply(op.slots_to_dofs(r[0], med.shape)), med.shape)
+    for prec, tol in ((ehs.EHS_C128, 1e-10), (ehs.EHS_C64, 5e-5)):
+        S = ehs.solver_for(med, levels=3, alpha=alpha, w=w, precond=ehs.EHS_PRECOND_DD, dd=g["split"],
+                           dd_overlap=g["overlap"], dd_pad=g["pad"], prec=prec)
+        rd = torch.from_numpy(r).cuda()
+        zd = torch.zeros_like(rd)
+        S.dd_precond(rd, zd, prec=prec)
+        assert _err(zd[0].cpu().numpy(), zo) <= tol, (case, prec, _err(zd[0].cpu().numpy(), zo))
+        S.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+@pytest.mark.parametrize("form", ["dd-mg", "dd-mg-dd"])
+def test_dd_uneven_split_fgmres_matches_oracle(case, form):
+    """FGMRES preconditioned by Algorithm DD on an uneven split (DD-MG with exact
+    subdomain coarsest solves, or DD-MG-DD with the subdomain coarsest grids split
+    2 x 2 (x 1)), in 3D with two sources in one batch: the oracle's iteration count
+    exactly in complex128 (+-1 in complex64), true residual <= 1e-6, solution
+    within 1e-5 of the oracle's element by element, for every source."""
+    ehs = _ehs()
+    med, g, alpha, w, nrhs = _uneven(case)
+    d = len(med.shape)
+    cdd = ((2, 2, 1)[:d], 1) if form == "dd-mg-dd" else None
+    D = odd.DD(med, g["osplit"], g["overlap"], g["pad"], 3, alpha, w=w, coarse_dd=cdd)
+    extra = dict(coarse_dd=(2, 2, 1), coarse_dd_overlap=1) if cdd else {}
+    for prec in (ehs.EHS_C128, ehs.EHS_C64):
+        q, u, info = _solve_both([med], 3, prec, nrhs=nrhs, alpha=alpha, w=w, precond=ehs.EHS_PRECOND_DD,
+                                 dd=g["split"], dd_overlap=g["overlap"], dd_pad=g["pad"], **extra)
+        for it in range(nrhs):
+            qo = op.slots_to_dofs(q[it], med.shape)
+            xo, io = krylov.fgmres(lambda v: D.K @ v, D.apply, qo, m=10)
+            ug = op.slots_to_dofs(u[it], med.shape)
+            assert info[it]["converged"] and np.linalg.norm(qo - D.K @ ug) / np.linalg.norm(qo) <= 1e-6
+            if prec == ehs.EHS_C128:
+                assert info[it]["iters"] == io["iters"], (case, form, it, info[it], io["iters"])
+            else:
+                assert abs(info[it]["iters"] - io["iters"]) <= 1, (case, form, it, info[it], io["iters"])
+            assert _err(ug, xo) <= 1e-5, (case, form, prec, it, _err(ug, xo))

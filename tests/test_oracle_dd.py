@@ -135,3 +135,28 @@ def test_near_equal_splits_agree():
             sizes = np.diff(e)
             assert e[0] == 0 and e[-1] == n and sizes.max() - sizes.min() <= 1
             assert np.all(np.diff(sizes) <= 0)
+
+
+def _shape_groups(shape, nsub, overlap, pad, levels):
+    """Padded subdomain shapes of each colour (Algorithm DD geometry)."""
+    splits = [dd.split_axis(shape[a], nsub[a]) for a in range(len(shape))]
+    groups = {}
+    for sidx in itertools.product(*[range(n) for n in nsub]):
+        sd = dd.Subdomain(shape, sidx, splits, overlap, pad, 2 ** (levels - 1))
+        groups.setdefault(sd.colour, set()).add(sd.shape)
+    return groups
+
+
+def test_uneven_parity_splits_have_several_shape_groups():
+    """The uneven splits of the GPU parity tests (44 x 32 split 3 x 3, overlap 2,
+    pad 4; 28 x 28 x 16 split 3 x 3 x 2, overlap 3, pad 4; 3 levels) give some
+    colour several padded shapes, so the library's per-colour shape groups
+    (one batched hierarchy per shape) are exercised, and every shape divides by
+    the coarsening factor."""
+    g2 = _shape_groups((32, 44), (3, 3), 2, 4, 3)
+    g3 = _shape_groups((16, 28, 28), (2, 3, 3), 3, 4, 3)
+    assert max(len(v) for v in g2.values()) == 4 and len(g2) == 4
+    assert max(len(v) for v in g3.values()) == 4 and len(g3) == 8
+    for g in (g2, g3):
+        for shapes in g.values():
+            assert all(s % 4 == 0 for sh in shapes for s in sh)
