@@ -92,7 +92,11 @@ typedef struct {
   int maxit;             /* max preconditioner applications per solve */
   double tol;            /* relative residual of the mixed system */
   int precond;           /* ehs_precond */
-  int prec;              /* ehs_prec of the preconditioner (the Krylov solve is FP64) */
+  int prec;              /* ehs_prec of the preconditioner cycle.  EHS_C128: complex128 cycle
+                            and FP64 Krylov solve (the plain FP64 form).  EHS_C64: complex64
+                            cycle and a double-float Krylov solve (pairs of FP32 numbers,
+                            about 48-bit significands: FP64-class, not IEEE FP64), with the
+                            true residual recomputed in double-float */
   int nrhs;              /* right-hand sides per medium; items = nmedia * nrhs */
   int dd[3];             /* subdomains per axis (DD only) */
   int dd_overlap;        /* overlap in cells (DD only) */
@@ -204,28 +208,36 @@ ehs_status ehs_gradient(ehs_ctx* ctx, const void* x, const void* w, double* g_la
                         double* g_rho);
 
 /* Allocation-free fine-level smoothing.  The paper has no counterpart: this
- * entry point exists for callers that cannot allocate device memory when
- * they need it -- code inside a CUDA stream capture (cudaMalloc cannot be
- * captured), host callbacks, or runtimes whose memory pool forbids extra
- * device allocations -- and therefore cannot build a context with
- * ehs_create.  It performs nsweeps red-black economic cell-wise relaxation
- * sweeps of the shifted fine operator K_s (the same kernels and result as
- * ehs_smooth on level 0 of a context built from the same problem) without any
- * cudaMalloc / cudaFree or allocating library call.
- *   prob: as for ehs_create, but lambda, mu, rho must be DEVICE pointers and
- *     nmedia <= 32; every n[k] even.  nrhs: items per medium; items =
+ * entry point exists for callers that may not allocate device memory when
+ * they need to relax a vector, and therefore cannot build a context with
+ * ehs_create -- for example a host program that gives all of the device
+ * memory to its own pool at start-up and forbids the libraries it loads to
+ * call cudaMalloc (so that its footprint stays fixed and known), or a
+ * latency-bound loop that must not stall on the allocator (cudaFree waits for
+ * the whole device).  It performs nsweeps red-black economic cell-wise
+ * relaxation sweeps of the shifted fine operator K_s (the same kernels and
+ * result as ehs_smooth on level 0 of a context built from the same problem)
+ * without any cudaMalloc / cudaFree or allocating library call.
+ *   prob: as for ehs_create, but lambda, mu, rho must be DEVICE pointers of
+ *     the current device and nmedia <= 32; every n[k] even; 0 <= abl_cells
+ *     <= min n[k] / 2.  The media VALUES are not checked here (ehs_create
+ *     checks them): rho <= 0, lambda + mu <= 0 or non-finite entries give
+ *     non-finite x instead of an error.  nrhs: items per medium; items =
  *     nmedia * nrhs.  alpha: shift; w, wp: damping of the u and p unknowns.
- *   prec: EHS_C64 or EHS_C128; b, x: device vectors of that precision in the
- *     slot layout (x is relaxed in place).  stream: a cudaStream_t or NULL.
- * Scratch: the cell coefficients and the ping-pong vector live in one static
- *   32 MiB device array per GPU, held from library load until process exit;
- *   problems needing more return EHS_ERR_OOM.  Every call shares that array
- *   (each call clears and rewrites what it uses), so calls whose GPU work can
- *   overlap -- other streams or host threads -- race and must be serialised
- *   by the caller.  The first call on each device looks up the array's device
- *   address; make that first call before any stream capture begins.
- * Returns EHS_ERR_ARG for invalid arguments or host pointers, EHS_ERR_OOM for
- *   a problem larger than the scratch, EHS_ERR_CUDA if a launch fails. */
+ *   prec: EHS_C64 or EHS_C128; b, x: device vectors of that precision on the
+ *     current device, in the slot layout (x is relaxed in place).
+ *   stream: a cudaStream_t or NULL.
+ * Scratch: the cell coefficients, the frequencies and the ping-pong vector
+ *   live in one static 32 MiB device array per GPU, held from library load
+ *   until process exit; problems needing more return EHS_ERR_OOM.  Every call
+ *   shares that array (each call clears and rewrites what it uses), so calls
+ *   whose GPU work can overlap -- other streams or host threads -- race and
+ *   must be serialised by the caller.  The first call on each device looks up
+ *   the array's device address; make that first call before any stream
+ *   capture begins.
+ * Returns EHS_ERR_ARG for invalid arguments, host pointers or memory of
+ *   another device, EHS_ERR_OOM for a problem larger than the scratch,
+ *   EHS_ERR_CUDA if a launch fails. */
 ehs_status ehs_fine_smooth_noalloc(const ehs_problem* prob, int nrhs, double alpha, double w,
                                    double wp, int nsweeps, int prec, const void* b, void* x,
                                    void* stream);

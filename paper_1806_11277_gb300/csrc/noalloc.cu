@@ -1,14 +1,15 @@
 // Allocation-free fine-level smoothing (ehs_fine_smooth_noalloc in ehs.h).
 //
 // Who needs this: callers that may not allocate device memory at the point
-// where they want to relax a vector -- for example code running inside a
-// CUDA stream capture (cudaMalloc is not capturable), a host callback, or an
-// embedding runtime whose memory pool forbids extra device allocations.
-// ehs_create allocates a whole hierarchy, so such a caller cannot obtain a
-// context; this entry point needs none.  It keeps its scratch (the matrix-free
-// cell coefficients and the red-black ping-pong vector) in one file-scope
-// device array of fixed size that every GPU loading the library holds until
-// the process exits.
+// where they want to relax a vector, and so cannot build a context (ehs_create
+// allocates a whole hierarchy).  Examples: a host program that hands all of
+// the device memory to its own pool at start-up and forbids the libraries it
+// loads to call cudaMalloc, so that its footprint stays fixed and known; and
+// latency-bound loops that must not stall on the allocator (cudaFree waits for
+// the whole device).  This entry point keeps its scratch (the matrix-free cell
+// coefficients, the per-medium frequencies and the red-black ping-pong vector)
+// in one file-scope device array of fixed size that every GPU loading the
+// library holds until the process exits, and calls no allocating routine.
 //
 // The array is shared by every call on a device: calls whose GPU work
 // overlaps (different streams, or different host threads) race on it and
@@ -31,17 +32,31 @@ constexpr int kMaxMedia = 32;
 void* g_scratch_addr[kMaxDev] = {nullptr};
 std::mutex g_scratch_mu;
 
+// the per-medium frequencies, passed to the device by value as a kernel
+// argument (no host-to-device copy from host memory that the call owns)
+struct Omegas {
+  double w[kMaxMedia];
+};
+
+__global__ void k_put_omegas(Omegas om, int n, double* dst) {
+  const int i = threadIdx.x;
+  if (i < n) dst[i] = om.w[i];
+}
+
 // the status alone reports the failure (this entry point has no context to
 // hold a message); the text documents each case at the call site
 inline ehs_status fail(ehs_status st, const char* /*why*/) { return st; }
 
-bool on_device(const void* p) {
+// device memory of the current device (or managed memory); anything else --
+// host memory, or memory of another GPU -- is refused
+bool on_this_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 template <typename T>
@@ -63,15 +78,15 @@ ehs_status run(const ehs_problem* P, int nrhs, double alpha, double w, double wp
   double* d_om = reinterpret_cast<double*>(scratch);
   Coef4<T>* cf = reinterpret_cast<Coef4<T>*>(scratch + om_bytes);
   C* t = reinterpret_cast<C*>(scratch + om_bytes + cb);
-  double om[kMaxMedia];
-  for (int m = 0; m < P->nmedia; ++m) om[m] = P->omegas ? P->omegas[m] : P->omega;
+  Omegas om{};
+  for (int m = 0; m < P->nmedia; ++m) om.w[m] = P->omegas ? P->omegas[m] : P->omega;
   for (int m = 0; m < P->nmedia; ++m)
-    if (!std::isfinite(om[m]) || !(om[m] > 0)) return fail(EHS_ERR_ARG, "omega must be positive and finite");
+    if (!std::isfinite(om.w[m]) || !(om.w[m] > 0)) return fail(EHS_ERR_ARG, "omega must be positive and finite");
   // the previous call's contents are still there: the frequencies are
   // overwritten, the coefficients fully rewritten, and the ping-pong vector
   // cleared so that its boundary slots (never written by a sweep) are zero
-  if (cudaMemcpyAsync(d_om, om, P->nmedia * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(t, 0, vec_bytes, s) != cudaSuccess)
+  k_put_omegas<<<1, kMaxMedia, 0, s>>>(om, P->nmedia, d_om);
+  if (cudaMemsetAsync(t, 0, vec_bytes, s) != cudaSuccess)
     return fail(EHS_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
   launch_fine_coef<T>(g, P->nmedia, P->lambda, P->mu, P->rho, d_om, P->abl_cells, P->abl_max,
                       P->gamma_add, cf, s);
@@ -91,18 +106,23 @@ extern "C" ehs_status ehs_fine_smooth_noalloc(const ehs_problem* P, int nrhs, do
                                               void* stream) {
   if (!P || !b || !x) return fail(EHS_ERR_ARG, "null argument");
   if (P->dim != 2 && P->dim != 3) return fail(EHS_ERR_ARG, "dim must be 2 or 3");
-  for (int k = 0; k < P->dim; ++k)
+  int nmin = P->n[0];
+  for (int k = 0; k < P->dim; ++k) {
     if (P->n[k] < 2 || P->n[k] % 2) return fail(EHS_ERR_ARG, "every n[k] must be even and >= 2");
+    nmin = P->n[k] < nmin ? P->n[k] : nmin;
+  }
+  if (P->abl_cells < 0 || 2 * P->abl_cells > nmin)
+    return fail(EHS_ERR_ARG, "abl_cells must be in [0, min n[k] / 2]");
   if (P->nmedia < 1 || P->nmedia > kMaxMedia || nrhs < 1 || nsweeps < 0)
     return fail(EHS_ERR_ARG, "bad nmedia (1..32), nrhs or nsweeps");
   if (!(P->h > 0)) return fail(EHS_ERR_ARG, "h must be positive");
   if (prec != EHS_C64 && prec != EHS_C128) return fail(EHS_ERR_ARG, "prec must be EHS_C64 or EHS_C128");
-  if (!P->lambda || !P->mu || !P->rho || !on_device(P->lambda) || !on_device(P->mu) ||
-      !on_device(P->rho) || !on_device(b) || !on_device(x))
-    return fail(EHS_ERR_ARG, "media, b and x must be device pointers");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
     return fail(EHS_ERR_CUDA, "no current CUDA device");
+  if (!P->lambda || !P->mu || !P->rho || !on_this_device(P->lambda, dev) || !on_this_device(P->mu, dev) ||
+      !on_this_device(P->rho, dev) || !on_this_device(b, dev) || !on_this_device(x, dev))
+    return fail(EHS_ERR_ARG, "media, b and x must be memory of the current device");
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
