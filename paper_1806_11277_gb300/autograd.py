@@ -7,6 +7,11 @@ output the gradient g = dL/dRe(x) + i dL/dIm(x) (twice the conjugate
 Wirtinger derivative), so that dL = Re(g^H dx); hence
     w = K^{-H} g,  grad_q = w,  dL/dm = -Re(w^H dK/dm x).
 All arithmetic runs in libehs.so; this module only moves tensors.
+
+The solver context built by the forward pass lives as long as the autograd
+graph that holds it (it is released with the graph, when the last reference to
+the output goes away), so backward may run more than once with
+retain_graph=True.
 """
 from __future__ import annotations
 
@@ -37,7 +42,6 @@ class ElasticHelmholtzSolve(torch.autograd.Function):
         w = torch.zeros_like(x)
         S.adjoint_solve(gx.contiguous(), w)
         gl, gm, gr = S.gradient(x, w)
-        S.close()
         need = ctx.needs_input_grad
         to = lambda t: t.to(ctx.mdev)
         return (to(gl) if need[0] else None, to(gm) if need[1] else None, to(gr) if need[2] else None,

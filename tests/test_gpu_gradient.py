@@ -112,3 +112,32 @@ def test_autograd_matches_finite_differences():
             g = float(t.grad[cell])
             scale = float(t.grad.abs().max())
             assert abs(fd - g) <= 2e-4 * scale, (name, cell, fd, g, scale)
+
+
+def test_autograd_backward_twice_and_release():
+    """backward with retain_graph=True may run twice (the solver context lives
+    with the graph): the second pass adds the same gradient again; the context
+    is released with the graph."""
+    import gc
+    import weakref
+    from paper_1806_11277_gb300 import autograd as ag
+    meds = _meds(32)[:1]
+    shape = meds[0].shape
+    lam = torch.tensor(meds[0].lam[None], dtype=torch.float64, requires_grad=True)
+    mu = torch.tensor(meds[0].mu[None], dtype=torch.float64, requires_grad=True)
+    rho = torch.tensor(meds[0].rho[None], dtype=torch.float64, requires_grad=True)
+    q = np.zeros((1, 3) + shape, dtype=np.complex128)
+    q[0, 0, 8, 16] = 1.0
+    qd = torch.from_numpy(q).cuda()
+    x = ag.solve(lam, mu, rho, qd, [meds[0].omega], 1.0, 6, levels=3, prec=0)
+    J = (x[0, 0, 9, 6:26].abs() ** 2).sum()
+    J.backward(retain_graph=True)
+    g1 = [t.grad.clone() for t in (lam, mu, rho)]
+    J.backward()
+    for t, g in zip((lam, mu, rho), g1):
+        assert torch.allclose(t.grad, 2 * g, rtol=1e-9, atol=1e-12 * float(g.abs().max()))
+    S_ref = weakref.ref(x.grad_fn.S) if hasattr(x.grad_fn, "S") else None
+    del x, J
+    gc.collect()
+    if S_ref is not None:
+        assert S_ref() is None
