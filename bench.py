@@ -67,17 +67,30 @@ def default_kw():
 
 
 # Roofline kernel of the default line: the MG-DD coarsest local products (k_dense_apply_v,
-# the largest share of the solve, 26% of the ncu launch list); per launch (one colour) the
-# live n_s x n_s entries of every subdomain inverse of the colour (4 B each, FP16 pairs) + r and z
+# the largest share of the solve in the ncu launch list); per launch (one colour) the live
+# n_s x n_s entries of every subdomain inverse of the colour (4 B each, FP16 pairs) + r and z
 ROOF = "coarse"
 ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 16 subdomain inverses "
                "x 4 media)")
 # Galerkin level-1 apply (k_st_rows): 87 stencil coefficients (FP16 pairs, 4 B) + x 24 + y 24
 ST_ROWS_L1_BYTES_PER_CELL = 87 * 4 + 24 + 24
 # DRAM read + write bytes of one roofline-kernel launch (one colour) of the default line, from an
-# ncu capture of the kernel as it stands (None whenever the kernel changes): mean of 7 warm
-# launches, profiles/k_dense_apply_v_mgdd_512x512.md
+# ncu capture of the kernel as it stands (None whenever the kernel changes): mean of 7 warm launches
 ROOF_TRAFFIC_C2 = 450.84e6 + 5.88e6
+
+# Stencil kernels of the default line (the metric's "stencil HBM GB/s"), each timed through the
+# C ABI call that launches it alone: algorithmic bytes per cell of the level it runs on (each
+# input read once, each output written once; complex64 vectors 8 B per value, 3 values per cell).
+#  fine sweep: one launch of the fused red-black sweep, x 24 + b 24 + coefficients 16 + x' 24
+#  fine residual + restriction: one fused launch, x 24 + b 24 + coefficients 16 + coarse r 6
+#  level-1 rows: the Galerkin residual pass (FP16 table of 87 coefficients x 4 B) + x 24 + y 24
+#  level-1 prolongation: x += P e, x 24 read + 24 written + e 6 (per level-1 cell)
+STENCIL = (
+    ("k_fine_sweep_tile (fine level, whole red-black sweep)", "sweep", 0, 88),
+    ("k_fine_resid_restrict_tile (fine residual + restriction)", "resid_restrict", 0, 70),
+    ("k_st_rows2<float,__half2,2,1> (Galerkin level 1, all rows, FP16 table)", "rows", 1, 87 * 4 + 48),
+    ("k_prolong_add<float,2> (level 2 -> level 1 correction)", "prolong", 1, 54),
+)
 
 
 def media(seed=0):
@@ -258,8 +271,10 @@ _ORACLE_CACHE = {}
 
 
 def oracle_sample(meds, iters_per_sample, which=0):
-    """Oracle (as it stands) FGMRES iterations on one medium; seconds per iteration.
-    The medium's operator and hierarchy are built once and reused (setup is not timed)."""
+    """Oracle (as it stands) FGMRES on one medium from a zero guess, iters_per_sample preconditioner
+    applications (10 = one whole restart cycle: ten Arnoldi steps with their CGS2 passes, the
+    x-update and the true residual); seconds per iteration.  The medium's operator and hierarchy
+    are built once and reused (setup is not timed)."""
     from oracle import krylov, multigrid as mg, operators as op
     k = which % len(meds)
     if k not in _ORACLE_CACHE:
@@ -333,12 +348,74 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores_used(_CPU_METER),
                          "threads_available": cpu_threads(), "kind": "oracle",
                          "sample": (f"{args.ref_iters} oracle FGMRES iterations per step on one medium "
-                                    f"(media cycled), seconds/iteration x the oracle's own mean iteration "
-                                    f"count per solve ({mean_iters}) from tests/golden/c2_oracle_iters.json")},
+                                    f"(media cycled; 10 = one whole restart cycle with its x-update and true "
+                                    f"residual), setup excluded, seconds/iteration x the oracle's own mean "
+                                    f"iteration count per solve ({mean_iters}) from tests/golden/c2_oracle_iters.json")},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _dofs_2d(v):
+    """Slot layout (3, n_y, n_x) -> the oracle's DOF order (u_x interior faces, u_y interior faces,
+    p; x fastest): index marshalling only, for comparing with stored oracle samples."""
+    return np.concatenate([v[0][:, 1:].ravel(), v[1][1:, :].ravel(), v[2].ravel()])
+
+
+def err_vs_oracle(u):
+    """Per medium: the GPU solution against the FP64 oracle's at the DOFs stored in
+    tests/golden/c2_oracle_samples.json (written by a script that calls only oracle/):
+    max |u - u_oracle| / max |u_oracle| over the samples (relative to the largest entry of the
+    oracle's whole solution), and the 2-norm over the samples relative to theirs."""
+    p = os.path.join(ROOT, "tests", "golden", "c2_oracle_samples.json")
+    try:
+        with open(p) as f:
+            media_s = json.load(f)["media"]
+    except Exception:
+        return None
+    out = []
+    for it, m in enumerate(media_s):
+        x = _dofs_2d(u[it])
+        idx = np.asarray(m["idx"])
+        ref = np.asarray(m["re"]) + 1j * np.asarray(m["im"])
+        d = x[idx] - ref
+        out.append({"sigma": m["sigma"], "max_rel": float(np.abs(d).max() / m["maxabs"]),
+                    "l2_rel_samples": float(np.linalg.norm(d) / np.linalg.norm(ref)), "samples": int(idx.size)})
+    return {"reference": "FP64 oracle solutions at 1e-6 residual, sampled (tests/golden/c2_oracle_samples.json)",
+            "media": out}
+
+
+def fp64_form_sample(meds, q_host, stream, dev, flush, steps=3):
+    """The same workload in the plain FP64 GPU form (complex128 cycle, FP64 tables and local
+    inverses, FP64 FGMRES): a short timed sample of solves/s with the same timing rules."""
+    import torch
+    from paper_1806_11277_gb300 import ehs
+    kw = default_kw()
+    kw.update(prec=0, coarse_fmt=0, coef_half=0)
+    with torch.cuda.stream(stream):
+        S = ehs.solver_for(meds, stream=stream.cuda_stream, **kw)
+    qd = torch.from_numpy(q_host).to(dev)
+    ud = torch.zeros_like(qd)
+    info = S.fgmres_solve(qd, ud)          # warm-up (graph capture)
+    times = []
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = S.fgmres_solve(qd, ud)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    S.close()
+    err = err_vs_oracle(ud.cpu().numpy())
+    return {"value": len(meds) * steps / sum(times), "unit": "solves/s", "steps": steps,
+            "iters": [i["iters"] for i in info], "dtype": "c128",
+            "err_vs_oracle": err["media"] if err else None,
+            "note": "plain FP64 GPU form of the same workload and solver (complex128 cycle, FP64 Galerkin "
+                    "tables and MG-DD local inverses, FP64 FGMRES); one warm-up solve, CUDA events, L2 flushed"}
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -466,6 +543,53 @@ def run_gpu(args):
         achieved = alg / t_launch / 1e9
         return t_launch, alg, achieved
 
+    def stencil_roofline():
+        """Achieved HBM GB/s of each stencil kernel of the default line (STENCIL), timed with CUDA
+        events on the solver's stream around the C ABI call that launches it, queued behind a
+        read-only 512 MiB pass that empties L2, median of samples.  The sweep is timed as ehs_smooth with two
+        sweeps (two launches, x -> t -> x; a single sweep would add a copy back into x), reported
+        per launch."""
+        if cfg is not None:
+            return None
+        peak, _ = peaks()
+        shp = [S.level_shape(lv) for lv in range(kw["levels"])]
+
+        def rnd(lv):
+            v = torch.randn(shp[lv], dtype=torch.complex64, device=dev)
+            v[:, 0, :, 0] = 0           # Dirichlet slots
+            v[:, 1, 0, :] = 0
+            return v
+        x0, b0, x1, y1, e2 = rnd(0), rnd(0), rnd(1), rnd(1), rnd(2)
+        rc1 = torch.zeros_like(x1)
+        calls = {"sweep": (lambda: S.smooth(b0, x0, level=0, nsweeps=2), 2),
+                 "resid_restrict": (lambda: S.residual_restrict(b0, x0, rc1, level=0), 1),
+                 "rows": (lambda: S.op_apply(x1, y1, level=1), 1),
+                 "prolong": (lambda: S.prolong_add(e2, x1, level=1), 1)}
+        out = []
+        for name, what, lvl, bpc in STENCIL:
+            fn, nl = calls[what]
+            ncell = int(np.prod(shp[lvl][2:])) * S.items
+            kt = []
+            for _ in range(args.kernel_reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    # a read-only 512 MiB pass: it evicts the kernel's data from L2 without leaving
+                    # dirty lines whose write-back would land inside the timed launch, and runs
+                    # long enough that the host-side call is queued before the events
+                    flush.sum()
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                e1.synchronize()
+                kt.append(e0.elapsed_time(e1) / 1e3 / nl)
+            t = statistics.median(kt)
+            gbs = bpc * ncell / t / 1e9
+            out.append({"kernel": name, "bytes_per_cell": bpc, "cells_per_launch": ncell,
+                        "alg_bytes_per_launch": bpc * ncell, "launch_us": t * 1e6, "achieved": gbs,
+                        "unit": "GB/s", "frac": gbs / peak, "launches_per_sample": nl})
+        return out
+
     if args.roofline_only:              # the roofline kernel loop alone (for ncu captures)
         t_launch, alg, achieved = roofline()
         print(json.dumps({"roofline_kernel_us": t_launch * 1e6, "alg_bytes": alg, "achieved_gbs": achieved}))
@@ -563,6 +687,8 @@ def run_gpu(args):
 
     t_launch, alg, achieved = roofline()
     peak, peak_kind = peaks()
+    stencil = stencil_roofline()
+    err_o = err_vs_oracle(ud.cpu().numpy()) if cfg is None else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -571,6 +697,12 @@ def run_gpu(args):
         # arithmetic of the path: complex64 preconditioner with a double-float (FP32-pair) Krylov
         # solve in the mixed form, complex128 everywhere in the plain FP64 form
         "dtype": "c128" if kw.get("prec", 1) == 0 else "c64+df64", "data": "synthetic",
+        "arithmetic": ("complex128 cycle and FP64 FGMRES (plain FP64 form)" if kw.get("prec", 1) == 0 else
+                       "complex64 cycle with FP32 accumulation; Galerkin tables stored as %s, coarsest "
+                       "inverses as %s; FGMRES vectors, operator, Arnoldi and true residual in double-float "
+                       "(FP32 pairs, about 48-bit significands; no IEEE FP64 on the path)" % (
+                           ["complex64", "FP16 pairs", "BF16 pairs"][kw.get("coef_half", 0)],
+                           ["double-float", "complex64", "FP16 pairs", "BF16 pairs"][kw.get("coarse_fmt", 0)])),
         "config": {"name": args.config, "workload": WORKLOAD if cfg is None else cfg["workload"],
                    "grid": list(meds[0].shape), "media": nsolve,
                    "sigmas": list(SIGMAS) if cfg is None else None, "levels": kw["levels"],
@@ -599,6 +731,12 @@ def run_gpu(args):
                      "one launch per event pair, queued behind a 512 MiB L2-flushing write"},
         "clocks": clk,
     }
+    if stencil:
+        line["roofline"]["stencil"] = stencil
+    if err_o:
+        line["err_vs_oracle"] = err_o
+    if cfg is None and not args.no_fp64_form:
+        line["fp64_form"] = fp64_form_sample(meds, q_host, stream, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu and cfg is None:
         iters_o = oracle_iteration_counts()
         t_it = []
@@ -612,8 +750,9 @@ def run_gpu(args):
         line["cpu_baseline"] = {
             "value": cpu_val, "unit": "solves/s", "cores": cores_used(_CPU_METER),
             "threads_available": cpu_threads(), "kind": "oracle",
-            "sample": (f"{args.cpu_iters} oracle FGMRES iterations on each of the 4 media; "
-                       f"seconds/iteration x mean iterations per solve ({mean_iters:.1f}, {src})")}
+            "sample": (f"{args.cpu_iters} oracle FGMRES iterations (one whole restart cycle: Arnoldi steps, "
+                       f"x-update and true residual) on each of the 4 media, setup excluded; seconds/iteration "
+                       f"x mean iterations per solve ({mean_iters:.1f}, {src})")}
     if rank == 0 and world == 1 and not args.no_cpu and args.config == "c1":
         # the 64x64 case is small enough for whole oracle solves (3-level V(1,1), alpha 0.2)
         from oracle import krylov, multigrid as mg, operators as op
@@ -651,12 +790,15 @@ def main():
     ap.add_argument("--config", default="c2", choices=["c2"] + sorted(OTHER),
                     help="c2: the 512x512 four-Poisson-ratio line (default); c3: 3D 128^3 DD-MG; c1: 64x64")
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--cpu-iters", type=int, default=4)
-    ap.add_argument("--ref-iters", type=int, default=4)
+    ap.add_argument("--cpu-iters", type=int, default=10,
+                    help="oracle iterations per medium in the CPU baseline (10 = one whole restart cycle)")
+    ap.add_argument("--ref-iters", type=int, default=10)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the roofline kernel from an ncu capture "
                          "(default: the capture of the current kernel for the c2 line)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the short timed sample of the plain FP64 GPU form of the default line")
     ap.add_argument("--roofline-only", action="store_true",
                     help="skip the solves; only the roofline kernel timing loop (for ncu captures)")
     ap.add_argument("--profile-step", action="store_true",

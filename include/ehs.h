@@ -164,6 +164,22 @@ ehs_status ehs_smooth(ehs_ctx* ctx, int level, int nsweeps, int prec, const void
  * from a zero initial guess.  Device pointers, fine-grid slot layout. */
 ehs_status ehs_vcycle(ehs_ctx* ctx, int prec, const void* b, void* x);
 
+/* Fine-to-coarse half of the coarse-grid correction (Algorithm TwoCycle step 2):
+ *   rc = P_l^T (b - K_l x)
+ * for every item: the residual of the shifted operator of level l restricted to
+ * level l+1 with the transpose of the staggered bilinear prolongation (Sec. 3).
+ * 0 <= level <= levels-2.  b, x: device vectors of level l, rc: device vector of
+ * level l+1 (slot layouts; rc's Dirichlet slots are written as zero).  In the
+ * complex64 form on a 2D fine level whose sizes split into the fused kernel's
+ * tiles (n_x divisible by 32, n_y by 16) this is one pass that never writes the
+ * fine residual; otherwise the residual goes through the level's scratch.  MG
+ * contexts only. */
+ehs_status ehs_residual_restrict(ehs_ctx* ctx, int level, int prec, const void* b, const void* x, void* rc);
+/* Coarse-to-fine half (Algorithm TwoCycle step 4): x += P_l ec for every item;
+ * ec: device vector of level l+1, x: device vector of level l, updated in place.
+ * 0 <= level <= levels-2.  MG contexts only. */
+ehs_status ehs_prolong_add(ehs_ctx* ctx, int level, int prec, const void* ec, void* x);
+
 /* Coarsest-level solve (Algorithm TwoCycle step 3 at the last level): x = K_c^{-1} b through
    the stored dense inverse (exact), or by the MG-DD sweep of Sec. 4 when opts.coarse_dd splits
    the coarsest grid.  b, x: device, [items][(d+1) * ncell_c] complex of prec (ehs_level_len of

@@ -88,6 +88,7 @@ struct Hier {
   int coarse_fmt = 0;          // coarsest inverses of the complex64 cycle: 0 df64, 1 c64, 2 FP16, 3 BF16
   CoarseDD cdd;
   bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
+  bool fused0 = false;         // 2D complex64 cycle: fused fine-level sweep and residual + restriction
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
   void* cfdf = nullptr;        // df64 coefficients (outer-Krylov operator of the global problem)
@@ -386,6 +387,10 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
   if (herr & EHS_DEVERR_SINGULAR) throw ArgError("coarsest Galerkin operator is singular");
   if (precs & 2) autotune_rows<float>(c, H);
   if (precs & 1) autotune_rows<double>(c, H);
+  // the fused fine-level kernels serve the economic 2D complex64 cycle on grids that split into
+  // their tiles; EHS_FINE_UNFUSED=1 selects the per-colour kernels instead (tests compare both)
+  const char* uf = getenv("EHS_FINE_UNFUSED");
+  H.fused0 = (precs & 2) && d == 2 && !H.full && fine_tiles_fit(H.g0) && !(uf && uf[0] == '1');
   if (const char* f = getenv("EHS_ROWS_VARIANT")) {   // fixed launch shape (tests)
     const int v = atoi(f);
     if (v >= 0 && v < ST_ROWS_VARIANTS)
@@ -550,6 +555,44 @@ void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typenam
 
 template <typename T>
 void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typename CT<T>::type* x,
+               bool guess);
+
+// Fine level of the 2D complex64 cycle with the fused kernels: pre-smoothing
+// sweeps (the first from the zero guess without reading x), residual and
+// restriction in one pass, the coarse cycle, and post-smoothing sweeps whose
+// first adds the prolongated correction while staging x.  Each sweep writes the
+// buffer it does not read (x or the level's t), chosen so that the last lands
+// in x.
+void cycle_fine_fused(ehs_ctx* c, Hier& H, const float2* b, float2* x, bool guess) {
+  Level& L = H.lv[0];
+  Level& Lc = H.lv[1];
+  float2* t = (float2*)L.ws[1][2];
+  float2* bc = (float2*)Lc.ws[1][0];
+  float2* xc = (float2*)Lc.ws[1][1];
+  const float wu = (float)L.w, wp = (float)(L.w * H.wp_ratio);
+  const float2* cur = guess ? x : nullptr;            // nullptr: the zero iterate
+  float2* out = guess ? t : (((H.nu1 + H.nu2) & 1) ? x : t);
+  auto sweep = [&](const float2* ec) {
+    launch_fine_sweep_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.h, H.alpha, wu, wp, b, cur, ec, out, c->s);
+    cnt(); post();
+    cur = out;
+    out = out == t ? x : t;
+  };
+  for (int s = 0; s < H.nu1; ++s) sweep(nullptr);
+  launch_fine_resid_restrict_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.h, H.alpha, cur, b, bc, c->s);
+  cnt(); post();
+  const int reps = (1 == H.nlev - 1) ? 1 : H.cyc;
+  for (int k = 0; k < reps; ++k) cycle_rec<float>(c, H, 1, bc, xc, k > 0);
+  for (int s = 0; s < H.nu2; ++s) sweep(s == 0 ? xc : nullptr);
+  if (cur != x) {   // only with an initial guess and an odd number of sweeps; copies every item
+                    // (the vectors of items outside an active list are not read afterwards)
+    const long long nv = (long long)H.items * 3 * L.g.ncell;
+    CK(cudaMemcpyAsync(x, cur, nv * sizeof(float2), cudaMemcpyDeviceToDevice, c->s));
+  }
+}
+
+template <typename T>
+void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typename CT<T>::type* x,
                bool guess) {
   typedef typename CT<T>::type C;
   Level& L = H.lv[l];
@@ -559,6 +602,12 @@ void cycle_rec(ehs_ctx* c, Hier& H, int l, const typename CT<T>::type* b, typena
     if (H.cdd.nsub) coarse_dd_solve<T>(c, H, b, x);
     else coarse_gemv<T>(c, H, L, (int)((L.g.d + 1) * L.g.ncell), H.items, b, x);
     return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (l == 0 && H.fused0 && H.nu1 >= 1 && H.nu2 >= 1) {
+      cycle_fine_fused(c, H, b, x, guess);
+      return;
+    }
   }
   C* t = (C*)L.ws[p][2];
   C* r = (C*)L.ws[p][3];
@@ -1210,6 +1259,24 @@ ehs_status ehs_smooth(ehs_ctx* c, int level, int nsweeps, int prec, const void* 
     if (level < 0 || level >= c->H.nlev - 1) throw ArgError("level out of range (the coarsest level is solved, not smoothed)");
     if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
     if (!b || !x || nsweeps < 0) throw ArgError("bad argument");
+    if (prec == EHS_C64 && level == 0 && c->H.fused0) {   // whole sweeps, x -> t -> x
+      Hier& H = c->H;
+      const Level& L = H.lv[0];
+      float2* t = (float2*)L.ws[1][2];
+      const float wu = (float)L.w, wp = (float)(L.w * H.wp_ratio);
+      const float2* cur = (const float2*)x;
+      for (int s = 0; s < nsweeps; ++s) {
+        float2* out = cur == (const float2*)x ? t : (float2*)x;
+        launch_fine_sweep_tile(L.g, H.lv[1].g, H.items, H.nrhs, H.cf32, H.h, H.alpha, wu, wp, (const float2*)b,
+                               cur, nullptr, out, c->s);
+        cnt(); post();
+        cur = out;
+      }
+      if (cur != (const float2*)x)
+        CK(cudaMemcpyAsync(x, cur, (size_t)H.items * 3 * L.g.ncell * sizeof(float2), cudaMemcpyDeviceToDevice,
+                           c->s));
+      return EHS_OK;
+    }
     for (int s = 0; s < nsweeps; ++s) {
       if (prec == EHS_C128)
         level_sweep<double>(c, c->H, level, (const double2*)b, (double2*)x, (double2*)c->H.lv[level].ws[0][2]);
@@ -1228,6 +1295,50 @@ ehs_status ehs_vcycle(ehs_ctx* c, int prec, const void* b, void* x) {
     if (!b || !x) throw ArgError("null vector");
     if (prec == EHS_C128) cycle_rec<double>(c, c->H, 0, (const double2*)b, (double2*)x, false);
     else cycle_rec<float>(c, c->H, 0, (const float2*)b, (float2*)x, false);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_residual_restrict(ehs_ctx* c, int level, int prec, const void* b, const void* x, void* rc) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
+    if (level < 0 || level >= c->H.nlev - 1) throw ArgError("level out of range (0 .. levels-2)");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!b || !x || !rc) throw ArgError("null vector");
+    Hier& H = c->H;
+    const Level& L = H.lv[level];
+    const Level& Lc = H.lv[level + 1];
+    if (prec == EHS_C64 && level == 0 && H.fused0) {
+      launch_fine_resid_restrict_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.h, H.alpha, (const float2*)x,
+                                      (const float2*)b, (float2*)rc, c->s);
+      cnt(); post();
+    } else if (prec == EHS_C64) {
+      float2* r = (float2*)L.ws[1][3];
+      level_apply<float>(c, H, level, H.alpha, (const float2*)x, (const float2*)b, r, 1);
+      launch_restrict<float>(L.g, Lc.g, H.items, r, (float2*)rc, c->s); cnt(); post();
+    } else {
+      double2* r = (double2*)L.ws[0][3];
+      level_apply<double>(c, H, level, H.alpha, (const double2*)x, (const double2*)b, r, 1);
+      launch_restrict<double>(L.g, Lc.g, H.items, r, (double2*)rc, c->s); cnt(); post();
+    }
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_prolong_add(ehs_ctx* c, int level, int prec, const void* ec, void* x) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
+    if (level < 0 || level >= c->H.nlev - 1) throw ArgError("level out of range (0 .. levels-2)");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!ec || !x) throw ArgError("null vector");
+    const Hier& H = c->H;
+    if (prec == EHS_C64)
+      launch_prolong_add<float>(H.lv[level].g, H.lv[level + 1].g, H.items, (const float2*)ec, (float2*)x, c->s);
+    else
+      launch_prolong_add<double>(H.lv[level].g, H.lv[level + 1].g, H.items, (const double2*)ec, (double2*)x, c->s);
+    cnt(); post();
     return EHS_OK;
   });
 }

@@ -150,6 +150,49 @@ __host__ __device__ constexpr int pw4(int kind, int j, int J, int nc) {
 // kind of component a along direction k
 __host__ __device__ constexpr int tkind(int a, int k, int d) { return a == d ? 2 : (a == k ? 0 : 1); }
 
+// The same 1D rules seen from a fine index j: at most two coarse indices J0,
+// J1 carry a weight (w0, w1; a zero weight is unused and its index is a valid
+// in-range placeholder).  Fine indices are those of unknowns (1..nf-1 for
+// kind 0, 0..nf-1 otherwise); pw(kind, j, J, nc) == w0 at J0 plus w1 at J1.
+template <typename T>
+__host__ __device__ constexpr void pw_pair(int kind, int j, int nc, int& J0, T& w0, int& J1, T& w1) {
+  if (kind == 0) {
+    if ((j & 1) == 0) {
+      J0 = j >> 1; w0 = (J0 >= 1 && J0 <= nc - 1) ? T(1) : T(0);
+      J1 = J0; w1 = T(0);
+    } else {
+      J0 = (j - 1) >> 1; w0 = (J0 >= 1 && J0 <= nc - 1) ? T(0.5) : T(0);
+      J1 = (j + 1) >> 1; w1 = (J1 >= 1 && J1 <= nc - 1) ? T(0.5) : T(0);
+      if (w1 == T(0)) J1 = J0;
+      if (w0 == T(0)) J0 = J1;
+    }
+    return;
+  }
+  J0 = j >> 1; w0 = T(0.75);
+  J1 = (j & 1) ? J0 + 1 : J0 - 1; w1 = T(0.25);
+  if (J1 < 0 || J1 >= nc) {
+    w1 = T(0); J1 = J0;
+    if (kind == 2) w0 = T(1);
+  }
+}
+// pw_pair() against pw() for every kind and unknown index of a coarse grid of nc cells
+__host__ __device__ constexpr bool pw_pair_agrees(int nc) {
+  for (int kind = 0; kind < 3; ++kind)
+    for (int j = (kind == 0 ? 1 : 0); j <= 2 * nc - 1; ++j) {
+      int J0 = 0, J1 = 0;
+      double w0 = 0, w1 = 0;
+      pw_pair<double>(kind, j, nc, J0, w0, J1, w1);
+      if (J0 < 0 || J0 >= nc || J1 < 0 || J1 >= nc) return false;
+      for (int J = 0; J < nc; ++J) {
+        const double w = (J == J0 ? w0 : 0.0) + (J == J1 ? w1 : 0.0);   // a placeholder adds 0
+        if (w != pw(kind, j, J, nc)) return false;
+      }
+    }
+  return true;
+}
+static_assert(pw_pair_agrees(2) && pw_pair_agrees(3) && pw_pair_agrees(4) && pw_pair_agrees(9),
+              "fine-index transfer rule = pw()");
+
 // Level-0 stencil layout of the mixed operator: (u_k, u_k) a 3^d box, (u_k, p)
 // offsets -1..0 along k, (p, u_k) offsets 0..1 along k, (p, p) the centre.
 __host__ __device__ constexpr StencilLayout make_fine_layout(int d) {

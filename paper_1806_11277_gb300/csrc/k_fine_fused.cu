@@ -1,0 +1,504 @@
+// Fused fine-level kernels of the 2D complex64 cycle (economic cell-wise
+// Vanka, Sec. 3 and Sec. 4.2; Algorithm TwoCycle steps 2 and 4 of Sec. 2.2).
+//
+// k_fine_sweep_tile: one whole red-black sweep in one launch.  A CTA owns a
+//   SW_X x SW_Y tile of fine cells of one item and stages x (u_0, u_1, p) and
+//   the cell coefficients of the tile plus a 3-cell halo in shared memory.  It
+//   relaxes every red cell of the tile and of the one-cell ring around it from
+//   the staged iterate (all red updates from the same old iterate, as in the
+//   red half-sweep), applies them in shared memory, then relaxes the black
+//   cells of the tile and writes the new iterate.  Every interior face belongs
+//   to exactly one black cell, whose CTA writes it; each CTA writes the
+//   pressures of its tile and zeros on its Dirichlet slots, so the output is a
+//   complete iterate.  The staged x is either the input iterate, zero (a zero
+//   initial guess: pre-smoothing of a cycle, no read of x), or the input
+//   iterate plus the prolongated coarse correction P e_c (Algorithm TwoCycle
+//   step 4 folded into the first post-smoothing sweep).
+// k_fine_resid_restrict_tile: r_c = P^T (b - K_s x) in one pass.  A CTA stages
+//   x and the coefficients of a RR_X x RR_Y fine tile plus a 2-cell halo,
+//   evaluates the fine residual on the tile plus a one-cell ring into shared
+//   memory, and forms the restriction of the tile's coarse cells from there;
+//   the fine residual is never written to memory.
+//
+// The row arithmetic is that of k_fine_apply / k_fine_vanka, with the
+// quantities that depend on the coefficients alone formed once per staged tile
+// instead of once per use: the mean of mu over the 4 cells around each vertex
+// (the tangential weight of the two face rows that meet there), the diagonal
+// of each face row and its inverse, and the inverse pressure Schur complement
+// of each relaxed cell's arrowhead block (eq. RelaxationMatrix); weights carry
+// the 1/h^2 factor.  Outside the
+// grid the displacements read zero (Dirichlet slots and the implicit high
+// boundary faces) and the coefficients repeat the nearest cell (the clamped
+// edge averages), so the rows need no per-load bounds checks.  Each cell update
+// loads every neighbouring value it needs once.
+#include "kernels.h"
+
+namespace ehs {
+namespace {
+
+constexpr int SW_X = 32, SW_Y = 16, SW_H = 3;                 // sweep tile and staged halo
+constexpr int SWS_X = SW_X + 2 * SW_H, SWS_Y = SW_Y + 2 * SW_H;
+constexpr int SW_RX = SW_X + 2, SW_RY = SW_Y + 2;             // red region: tile + one-cell ring
+constexpr int SW_NRED = SW_RX * SW_RY / 2;                    // 306 red cells
+constexpr int SW_T = SW_X * SW_Y / 2;                         // 256 threads: one cell pair each
+constexpr int SW_RPT = (SW_NRED + SW_T - 1) / SW_T;           // red cells per thread (2)
+
+constexpr int RR_X = 32, RR_Y = 16, RR_H = 2;                 // residual + restriction tile
+constexpr int RRS_X = RR_X + 2 * RR_H, RRS_Y = RR_Y + 2 * RR_H;
+constexpr int RR_RX = RR_X + 2, RR_RY = RR_Y + 2;             // fine residual region
+constexpr int RR_T = 256;
+constexpr int RR_RPT = (RR_RX * RR_RY + RR_T - 1) / RR_T;     // residual cells per thread (3)
+
+static_assert(SW_X % 2 == 0 && RR_X % 4 == 0 && RR_Y % 2 == 0, "tile shapes");
+
+struct FP {
+  float h2inv, hinv, alpha;
+};
+
+// Staged tile of W x H cells (local (lx, ly) = global (x0 + lx, y0 + ly)).
+//   x:   u_0, u_1, p (zero outside the grid and on Dirichlet slots)
+//   mu:  cell mu / h^2 (clamped outside the grid); kap: cell 1/(lambda+mu)
+//   mm:  cell (omega^2 rho, omega rho gamma) (clamped) while staging; in the
+//        sweep, afterwards, the inverse Schur complement
+//        1/(-kap - sum_faces (1/h^2) / dg) of the cells that are relaxed
+//   vm:  vm[ly][lx] = mean of mu / h^2 over cells (lx-1..lx, ly-1..ly), the
+//        vertex at the low corner of cell (lx, ly)
+//   fx / fy: per face of u_0 (between cells lx-1 and lx) / u_1 (between cells
+//        ly-1 and ly) the diagonal dg of its row (residual tile) or its inverse
+//        (sweep tile: the cell solve needs only 1/dg).  Formed by prep() on the
+//        faces the kernel's rows use.
+template <int W, int H>
+struct Tile {
+  float2 x[3][H][W];
+  float mu[H][W], kap[H][W], vm[H][W];
+  float2 mm[H][W];
+  float2 fx[H][W], fy[H][W];
+};
+
+__device__ __forceinline__ void cpa8(void* dst, const void* src, int nbytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// (P e_c) of component a at fine cell (gx, gy): coarse item vector ec ([3][ncc])
+__device__ __forceinline__ float2 prolong_at(const float2* __restrict__ ec, int a, int gx, int gy, int ncx,
+                                             int ncy) {
+  const int kx = a == 2 ? 2 : (a == 0 ? 0 : 1);
+  const int ky = a == 2 ? 2 : (a == 1 ? 0 : 1);
+  int X0, X1, Y0, Y1;
+  float wx0, wx1, wy0, wy1;
+  pw_pair<float>(kx, gx, ncx, X0, wx0, X1, wx1);
+  pw_pair<float>(ky, gy, ncy, Y0, wy0, Y1, wy1);
+  const float2* e = ec + (long long)a * ncx * ncy;
+  float2 acc = make_float2(0.f, 0.f);
+  if (wy0 != 0.0f) {
+    const float2* row = e + (long long)Y0 * ncx;
+    if (wx0 != 0.0f) acc = cfma(make_float2(wy0 * wx0, 0.f), __ldg(row + X0), acc);
+    if (wx1 != 0.0f) acc = cfma(make_float2(wy0 * wx1, 0.f), __ldg(row + X1), acc);
+  }
+  if (wy1 != 0.0f) {
+    const float2* row = e + (long long)Y1 * ncx;
+    if (wx0 != 0.0f) acc = cfma(make_float2(wy1 * wx0, 0.f), __ldg(row + X0), acc);
+    if (wx1 != 0.0f) acc = cfma(make_float2(wy1 * wx1, 0.f), __ldg(row + X1), acc);
+  }
+  return acc;
+}
+
+// Stage the clamped coefficients of the tile (x0, y0) and x: from xv (null:
+// the zero iterate), plus P e when e is given, with the zero fill.
+template <int W, int H, int NT>
+__device__ __forceinline__ void stage(Tile<W, H>& S, const float4* __restrict__ cfs, const float2* __restrict__ xv,
+                                      const float2* __restrict__ e, const Grid& gc, int N, int nx, int ny,
+                                      int x0, int y0, float h2inv) {
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < W * H; idx += NT) {
+    const int lx = idx % W, ly = idx / W;
+    const int gx = x0 + lx, gy = y0 + ly;
+    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const int cx = min(max(gx, 0), nx - 1), cy = min(max(gy, 0), ny - 1);
+    const int gcl = cy * nx + cx;                                  // a valid address in every case
+    const bool v0 = in && gx >= 1, v1 = in && gy >= 1;            // u_k slot 0 is a boundary face
+    if (!e) {
+      if (xv) {
+        cpa8(&S.x[0][ly][lx], xv + gcl, v0 ? 8 : 0);
+        cpa8(&S.x[1][ly][lx], xv + N + gcl, v1 ? 8 : 0);
+        cpa8(&S.x[2][ly][lx], xv + 2 * N + gcl, in ? 8 : 0);
+      } else {
+        const float2 z = make_float2(0.f, 0.f);
+        S.x[0][ly][lx] = z; S.x[1][ly][lx] = z; S.x[2][ly][lx] = z;
+      }
+    } else {
+      float2 u0 = make_float2(0.f, 0.f), u1 = u0, pv = u0;
+      if (v0) u0 = cadd(xv ? __ldg(xv + gcl) : u0, prolong_at(e, 0, gx, gy, gc.n[0], gc.n[1]));
+      if (v1) u1 = cadd(xv ? __ldg(xv + N + gcl) : u1, prolong_at(e, 1, gx, gy, gc.n[0], gc.n[1]));
+      if (in) pv = cadd(xv ? __ldg(xv + 2 * N + gcl) : pv, prolong_at(e, 2, gx, gy, gc.n[0], gc.n[1]));
+      S.x[0][ly][lx] = u0; S.x[1][ly][lx] = u1; S.x[2][ly][lx] = pv;
+    }
+    const float4 c = __ldg(cfs + gcl);
+    S.mu[ly][lx] = c.x * h2inv;
+    S.kap[ly][lx] = c.y;
+    S.mm[ly][lx] = make_float2(c.z, c.w);
+  }
+}
+
+// Coefficient terms of the rows of the cells in [RX0, RX1] x [RY0, RY1] (staged
+// coordinates) and of their faces: vertex means and face diagonals, or with INV
+// the inverse diagonals and the cells' inverse Schur complements (after stage()
+// and a barrier; ends with a barrier).  ox, oy: global coordinates of staged (0, 0).
+template <int W, int H, int NT, int RX0, int RX1, int RY0, int RY1, bool INV>
+__device__ __forceinline__ void prep(Tile<W, H>& S, const FP& P, int ox, int oy, int nx, int ny) {
+  static_assert(RX0 >= 1 && RY0 >= 1 && RX1 + 1 <= W - 1 && RY1 + 1 <= H - 1, "prep region inside the tile");
+  constexpr int VX = RX1 - RX0 + 2, VY = RY1 - RY0 + 2;          // vertices and faces: one wider
+  for (int idx = threadIdx.x; idx < VX * VY; idx += NT) {
+    const int lx = RX0 + idx % VX, ly = RY0 + idx / VX;
+    S.vm[ly][lx] = 0.25f * ((S.mu[ly][lx] + S.mu[ly][lx - 1]) + S.mu[ly - 1][lx] + S.mu[ly - 1][lx - 1]);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < VX * VY; idx += NT) {
+    const int lx = RX0 + idx % VX, ly = RY0 + idx / VX;
+    if (ly <= RY1) {     // u_0 face between cells (lx-1, ly) and (lx, ly)
+      const float wsum = (S.mu[ly][lx] + S.mu[ly][lx - 1]) + S.vm[ly + 1][lx] + S.vm[ly][lx];
+      const float2 m0 = S.mm[ly][lx], m1 = S.mm[ly][lx - 1];
+      const float rf = 0.5f * (m0.x + m1.x), gf = 0.5f * (m0.y + m1.y);
+      const float2 d = make_float2(wsum - rf, gf + P.alpha * rf);
+      S.fx[ly][lx] = INV ? cinv(d) : d;
+    }
+    if (lx <= RX1) {     // u_1 face between cells (lx, ly-1) and (lx, ly)
+      const float wsum = (S.mu[ly][lx] + S.mu[ly - 1][lx]) + S.vm[ly][lx + 1] + S.vm[ly][lx];
+      const float2 m0 = S.mm[ly][lx], m1 = S.mm[ly - 1][lx];
+      const float rf = 0.5f * (m0.x + m1.x), gf = 0.5f * (m0.y + m1.y);
+      const float2 d = make_float2(wsum - rf, gf + P.alpha * rf);
+      S.fy[ly][lx] = INV ? cinv(d) : d;
+    }
+  }
+  __syncthreads();
+  if constexpr (INV) {   // Schur complements of the relaxed cells (mm is no longer read)
+    Tile<W, H>& T = S;
+    constexpr int CX = RX1 - RX0 + 1, CY = RY1 - RY0 + 1;
+    for (int idx = threadIdx.x; idx < CX * CY; idx += NT) {
+      const int lx = RX0 + idx % CX, ly = RY0 + idx / CX;
+      const int gx = ox + lx, gy = oy + ly;
+      float2 sd = make_float2(0.f, 0.f);                          // sum of the faces' 1/dg
+      if (gx >= 1) sd = cadd(sd, T.fx[ly][lx]);
+      if (gx + 1 < nx) sd = cadd(sd, T.fx[ly][lx + 1]);
+      if (gy >= 1) sd = cadd(sd, T.fy[ly][lx]);
+      if (gy + 1 < ny) sd = cadd(sd, T.fy[ly + 1][lx]);
+      const float2 sch = make_float2(-T.kap[ly][lx] - P.h2inv * sd.x, -P.h2inv * sd.y);
+      T.mm[ly][lx] = cinv(sch);
+    }
+    __syncthreads();
+  }
+}
+
+// Off-diagonal part of a face row and its pressure coupling:
+// b - (K_s row - dg xc) = b + (wpn xn+ + wmn xn- + wtp xt+ + wtm xt-) - (p_high - p_low) / h
+__device__ __forceinline__ float2 face_rhs(float2 b, float wpn, float2 xnp, float wmn, float2 xnm, float wtp,
+                                           float2 xtp, float wtm, float2 xtm, float2 phi, float2 plo, float hinv) {
+  float2 s;
+  s.x = fmaf(wpn, xnp.x, b.x); s.y = fmaf(wpn, xnp.y, b.y);
+  s.x = fmaf(wmn, xnm.x, s.x); s.y = fmaf(wmn, xnm.y, s.y);
+  s.x = fmaf(wtp, xtp.x, s.x); s.y = fmaf(wtp, xtp.y, s.y);
+  s.x = fmaf(wtm, xtm.x, s.x); s.y = fmaf(wtm, xtm.y, s.y);
+  return make_float2(fmaf(-hinv, phi.x - plo.x, s.x), fmaf(-hinv, phi.y - plo.y, s.y));
+}
+
+// Economic cell update (eq. RelaxationMatrix: diagonal of the displacement block,
+// displacement-pressure couplings g = (+1/h, +1/h, -1/h, -1/h), pressure diagonal)
+// of the cell at staged (sx, sy), global (gx, gy), in-item index c: new values
+// of its low faces (o[0] u_0, o[1] u_1), high faces (o[2] u_0 of cell + e_x,
+// o[3] u_1 of cell + e_y) and pressure (o[4]); ok[a] marks the faces that are
+// unknowns.  With r the residual of the block's rows and t_a = r_a / dg_a
+// = (b_a - offdiag_a) / dg_a - x_a:
+//   dp = (r_p - sum_a g_a t_a) / S,  du_a = t_a - g_a dp / dg_a,
+// S = -kap - sum_a g_a^2 / dg_a (stored inverted per cell).
+template <int W, int H>
+__device__ __forceinline__ void cell_update(const Tile<W, H>& S, int sx, int sy, int gx, int gy, int nx, int ny,
+                                            int N, int c, const float2* __restrict__ bb, const FP& P,
+                                            float wu, float wp, float2 o[5], bool ok[4]) {
+  ok[0] = gx >= 1;
+  ok[1] = gy >= 1;
+  ok[2] = gx + 1 < nx;
+  ok[3] = gy + 1 < ny;
+  // right-hand sides first (global loads in flight while the rows are formed)
+  const float2 z = make_float2(0.f, 0.f);
+  const float2 b0 = ok[0] ? __ldg(bb + c) : z, b1 = ok[1] ? __ldg(bb + N + c) : z;
+  const float2 b2 = ok[2] ? __ldg(bb + c + 1) : z, b3 = ok[3] ? __ldg(bb + N + c + nx) : z;
+  const float2 b4 = __ldg(bb + 2 * N + c);
+  // every staged value the five rows read, once
+  const float2 u0m = S.x[0][sy][sx - 1], u00 = S.x[0][sy][sx], u01 = S.x[0][sy][sx + 1], u02 = S.x[0][sy][sx + 2];
+  const float2 u0dn = S.x[0][sy - 1][sx], u0up = S.x[0][sy + 1][sx];
+  const float2 u1dn = S.x[0][sy - 1][sx + 1], u1up = S.x[0][sy + 1][sx + 1];
+  const float2 v0m = S.x[1][sy - 1][sx], v00 = S.x[1][sy][sx], v01 = S.x[1][sy + 1][sx], v02 = S.x[1][sy + 2][sx];
+  const float2 v0l = S.x[1][sy][sx - 1], v0r = S.x[1][sy][sx + 1];
+  const float2 v1l = S.x[1][sy + 1][sx - 1], v1r = S.x[1][sy + 1][sx + 1];
+  const float2 pc = S.x[2][sy][sx], pl = S.x[2][sy][sx - 1], pr = S.x[2][sy][sx + 1];
+  const float2 pd = S.x[2][sy - 1][sx], pu = S.x[2][sy + 1][sx];
+  const float mc = S.mu[sy][sx], ml = S.mu[sy][sx - 1], mr = S.mu[sy][sx + 1];
+  const float md = S.mu[sy - 1][sx], mup = S.mu[sy + 1][sx];
+  const float w00 = S.vm[sy][sx], w10 = S.vm[sy][sx + 1], w01 = S.vm[sy + 1][sx], w11 = S.vm[sy + 1][sx + 1];
+  const float hinv = P.hinv;
+  float2 dinv[4];
+  dinv[0] = S.fx[sy][sx];
+  dinv[1] = S.fy[sy][sx];
+  dinv[2] = S.fx[sy][sx + 1];
+  dinv[3] = S.fy[sy + 1][sx];
+  float2 t[4];
+  t[0] = csub(cmul(dinv[0], face_rhs(b0, mc, u01, ml, u0m, w01, u0up, w00, u0dn, pc, pl, hinv)), u00);
+  t[1] = csub(cmul(dinv[1], face_rhs(b1, mc, v01, md, v0m, w10, v0r, w00, v0l, pc, pd, hinv)), v00);
+  t[2] = csub(cmul(dinv[2], face_rhs(b2, mr, u02, mc, u00, w11, u1up, w10, u1dn, pr, pc, hinv)), u01);
+  t[3] = csub(cmul(dinv[3], face_rhs(b3, mup, v02, mc, v00, w11, v1r, w01, v1l, pu, pc, hinv)), v01);
+  // pressure row residual: b - (-kap p + (div u) / h)
+  const float kap = S.kap[sy][sx];
+  const float2 sdiv = make_float2((u00.x - u01.x) + (v00.x - v01.x), (u00.y - u01.y) + (v00.y - v01.y));
+  float2 rp = make_float2(b4.x - fmaf(-kap, pc.x, hinv * sdiv.x), b4.y - fmaf(-kap, pc.y, hinv * sdiv.y));
+  const float gk[4] = {hinv, hinv, -hinv, -hinv};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (!ok[a]) continue;
+    rp.x = fmaf(-gk[a], t[a].x, rp.x);
+    rp.y = fmaf(-gk[a], t[a].y, rp.y);
+  }
+  const float2 dp = cmul(rp, S.mm[sy][sx]);
+  o[4] = make_float2(fmaf(wp, dp.x, pc.x), fmaf(wp, dp.y, pc.y));
+  const float2 xv[4] = {u00, v00, u01, v01};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (!ok[a]) { o[a] = xv[a]; continue; }
+    const float2 q = cmul(dp, dinv[a]);
+    const float2 du = make_float2(fmaf(-gk[a], q.x, t[a].x), fmaf(-gk[a], q.y, t[a].y));
+    o[a] = make_float2(fmaf(wu, du.x, xv[a].x), fmaf(wu, du.y, xv[a].y));
+  }
+}
+
+typedef Tile<SWS_X, SWS_Y> SweepTile;
+typedef Tile<RRS_X, RRS_Y> ResTile;
+
+__global__ void __launch_bounds__(SW_T, 4) k_fine_sweep_tile(Grid g, Grid gc, int nrhs, const float4* __restrict__ cf,
+                                                             FP P, float wu, float wp,
+                                                             const float2* __restrict__ b,
+                                                             const float2* __restrict__ xi,
+                                                             const float2* __restrict__ ec,
+                                                             float2* __restrict__ xo, const int* __restrict__ il) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SweepTile& S = *reinterpret_cast<SweepTile*>(smem_raw);
+  const int item = il ? il[blockIdx.z] : blockIdx.z;
+  const int N = (int)g.ncell;                                      // ncell < 2^31 on every level
+  const int nx = g.n[0], ny = g.n[1];
+  const long long vo = (long long)item * 3 * N;
+  const float4* cfs = cf + (long long)(item / nrhs) * N;
+  const float2* x = xi ? xi + vo : nullptr;
+  const float2* e = ec ? ec + (long long)item * 3 * gc.ncell : nullptr;
+  const int X0 = blockIdx.x * SW_X, Y0 = blockIdx.y * SW_Y;
+  const int x0 = X0 - SW_H, y0 = Y0 - SW_H;
+  stage<SWS_X, SWS_Y, SW_T>(S, cfs, x, e, gc, N, nx, ny, x0, y0, P.h2inv);
+  cpa_wait();
+  __syncthreads();
+  // the red region (tile + one-cell ring) spans staged [SW_H - 1, SW_H + SW_X] x [SW_H - 1, SW_H + SW_Y]
+  prep<SWS_X, SWS_Y, SW_T, SW_H - 1, SW_H + SW_X, SW_H - 1, SW_H + SW_Y, true>(S, P, x0, y0, nx, ny);
+  const float2* bb = b + vo;
+  float2* xout = xo + vo;
+  // ---- red cells of the tile and its one-cell ring, all from the staged iterate
+  float2 ro[SW_RPT][5];
+  bool rok[SW_RPT][4];
+  int rsx[SW_RPT], rsy[SW_RPT];
+#pragma unroll
+  for (int q = 0; q < SW_RPT; ++q) {
+    rsx[q] = -1;
+    const int id = threadIdx.x + q * SW_T;
+    if (id >= SW_NRED) continue;
+    const int ry = id / (SW_RX / 2), kx = id % (SW_RX / 2);
+    const int gy = Y0 - 1 + ry;
+    const int gxs = X0 - 1;
+    const int gx = gxs + 2 * kx + ((gxs + gy) & 1);                 // (gx + gy) even: red
+    if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
+    const int sx = gx - x0, sy = gy - y0;
+    cell_update<SWS_X, SWS_Y>(S, sx, sy, gx, gy, nx, ny, N, gy * nx + gx, bb, P, wu, wp, ro[q], rok[q]);
+    rsx[q] = sx; rsy[q] = sy;
+  }
+  __syncthreads();                                                 // every red row has read the old iterate
+#pragma unroll
+  for (int q = 0; q < SW_RPT; ++q) {
+    if (rsx[q] < 0) continue;
+    const int sx = rsx[q], sy = rsy[q];
+    if (rok[q][0]) S.x[0][sy][sx] = ro[q][0];
+    if (rok[q][1]) S.x[1][sy][sx] = ro[q][1];
+    if (rok[q][2]) S.x[0][sy][sx + 1] = ro[q][2];
+    if (rok[q][3]) S.x[1][sy + 1][sx] = ro[q][3];
+    S.x[2][sy][sx] = ro[q][4];
+  }
+  __syncthreads();
+  // ---- black cells of the tile from the red-updated iterate; outputs
+  const int t = threadIdx.x;
+  const int ty = t / (SW_X / 2), kx = t % (SW_X / 2);
+  const int gy = Y0 + ty;
+  const int gxb = X0 + 2 * kx + ((gy + 1) & 1);                    // (gx + gy) odd: black
+  const int gxr = gxb ^ 1;                                         // the red cell of the pair
+  const int cb = gy * nx + gxb, cr = gy * nx + gxr;
+  const int sy = gy - y0;
+  // red pressure of the pair: the red update
+  xout[2 * N + cr] = S.x[2][sy][gxr - x0];
+  // Dirichlet slots of the pair's two cells (never written by any update)
+  if (gxb == 0) xout[cb] = make_float2(0.f, 0.f);
+  if (gxr == 0) xout[cr] = make_float2(0.f, 0.f);
+  if (gy == 0) { xout[N + cb] = make_float2(0.f, 0.f); xout[N + cr] = make_float2(0.f, 0.f); }
+  float2 o[5];
+  bool ok[4];
+  cell_update<SWS_X, SWS_Y>(S, gxb - x0, sy, gxb, gy, nx, ny, N, cb, bb, P, wu, wp, o, ok);
+  xout[2 * N + cb] = o[4];
+  if (ok[0]) xout[cb] = o[0];
+  if (ok[1]) xout[N + cb] = o[1];
+  if (ok[2]) xout[cb + 1] = o[2];
+  if (ok[3]) xout[N + cb + nx] = o[3];
+}
+
+// 1D restriction weight of fine index j in coarse index J (pw4 in quarters)
+__device__ __forceinline__ float rw(int kind, int j, int J, int nc) { return 0.25f * (float)pw4(kind, j, J, nc); }
+
+__global__ void __launch_bounds__(RR_T, 4) k_fine_resid_restrict_tile(Grid g, Grid gc, int nrhs,
+                                                                      const float4* __restrict__ cf, FP P,
+                                                                      const float2* __restrict__ x,
+                                                                      const float2* __restrict__ b,
+                                                                      float2* __restrict__ rc,
+                                                                      const int* __restrict__ il) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ResTile& S = *reinterpret_cast<ResTile*>(smem_raw);
+  const int item = il ? il[blockIdx.z] : blockIdx.z;
+  const int N = (int)g.ncell;                                      // ncell < 2^31 on every level
+  const int nx = g.n[0], ny = g.n[1];
+  const long long vo = (long long)item * 3 * N;
+  const float4* cfs = cf + (long long)(item / nrhs) * N;
+  const int X0 = blockIdx.x * RR_X, Y0 = blockIdx.y * RR_Y;
+  const int x0 = X0 - RR_H, y0 = Y0 - RR_H;
+  stage<RRS_X, RRS_Y, RR_T>(S, cfs, x + vo, nullptr, gc, N, nx, ny, x0, y0, P.h2inv);
+  cpa_wait();
+  __syncthreads();
+  // the residual region (tile + one-cell ring) spans staged [RR_H - 1, RR_H + RR_X] x [RR_H - 1, RR_H + RR_Y]
+  prep<RRS_X, RRS_Y, RR_T, RR_H - 1, RR_H + RR_X, RR_H - 1, RR_H + RR_Y, false>(S, P, x0, y0, nx, ny);
+  const float2* bb = b + vo;
+  const float hinv = P.hinv;
+  // fine residual b - K_s x on the tile and its one-cell ring (zero outside the grid and on
+  // the Dirichlet slots): the low-face rows of u_0 and u_1 and the pressure row of each cell
+  float2 rr[RR_RPT][3];
+#pragma unroll
+  for (int q = 0; q < RR_RPT; ++q) {
+    const int id = threadIdx.x + q * RR_T;
+    rr[q][0] = rr[q][1] = rr[q][2] = make_float2(0.f, 0.f);
+    if (id >= RR_RX * RR_RY) continue;
+    const int rx = id % RR_RX, ry = id / RR_RX;
+    const int gx = X0 - 1 + rx, gy = Y0 - 1 + ry;
+    if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
+    const int sx = gx - x0, sy = gy - y0;
+    const int c = gy * nx + gx;
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 b0 = gx >= 1 ? __ldg(bb + c) : z;
+    const float2 b1 = gy >= 1 ? __ldg(bb + N + c) : z;
+    const float2 b2 = __ldg(bb + 2 * N + c);
+    const float2 u0m = S.x[0][sy][sx - 1], u00 = S.x[0][sy][sx], u01 = S.x[0][sy][sx + 1];
+    const float2 u0dn = S.x[0][sy - 1][sx], u0up = S.x[0][sy + 1][sx];
+    const float2 v0m = S.x[1][sy - 1][sx], v00 = S.x[1][sy][sx], v01 = S.x[1][sy + 1][sx];
+    const float2 v0l = S.x[1][sy][sx - 1], v0r = S.x[1][sy][sx + 1];
+    const float2 pc = S.x[2][sy][sx], pl = S.x[2][sy][sx - 1], pd = S.x[2][sy - 1][sx];
+    const float mc = S.mu[sy][sx], ml = S.mu[sy][sx - 1], md = S.mu[sy - 1][sx];
+    const float w00 = S.vm[sy][sx], w10 = S.vm[sy][sx + 1], w01 = S.vm[sy + 1][sx];
+    if (gx >= 1) rr[q][0] = csub(face_rhs(b0, mc, u01, ml, u0m, w01, u0up, w00, u0dn, pc, pl, hinv), cmul(S.fx[sy][sx], u00));
+    if (gy >= 1) rr[q][1] = csub(face_rhs(b1, mc, v01, md, v0m, w10, v0r, w00, v0l, pc, pd, hinv), cmul(S.fy[sy][sx], v00));
+    const float kap = S.kap[sy][sx];
+    const float2 sdiv = make_float2((u00.x - u01.x) + (v00.x - v01.x), (u00.y - u01.y) + (v00.y - v01.y));
+    rr[q][2] = make_float2(b2.x - fmaf(-kap, pc.x, hinv * sdiv.x), b2.y - fmaf(-kap, pc.y, hinv * sdiv.y));
+  }
+  __syncthreads();                                                 // the staged x is no longer read
+  float2(*rs)[RR_RY][RR_RX] = reinterpret_cast<float2(*)[RR_RY][RR_RX]>(&S.x[0][0][0]);   // [3][RY][RX]
+  static_assert(sizeof(float2) * 3 * RR_RY * RR_RX <= sizeof(ResTile::x), "residual fits in the staged x");
+#pragma unroll
+  for (int q = 0; q < RR_RPT; ++q) {
+    const int id = threadIdx.x + q * RR_T;
+    if (id >= RR_RX * RR_RY) continue;
+    const int rx = id % RR_RX, ry = id / RR_RX;
+    rs[0][ry][rx] = rr[q][0];
+    rs[1][ry][rx] = rr[q][1];
+    rs[2][ry][rx] = rr[q][2];
+  }
+  __syncthreads();
+  // restriction: thread t < 128 forms u_0 and u_1 of coarse cell t, thread t >= 128 its pressure
+  constexpr int CX = RR_X / 2, CY = RR_Y / 2;
+  const int t = threadIdx.x % (CX * CY), half = threadIdx.x / (CX * CY);
+  const int I = X0 / 2 + t % CX, J = Y0 / 2 + t / CX;
+  if (I >= gc.n[0] || J >= gc.n[1]) return;
+  const int ncx = gc.n[0], ncy = gc.n[1];
+  const long long Nc = gc.ncell;
+  float2* o = rc + (long long)item * 3 * Nc + (long long)J * ncx + I;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int a = half ? 2 : s;                                    // half 0: u_0, u_1; half 1: p
+    if (half && s) break;
+    float2 acc = make_float2(0.f, 0.f);
+    const bool valid = a == 2 || (a == 0 ? I >= 1 : J >= 1);
+    if (valid) {
+      const int kx = a == 2 ? 2 : (a == 0 ? 0 : 1);
+      const int ky = a == 2 ? 2 : (a == 1 ? 0 : 1);
+#pragma unroll
+      for (int dy = -1; dy <= 2; ++dy) {
+        const int j = 2 * J + dy;
+        const float wy = rw(ky, j, J, ncy);
+        if (wy == 0.0f) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 2; ++dx) {
+          const int i = 2 * I + dx;
+          const float wx = rw(kx, i, I, ncx);
+          if (wx == 0.0f) continue;
+          acc = cfma(make_float2(wy * wx, 0.f), rs[a][j - (Y0 - 1)][i - (X0 - 1)], acc);
+        }
+      }
+    }
+    o[(long long)a * Nc] = acc;
+  }
+}
+
+// dynamic shared memory above the 48 KB default: set once per process and device
+template <typename K> void smem_attr(K kernel, size_t bytes) {
+  static int done[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  if (dev >= 0 && dev < 64 && !done[dev]) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done[dev] = 1;
+  }
+}
+
+}  // namespace
+
+bool fine_tiles_fit(const Grid& g) {
+  return g.d == 2 && g.n[0] % SW_X == 0 && g.n[1] % SW_Y == 0 && g.n[0] % RR_X == 0 && g.n[1] % RR_Y == 0;
+}
+
+void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf, double h,
+                            double alpha, float wu, float wp, const float2* b, const float2* xi,
+                            const float2* ec, float2* xo, cudaStream_t s) {
+  FP P;
+  P.h2inv = (float)(1.0 / (h * h));
+  P.hinv = (float)(1.0 / h);
+  P.alpha = (float)alpha;
+  smem_attr(k_fine_sweep_tile, sizeof(SweepTile));
+  const dim3 gr(g.n[0] / SW_X, g.n[1] / SW_Y, sel_items(items));
+  k_fine_sweep_tile<<<gr, SW_T, sizeof(SweepTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf), P, wu, wp,
+                                                         b, xi, ec, xo, g_sel.list);
+}
+
+void launch_fine_resid_restrict_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
+                                     double h, double alpha, const float2* x, const float2* b, float2* rc,
+                                     cudaStream_t s) {
+  FP P;
+  P.h2inv = (float)(1.0 / (h * h));
+  P.hinv = (float)(1.0 / h);
+  P.alpha = (float)alpha;
+  smem_attr(k_fine_resid_restrict_tile, sizeof(ResTile));
+  const dim3 gr(g.n[0] / RR_X, g.n[1] / RR_Y, sel_items(items));
+  k_fine_resid_restrict_tile<<<gr, RR_T, sizeof(ResTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf), P,
+                                                                x, b, rc, g_sel.list);
+}
+
+}  // namespace ehs

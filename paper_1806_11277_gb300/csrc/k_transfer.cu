@@ -2,12 +2,16 @@
 // steps 2 and 4) with the bilinear staggered-grid transfer of Sec. 3: per
 // component a tensor product of 1D rules (vertex-like along the component's
 // own direction, cell-like with zero ghosts across it, cell-like with clamped
-// ghosts for p).  The 1D weights come from pw4() in common.cuh (exact quarters).
+// ghosts for p).  The 1D weights come from pw4() / pw_pair() in common.cuh
+// (exact quarters); every tap loop has a fixed trip count and is unrolled, so
+// a thread issues all of its loads back to back.  (The 2D complex64 fine
+// level of the cycle uses the fused kernels of k_fine_fused.cu instead.)
 #include "kernels.h"
 
 namespace ehs {
 namespace {
 
+// thread per coarse cell: fine offsets -1..2 around 2I along every direction
 template <typename T, int D>
 __global__ void k_restrict(Grid gf, Grid gc, const typename CT<T>::type* __restrict__ rf,
                            typename CT<T>::type* __restrict__ rc, const int* __restrict__ il) {
@@ -19,36 +23,37 @@ __global__ void k_restrict(Grid gf, Grid gc, const typename CT<T>::type* __restr
   C* o = rc + (long long)item * (D + 1) * gc.ncell;
   int I[3];
   cell_coords(gc, c, I);
+  constexpr int NZ = D == 3 ? 4 : 1;
 #pragma unroll
   for (int a = 0; a <= D; ++a) {
     C acc = czero<C>();
     if (slot_valid(a, D, I)) {
-      int fi[3][4];
-      T fw[3][4];
-      int nf[3] = {1, 1, 1};
-      for (int k = 0; k < 3; ++k) {
-        if (k >= D) { fi[k][0] = 0; fw[k][0] = 1; continue; }
-        int n = 0;
-        const int kind = tkind(a, k, D);
-        for (int i = 2 * I[k] - 1; i <= 2 * I[k] + 2; ++i) {
-          const int v = pw4(kind, i, I[k], gc.n[k]);
-          if (v != 0) { fi[k][n] = i; fw[k][n] = T(0.25) * (T)v; ++n; }
-        }
-        nf[k] = n;
-      }
+      T w[3][4];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          w[k][t] = k < D ? T(0.25) * (T)pw4(tkind(a, k, D), 2 * I[k] - 1 + t, I[k], gc.n[k]) : T(t == 0);
       const C* fa = f + (long long)a * gf.ncell;
-      for (int z = 0; z < nf[2]; ++z)
-        for (int y = 0; y < nf[1]; ++y) {
-          const long long row = ((long long)fi[2][z] * gf.n[1] + fi[1][y]) * gf.n[0];
-          const T wzy = fw[2][z] * fw[1][y];
-          for (int x = 0; x < nf[0]; ++x)
-            acc = cfma(mk<T>(wzy * fw[0][x], 0), __ldg(fa + row + fi[0][x]), acc);
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) {
+        const int fz = D == 3 ? 2 * I[2] - 1 + z : 0;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const T wzy = w[2][z] * w[1][y];
+          if (wzy == T(0)) continue;
+          const long long row = ((long long)fz * gf.n[1] + (2 * I[1] - 1 + y)) * gf.n[0];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+            if (w[0][x] != T(0)) acc = cfma(mk<T>(wzy * w[0][x], 0), __ldg(fa + row + 2 * I[0] - 1 + x), acc);
         }
+      }
     }
     o[(long long)a * gc.ncell + c] = acc;
   }
 }
 
+// thread per fine cell: at most two coarse indices per direction (pw_pair)
 template <typename T, int D>
 __global__ void k_prolong_add(Grid gf, Grid gc, const typename CT<T>::type* __restrict__ ec,
                               typename CT<T>::type* __restrict__ xf, const int* __restrict__ il) {
@@ -60,30 +65,26 @@ __global__ void k_prolong_add(Grid gf, Grid gc, const typename CT<T>::type* __re
   C* x = xf + (long long)item * (D + 1) * gf.ncell;
   int i[3];
   cell_coords(gf, c, i);
+  constexpr int NZ = D == 3 ? 2 : 1;
 #pragma unroll
   for (int a = 0; a <= D; ++a) {
     if (!slot_valid(a, D, i)) continue;
-    int ci[3][3];
-    T cw[3][3];
-    int nc[3] = {1, 1, 1};
-    for (int k = 0; k < 3; ++k) {
-      if (k >= D) { ci[k][0] = 0; cw[k][0] = 1; continue; }
-      int n = 0;
-      const int kind = tkind(a, k, D);
-      for (int J = (i[k] >> 1) - 1; J <= (i[k] >> 1) + 1; ++J) {
-        const int v = pw4(kind, i[k], J, gc.n[k]);
-        if (v != 0) { ci[k][n] = J; cw[k][n] = T(0.25) * (T)v; ++n; }
-      }
-      nc[k] = n;
-    }
+    int J[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    T w[3][2] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
+#pragma unroll
+    for (int k = 0; k < D; ++k) pw_pair<T>(tkind(a, k, D), i[k], gc.n[k], J[k][0], w[k][0], J[k][1], w[k][1]);
     const C* ea = e + (long long)a * gc.ncell;
     C acc = czero<C>();
-    for (int z = 0; z < nc[2]; ++z)
-      for (int y = 0; y < nc[1]; ++y) {
-        const long long row = ((long long)ci[2][z] * gc.n[1] + ci[1][y]) * gc.n[0];
-        const T wzy = cw[2][z] * cw[1][y];
-        for (int xx = 0; xx < nc[0]; ++xx)
-          acc = cfma(mk<T>(wzy * cw[0][xx], 0), __ldg(ea + row + ci[0][xx]), acc);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        const T wzy = w[2][z] * w[1][y];
+        if (wzy == T(0)) continue;
+        const long long row = ((long long)J[2][z] * gc.n[1] + J[1][y]) * gc.n[0];
+#pragma unroll
+        for (int xx = 0; xx < 2; ++xx)
+          if (w[0][xx] != T(0)) acc = cfma(mk<T>(wzy * w[0][xx], 0), __ldg(ea + row + J[0][xx]), acc);
       }
     const long long idx = (long long)a * gf.ncell + c;
     x[idx] = cadd(x[idx], acc);

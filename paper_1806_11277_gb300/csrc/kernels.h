@@ -50,6 +50,17 @@ void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
                        double alpha, T wu, T wp, int colour,
                        const typename CT<T>::type* b, const typename CT<T>::type* xi,
                        typename CT<T>::type* xo, cudaStream_t s, int full = 0);
+// Fused fine-level kernels of the 2D complex64 cycle (economic block), for grids
+// that split into their tiles (fine_tiles_fit).  One whole red-black sweep:
+// xo = sweep(x_in), x_in = (xi or 0) + (P ec if ec), xo != xi; ec: coarse
+// vector of grid gc (ignored when null).  And r_c = P^T (b - K_s x) in one pass.
+bool fine_tiles_fit(const Grid& g);
+void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf, double h,
+                            double alpha, float wu, float wp, const float2* b, const float2* xi,
+                            const float2* ec, float2* xo, cudaStream_t s);
+void launch_fine_resid_restrict_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
+                                     double h, double alpha, const float2* x, const float2* b, float2* rc,
+                                     cudaStream_t s);
 // level-0 stencil table (double) of K_s for the Galerkin setup
 void fine_table_layout(int d, StencilLayout* L);
 void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double h,

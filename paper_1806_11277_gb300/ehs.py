@@ -50,7 +50,7 @@ EXPORTS = ["ehs_default_opts", "ehs_create", "ehs_destroy", "ehs_op_apply", "ehs
            "ehs_vcycle", "ehs_dd_precond", "ehs_fgmres_solve", "ehs_adjoint_solve", "ehs_items",
            "ehs_level_len", "ehs_level_dims", "ehs_sync", "ehs_kernel_launches", "ehs_last_error",
            "ehs_fine_smooth_noalloc", "ehs_gradient", "ehs_coarse_solve", "ehs_coarse_dims",
-           "ehs_coarse_local_apply"]
+           "ehs_coarse_local_apply", "ehs_residual_restrict", "ehs_prolong_add"]
 
 _lib = None
 
@@ -89,6 +89,8 @@ def load(path=LIB_PATH):
     lib.ehs_coarse_solve.argtypes = [vp, i, vp, vp]
     lib.ehs_coarse_dims.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
     lib.ehs_coarse_local_apply.argtypes = [vp, i, i, vp, vp]
+    lib.ehs_residual_restrict.argtypes = [vp, i, i, vp, vp, vp]
+    lib.ehs_prolong_add.argtypes = [vp, i, i, vp, vp]
     for name in EXPORTS:
         getattr(lib, name)
     _lib = lib
@@ -201,6 +203,16 @@ class Solver:
     def vcycle(self, b, x, prec=None):
         prec = _prec_of(x) if prec is None else prec
         self._check(self.lib.ehs_vcycle(self.ctx, prec, _ptr(b), _ptr(x)))
+
+    def residual_restrict(self, b, x, rc, level=0, prec=None):
+        """rc = P_l^T (b - K_l x)."""
+        prec = _prec_of(x) if prec is None else prec
+        self._check(self.lib.ehs_residual_restrict(self.ctx, level, prec, _ptr(b), _ptr(x), _ptr(rc)))
+
+    def prolong_add(self, ec, x, level=0, prec=None):
+        """x += P_l ec."""
+        prec = _prec_of(x) if prec is None else prec
+        self._check(self.lib.ehs_prolong_add(self.ctx, level, prec, _ptr(ec), _ptr(x)))
 
     def coarse_solve(self, b, x, prec=None):
         prec = _prec_of(x) if prec is None else prec

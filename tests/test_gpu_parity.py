@@ -101,8 +101,11 @@ def test_galerkin_levels_match_oracle(case):
     S.close()
 
 
-@pytest.mark.parametrize("case", ["2d", "3d"])
-def test_smooth_matches_oracle(case):
+@pytest.mark.parametrize("case,nsweeps", [("2d", 1), ("3d", 1), ("2d", 2), ("2d", 3)])
+def test_smooth_matches_oracle(case, nsweeps):
+    """nsweeps red-black sweeps of every smoothed level (2D complex64 level 0:
+    the fused whole-sweep kernel, ping-ponging between x and the level's
+    scratch)."""
     ehs = _ehs()
     meds = _media_2d(32, 2) if case == "2d" else _media_3d(16, 1)
     levels = 3
@@ -115,34 +118,81 @@ def test_smooth_matches_oracle(case):
         for dt, tol in ((torch.complex128, 1e-11), (torch.complex64, 2e-5)):
             bd = torch.from_numpy(b_).to("cuda", dt)
             xd = torch.from_numpy(x_).to("cuda", dt)
-            S.smooth(bd, xd, level=l, nsweeps=1)
+            S.smooth(bd, xd, level=l, nsweeps=nsweeps)
             for it, med in enumerate(meds):
                 H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels)
                 be = op.slots_to_dofs(bd[it].cpu().numpy().astype(np.complex128), gshape)
                 xe = op.slots_to_dofs(torch.from_numpy(x_[it]).to(dt).numpy().astype(np.complex128), gshape)
-                xr = op.dofs_to_slots(H.relax(l, be, xe), gshape)
+                for _ in range(nsweeps):
+                    xe = H.relax(l, be, xe)
+                xr = op.dofs_to_slots(xe, gshape)
                 got = xd[it].cpu().numpy()
                 assert _err(got, xr) <= tol, (l, dt, it, _err(got, xr))
     S.close()
 
 
-@pytest.mark.parametrize("case,levels", [("2d", 3), ("2d", 4), ("3d", 3)])
-def test_vcycle_matches_oracle(case, levels):
+@pytest.mark.parametrize("case,levels,n,nu,unfused", [("2d", 3, 64, 1, 0), ("2d", 4, 64, 1, 0), ("3d", 3, 16, 1, 0),
+                                                     ("2d", 3, 64, 1, 1), ("2d", 3, 48, 1, 0), ("2d", 3, 64, 2, 0),
+                                                     ("2d", 3, 64, 3, 0)])
+def test_vcycle_matches_oracle(case, levels, n, nu, unfused, monkeypatch):
+    """One V(nu, nu) cycle.  In 2D complex64 the fine level runs the fused
+    kernels (whole red-black sweeps, residual + restriction in one pass,
+    prolongation folded into the first post-smoothing sweep) when the grid
+    splits into their tiles (64 x 64); 48 x 48 and EHS_FINE_UNFUSED=1 run the
+    per-colour kernels and the separate transfers."""
     ehs = _ehs()
-    meds = _media_2d(64, 2) if case == "2d" else _media_3d(16, 1)
-    S = ehs.solver_for(meds, levels=levels, alpha=0.2)
+    if unfused:
+        monkeypatch.setenv("EHS_FINE_UNFUSED", "1")
+    meds = _media_2d(n, 2) if case == "2d" else _media_3d(n, 1)
+    S = ehs.solver_for(meds, levels=levels, alpha=0.2, nu_pre=nu, nu_post=nu)
     shape = meds[0].shape
     b_ = _rand_slots(shape, S.items, 5)
     for dt, tol in ((torch.complex128, 1e-10), (torch.complex64, 5e-5)):
         bd = torch.from_numpy(b_).to("cuda", dt)
-        xd = torch.zeros_like(bd)
+        xd = torch.full_like(bd, 7.0)                # the cycle ignores the input of x
         S.vcycle(bd, xd)
         for it, med in enumerate(meds):
             H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, levels,
                              w=[0.75, 0.5, 0.25, 0.25, 0.25][:levels - 1])
-            xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape)), shape)
+            xr = op.dofs_to_slots(H.cycle(op.slots_to_dofs(b_[it], shape), nu1=nu, nu2=nu), shape)
             assert _err(xd[it].cpu().numpy(), xr) <= tol, (dt, it, _err(xd[it].cpu().numpy(), xr))
     S.close()
+
+
+@pytest.mark.parametrize("n,unfused", [(64, 0), (64, 1), (48, 0)])
+def test_transfers_match_oracle(n, unfused, monkeypatch):
+    """ehs_residual_restrict (P^T (b - K_l x), Algorithm TwoCycle step 2) and
+    ehs_prolong_add (x + P e_c, step 4) on every level pair against the
+    oracle's assembled K_l and P_l; 2D complex64 level 0 of a 64 x 64 grid runs
+    the fused residual + restriction kernel, 48 x 48 or EHS_FINE_UNFUSED=1 the
+    residual pass and the separate restriction.  Also 3D (16^3)."""
+    ehs = _ehs()
+    if unfused:
+        monkeypatch.setenv("EHS_FINE_UNFUSED", "1")
+    for meds in (_media_2d(n, 2), _media_3d(16, 1)):
+        S = ehs.solver_for(meds, levels=3, alpha=0.2)
+        for l in range(2):
+            fs, cs = tuple(S.level_shape(l)[2:]), tuple(S.level_shape(l + 1)[2:])
+            b_ = _rand_slots(fs, S.items, 60 + l)
+            x_ = _rand_slots(fs, S.items, 70 + l)
+            e_ = _rand_slots(cs, S.items, 80 + l)
+            for dt, npt, tol in ((torch.complex128, np.complex128, 1e-12), (torch.complex64, np.complex64, 1e-5)):
+                bd = torch.from_numpy(b_).to("cuda", dt)
+                xd = torch.from_numpy(x_).to("cuda", dt)
+                ed = torch.from_numpy(e_).to("cuda", dt)
+                rc = torch.full((S.items, len(fs) + 1) + cs, 3.0, dtype=dt, device="cuda")
+                S.residual_restrict(bd, xd, rc, level=l)
+                S.prolong_add(ed, xd, level=l)
+                for it, med in enumerate(meds):
+                    H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, 3)
+                    xe = op.slots_to_dofs(x_[it].astype(npt).astype(np.complex128), fs)
+                    be = op.slots_to_dofs(b_[it].astype(npt).astype(np.complex128), fs)
+                    ee = op.slots_to_dofs(e_[it].astype(npt).astype(np.complex128), cs)
+                    rr = op.dofs_to_slots(H.P[l].T @ (be - H.K[l] @ xe), cs)
+                    xr = op.dofs_to_slots(xe + H.P[l] @ ee, fs)
+                    assert _err(rc[it].cpu().numpy(), rr) <= tol, (n, l, dt, it, _err(rc[it].cpu().numpy(), rr))
+                    assert _err(xd[it].cpu().numpy(), xr) <= tol, (n, l, dt, it, _err(xd[it].cpu().numpy(), xr))
+        S.close()
 
 
 def _solve_both(meds, levels, prec, nrhs=1, host=False, **kw):
