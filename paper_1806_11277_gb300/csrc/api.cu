@@ -232,8 +232,11 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
     const long long nt = (long long)H.nsets * L.L.nslot * L.g.ncell;
     L.tab32 = dalloc<float2>(c, nt);
     launch_table_cast<float>(nt, L.tab64, L.tab32, c->s); cnt(); post();
-    if (H.half) {
-      L.tabh = dalloc<float>(c, nt);   // 4 bytes per complex coefficient
+    if (H.half && d == 2) {   // 4 bytes per complex coefficient, one of each mirrored pair (K_c = K_c^T)
+      L.tabh = dalloc<float>(c, (size_t)H.nsets * half_table_slots(L.L) * L.g.ncell);
+      launch_table_half_sym(L.g, H.nsets, L.L, L.tab64, L.tabh, H.half, c->s); cnt(); post();
+    } else if (H.half) {      // 3D: the whole table, 4 bytes per complex coefficient
+      L.tabh = dalloc<float>(c, nt);
       launch_table_half(nt, L.tab64, L.tabh, H.half, c->s); cnt(); post();
     }
     Lf = L.L;

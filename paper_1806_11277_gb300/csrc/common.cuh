@@ -283,6 +283,112 @@ static_assert(same_layout(level_layout(2, 2), level_layout(2, 3)), "2D Galerkin 
 static_assert(same_layout(level_layout(3, 2), level_layout(3, 3)), "3D Galerkin boxes settle at level 2");
 static_assert(level_layout(2, 1).nslot == 87 && level_layout(2, 2).nslot == 135, "2D table sizes");
 
+// Half ("symmetric") storage of a Galerkin table.  K_c = P^T K_s P is complex
+// symmetric (P real, K_s = K_s^T), so the coefficient (row a, column b, offset
+// o) at cell c equals (row b, column a, offset -o) at cell c + o.  Stored: pairs
+// a < b whole, pairs a == b for offsets o >= 0 in lexicographic (z, y, x)
+// order, pairs a > b not at all; a row reads an unstored coefficient from its
+// mirror's compact slot at the neighbour cell c + o.
+#define EHS_MAXSLOT 960
+struct HalfMap {
+  int nslot;                  // stored coefficients per cell
+  int slot[EHS_MAXSLOT];      // per full slot: the compact slot holding it (its own or its mirror's)
+  bool mir[EHS_MAXSLOT];      // the full slot is read from its mirror at cell c + o
+  int full[EHS_MAXSLOT];      // per compact slot: the full slot stored there
+  bool ok;                    // every unstored coefficient has a stored mirror
+};
+__host__ __device__ constexpr bool half_stored(int a, int b, int ox, int oy, int oz) {
+  return a < b || (a == b && (oz > 0 || (oz == 0 && (oy > 0 || (oy == 0 && ox >= 0)))));
+}
+__host__ __device__ constexpr HalfMap make_half_map(const StencilLayout& L) {
+  HalfMap H{};
+  H.ok = L.nslot <= EHS_MAXSLOT;
+  int n = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int q = 0; q < L.npair; ++q) {
+      const PairBox& P = L.p[q];
+      for (int iz = 0; iz < P.ext[2]; ++iz)
+        for (int iy = 0; iy < P.ext[1]; ++iy)
+          for (int ix = 0; ix < P.ext[0]; ++ix) {
+            const int ox = P.lo[0] + ix, oy = P.lo[1] + iy, oz = P.lo[2] + iz;
+            const int sl = P.base + (iz * P.ext[1] + iy) * P.ext[0] + ix;
+            if (sl >= EHS_MAXSLOT) { H.ok = false; continue; }
+            const bool st = half_stored(P.a, P.b, ox, oy, oz);
+            if (pass == 0 && st) {             // stored entries, numbered in full-slot order
+              H.slot[sl] = n; H.mir[sl] = false; H.full[n] = sl; ++n;
+            } else if (pass == 1 && !st) {     // the others read their mirror
+              const int ms = st_slot(L, P.b, P.a, -ox, -oy, -oz);
+              if (ms < 0 || !half_stored(P.b, P.a, -ox, -oy, -oz)) { H.ok = false; continue; }
+              H.slot[sl] = H.slot[ms]; H.mir[sl] = true;
+            }
+          }
+    }
+  H.nslot = n;
+  return H;
+}
+// The same numbering in closed form, for kernels that walk a row's boxes with the
+// pair index q known at compile time and the box position ti (x fastest, as the
+// full slots) unrolled: pairs a < b store their box whole from half_base(q);
+// a diagonal pair's box is symmetric about 0, so its offsets o >= 0 are the
+// positions ti >= (n-1)/2 of its n entries, and the mirror of ti is n-1-ti;
+// the box of a pair a > b is the point reflection of pair (b, a)'s box.
+__host__ __device__ constexpr int half_base(const StencilLayout& L, int q) {
+  int n = 0;
+  for (int k = 0; k < q; ++k) {
+    const PairBox& P = L.p[k];
+    const int ne = P.ext[0] * P.ext[1] * P.ext[2];
+    n += P.a < P.b ? ne : (P.a == P.b ? (ne + 1) / 2 : 0);
+  }
+  return n;
+}
+__host__ __device__ constexpr int half_index(const StencilLayout& L, int q, int ti, bool& mir) {
+  const PairBox& P = L.p[q];
+  const int ne = P.ext[0] * P.ext[1] * P.ext[2];
+  if (P.a < P.b) { mir = false; return half_base(L, q) + ti; }
+  if (P.a == P.b) {
+    const int tc = (ne - 1) / 2;
+    mir = ti < tc;
+    return half_base(L, q) + (mir ? tc - ti : ti - tc);
+  }
+  mir = true;
+  return half_base(L, L.pidx[P.b][P.a]) + (ne - 1 - ti);
+}
+__host__ __device__ constexpr int half_slot_c(const StencilLayout& L, int q, int ti) {
+  bool m = false;
+  return half_index(L, q, ti, m);
+}
+__host__ __device__ constexpr bool half_mir_c(const StencilLayout& L, int q, int ti) {
+  bool m = false;
+  half_index(L, q, ti, m);
+  return m;
+}
+// the closed form agrees with make_half_map on every slot
+__host__ __device__ constexpr bool half_index_agrees(const StencilLayout& L) {
+  const HalfMap H = make_half_map(L);
+  if (!H.ok) return false;
+  for (int q = 0; q < L.npair; ++q) {
+    const PairBox& P = L.p[q];
+    const int ne = P.ext[0] * P.ext[1] * P.ext[2];
+    if (P.a == P.b && (ne % 2 == 0 || P.lo[0] != -(P.ext[0] - 1) / 2 || P.lo[1] != -(P.ext[1] - 1) / 2 ||
+                       P.lo[2] != -(P.ext[2] - 1) / 2))
+      return false;
+    for (int ti = 0; ti < ne; ++ti) {
+      bool mir = false;
+      const int hs = half_index(L, q, ti, mir);
+      if (hs != H.slot[P.base + ti] || mir != H.mir[P.base + ti]) return false;
+    }
+  }
+  return true;
+}
+static_assert(half_index_agrees(level_layout(2, 1)) && half_index_agrees(level_layout(2, 2)) &&
+              half_index_agrees(level_layout(3, 1)) && half_index_agrees(level_layout(3, 2)),
+              "closed-form half-table index");
+static_assert(make_half_map(level_layout(2, 1)).ok && make_half_map(level_layout(2, 1)).nslot == 45,
+              "2D level-1 half table");
+static_assert(make_half_map(level_layout(2, 2)).ok && make_half_map(level_layout(2, 2)).nslot == 69,
+              "2D half table from level 2 on");
+static_assert(make_half_map(level_layout(3, 1)).ok && make_half_map(level_layout(3, 2)).ok, "3D half tables");
+
 // a valid unknown slot?  (u_k at i_k == 0 is a boundary face)
 EHS_HD bool slot_valid(int a, int d, const int i[3]) { return a == d || i[a] >= 1; }
 

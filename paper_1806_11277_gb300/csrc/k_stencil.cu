@@ -140,11 +140,34 @@ __global__ void k_table_cast(long long n, const double2* in, C* out) {
   }
 }
 
+// Compact slot and mirror flag of box position ti of pair Q in a half table
+// (half_index in common.cuh with the pair's constants folded).
+template <int D, int LV, int Q>
+__device__ __forceinline__ int half_slot_of(int ti, bool& mir) {
+  constexpr StencilLayout L = level_layout(D, LV);
+  constexpr int a = L.p[Q].a, b = L.p[Q].b;
+  constexpr int ne = L.p[Q].ext[0] * L.p[Q].ext[1] * L.p[Q].ext[2];
+  constexpr int hb = half_base(L, Q);
+  if constexpr (a < b) {
+    mir = false;
+    return hb + ti;
+  } else if constexpr (a == b) {
+    constexpr int tc = (ne - 1) / 2;
+    mir = ti < tc;
+    return hb + (mir ? tc - ti : ti - tc);
+  } else {
+    constexpr int hbm = half_base(L, L.pidx[b][a]);
+    mir = true;
+    return hbm + (ne - 1 - ti);
+  }
+}
+
 // Row a of the stored operator at cell c (coords i), with the stencil box of
 // Galerkin level variant LV (1 = first coarse level, 2 = all coarser ones)
 // known at compile time so that every table and vector load of the row is
-// issued back to back.
-template <typename T, typename TT, int D, int LV, int Q, int QE>
+// issued back to back.  SYM: the table is stored half (common.cuh HalfMap), an
+// unstored coefficient read from its mirror at the neighbour cell.
+template <typename T, typename TT, int D, int LV, bool SYM, int Q, int QE>
 __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
                                         const TT* __restrict__ tab,
                                         long long c, const int i[3],
@@ -168,24 +191,32 @@ __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
         for (int ox = 0; ox < e0; ++ox) {
           const int jx = i[0] + lo0 + ox;
           if (rin && jx >= 0 && jx < g.n[0]) {
-            const int sl = base + (oz * e1 + oy) * e0 + ox;
+            const int ti = (oz * e1 + oy) * e0 + ox;
             const long long cj = c + (lo2 + oz) * sz + (lo1 + oy) * sy + (lo0 + ox);
-            y = cfma(ldtab<T>(tab + (long long)sl * N + c), __ldg(xb + cj), y);
+            const TT* tp;
+            if constexpr (SYM) {
+              bool mir = false;
+              const int hs = half_slot_of<D, LV, Q>(ti, mir);
+              tp = tab + (long long)hs * N + (mir ? cj : c);
+            } else {
+              tp = tab + (long long)(base + ti) * N + c;
+            }
+            y = cfma(ldtab<T>(tp), __ldg(xb + cj), y);
           }
         }
       }
     }
-    row_acc<T, TT, D, LV, Q + 1, QE>(y, g, tab, c, i, x);
+    row_acc<T, TT, D, LV, SYM, Q + 1, QE>(y, g, tab, c, i, x);
   }
 }
 
-template <typename T, typename TT, int D, int LV, int A>
+template <typename T, typename TT, int D, int LV, bool SYM, int A>
 __device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const TT* tab,
                                                            long long c, const int i[3],
                                                            const typename CT<T>::type* x) {
   constexpr StencilLayout L = level_layout(D, LV);
   typename CT<T>::type y = czero<typename CT<T>::type>();
-  row_acc<T, TT, D, LV, L.row_first[A], L.row_first[A + 1]>(y, g, tab, c, i, x);
+  row_acc<T, TT, D, LV, SYM, L.row_first[A], L.row_first[A + 1]>(y, g, tab, c, i, x);
   return y;
 }
 
@@ -194,7 +225,7 @@ __device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const T
 // a warp and the row's stencil loop is fully unrolled.  mode 0: y = A x,
 // mode 1: y = b - A x.  colour >= 0 restricts the pressure rows to cells of
 // that colour (the rows a red-black half-sweep needs).
-template <typename T, typename TT, int D, int LV, int A>
+template <typename T, typename TT, int D, int LV, bool SYM, int A>
 __device__ __forceinline__ void st_one_row(const Grid& g, const TT* ts, long long c,
                                            const int i[3], const typename CT<T>::type* xv,
                                            const typename CT<T>::type* bv, typename CT<T>::type* yv,
@@ -203,13 +234,13 @@ __device__ __forceinline__ void st_one_row(const Grid& g, const TT* ts, long lon
   const long long N = g.ncell;
   Cx r = czero<Cx>();
   if (slot_valid(A, D, i)) {
-    r = st_row_ct<T, TT, D, LV, A>(g, ts, c, i, xv);
+    r = st_row_ct<T, TT, D, LV, SYM, A>(g, ts, c, i, xv);
     if (mode) r = csub(__ldg(bv + (long long)A * N + c), r);
   }
   yv[(long long)A * N + c] = r;
 }
 
-template <typename T, typename TT, int D, int LV>
+template <typename T, typename TT, int D, int LV, bool SYM>
 __global__ void __launch_bounds__(256) k_st_rows(Grid g, int nrhs, const TT* __restrict__ tab,
                                                  const typename CT<T>::type* __restrict__ x,
                                                  const typename CT<T>::type* __restrict__ b,
@@ -225,12 +256,13 @@ __global__ void __launch_bounds__(256) k_st_rows(Grid g, int nrhs, const TT* __r
   if (a == D && colour >= 0 && ((i[0] + i[1] + i[2]) & 1) != colour) return;
   const long long N = g.ncell;
   const long long vo = (long long)item * (D + 1) * N;
-  const TT* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  constexpr int nslot = SYM ? half_base(L, L.npair) : L.nslot;
+  const TT* ts = tab + (long long)(item / nrhs) * nslot * N;
   const typename CT<T>::type* bv = mode ? b + vo : nullptr;
-  if (a == 0) st_one_row<T, TT, D, LV, 0>(g, ts, c, i, x + vo, bv, y + vo, mode);
-  else if (a == 1) st_one_row<T, TT, D, LV, 1>(g, ts, c, i, x + vo, bv, y + vo, mode);
-  else if (a == 2) st_one_row<T, TT, D, LV, 2>(g, ts, c, i, x + vo, bv, y + vo, mode);
-  else if constexpr (D == 3) st_one_row<T, TT, D, LV, 3>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  if (a == 0) st_one_row<T, TT, D, LV, SYM, 0>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if (a == 1) st_one_row<T, TT, D, LV, SYM, 1>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if (a == 2) st_one_row<T, TT, D, LV, SYM, 2>(g, ts, c, i, x + vo, bv, y + vo, mode);
+  else if constexpr (D == 3) st_one_row<T, TT, D, LV, SYM, 3>(g, ts, c, i, x + vo, bv, y + vo, mode);
 }
 
 // Two-cells-per-thread variant of the residual pass: cells c and c+1 (same x
@@ -265,7 +297,7 @@ template <> struct Pair2<__nv_bfloat162> {
   }
 };
 
-template <typename T, typename TT, int D, int LV, int Q, int QE>
+template <typename T, typename TT, int D, int LV, bool SYM, int Q, int QE>
 __device__ __forceinline__ void row_acc2(typename CT<T>::type& y0, typename CT<T>::type& y1, const Grid& g,
                                          const TT* __restrict__ tab, long long c, const int i[3],
                                          const typename CT<T>::type* __restrict__ x) {
@@ -288,20 +320,39 @@ __device__ __forceinline__ void row_acc2(typename CT<T>::type& y0, typename CT<T
 #pragma unroll
         for (int ox = 0; ox < e0; ++ox) {
           const int jx = i[0] + lo0 + ox;       // neighbour of cell c; jx + 1 is the one of c + 1
-          const int sl = base + (oz * e1 + oy) * e0 + ox;
+          const int ti = (oz * e1 + oy) * e0 + ox;
           const long long cj = c + (lo2 + oz) * sz + (lo1 + oy) * sy + (lo0 + ox);
-          Cx t0, t1;
-          Pair2<TT>::ld(tab + (long long)sl * N + c, t0, t1);
+          Cx t0 = czero<Cx>(), t1 = czero<Cx>();
+          if constexpr (SYM) {
+            // the mirror of cell c's coefficient sits at cell cj, c + 1's at cj + 1; cj is even
+            // (aligned pair load) when the x offset is even (n_x is even here)
+            bool mir = false;
+            const int hs = half_slot_of<D, LV, Q>(ti, mir);
+            const TT* tp = tab + (long long)hs * N + (mir ? cj : c);
+            const bool in0 = rin && jx >= 0 && jx < g.n[0], in1 = rin && jx + 1 >= 0 && jx + 1 < g.n[0];
+            if (!mir || ((lo0 + ox) & 1) == 0) {
+              if (!mir || (in0 && in1)) Pair2<TT>::ld(tp, t0, t1);
+              else {                            // a mirror cell outside the grid is not read
+                if (in0) t0 = ldtab<T>(tp);
+                if (in1) t1 = ldtab<T>(tp + 1);
+              }
+            } else {
+              if (in0) t0 = ldtab<T>(tp);
+              if (in1) t1 = ldtab<T>(tp + 1);
+            }
+          } else {
+            Pair2<TT>::ld(tab + (long long)(base + ti) * N + c, t0, t1);
+          }
           if (rin && jx >= 0 && jx < g.n[0]) y0 = cfma(t0, __ldg(xb + cj), y0);
           if (rin && jx + 1 >= 0 && jx + 1 < g.n[0]) y1 = cfma(t1, __ldg(xb + cj + 1), y1);
         }
       }
     }
-    row_acc2<T, TT, D, LV, Q + 1, QE>(y0, y1, g, tab, c, i, x);
+    row_acc2<T, TT, D, LV, SYM, Q + 1, QE>(y0, y1, g, tab, c, i, x);
   }
 }
 
-template <typename T, typename TT, int D, int LV, int A>
+template <typename T, typename TT, int D, int LV, bool SYM, int A>
 __device__ __forceinline__ void st_two_rows(const Grid& g, const TT* ts, long long c, const int i[3],
                                             const typename CT<T>::type* xv, const typename CT<T>::type* bv,
                                             typename CT<T>::type* yv, int mode, int colour) {
@@ -309,7 +360,7 @@ __device__ __forceinline__ void st_two_rows(const Grid& g, const TT* ts, long lo
   constexpr StencilLayout L = level_layout(D, LV);
   const long long N = g.ncell;
   Cx y0 = czero<Cx>(), y1 = czero<Cx>();
-  row_acc2<T, TT, D, LV, L.row_first[A], L.row_first[A + 1]>(y0, y1, g, ts, c, i, xv);
+  row_acc2<T, TT, D, LV, SYM, L.row_first[A], L.row_first[A + 1]>(y0, y1, g, ts, c, i, xv);
   const int i1[3] = {i[0] + 1, i[1], i[2]};
   const bool v0 = slot_valid(A, D, i), v1 = slot_valid(A, D, i1);
   const int par = (i[0] + i[1] + i[2]) & 1;
@@ -322,7 +373,7 @@ __device__ __forceinline__ void st_two_rows(const Grid& g, const TT* ts, long lo
   if (w1) yv[(long long)A * N + c + 1] = v1 ? y1 : czero<Cx>();
 }
 
-template <typename T, typename TT, int D, int LV>
+template <typename T, typename TT, int D, int LV, bool SYM>
 __global__ void k_st_rows2(Grid g, int nrhs, const TT* __restrict__ tab, const typename CT<T>::type* __restrict__ x,
                            const typename CT<T>::type* __restrict__ b, typename CT<T>::type* __restrict__ y,
                            int mode, int colour, const int* __restrict__ il) {
@@ -336,18 +387,57 @@ __global__ void k_st_rows2(Grid g, int nrhs, const TT* __restrict__ tab, const t
   cell_coords(g, c, i);
   const long long N = g.ncell;
   const long long vo = (long long)item * (D + 1) * N;
-  const TT* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  constexpr int nslot = SYM ? half_base(L, L.npair) : L.nslot;
+  const TT* ts = tab + (long long)(item / nrhs) * nslot * N;
   const typename CT<T>::type* bv = mode ? b + vo : nullptr;
-  if (a == 0) st_two_rows<T, TT, D, LV, 0>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
-  else if (a == 1) st_two_rows<T, TT, D, LV, 1>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
-  else if (a == 2) st_two_rows<T, TT, D, LV, 2>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
-  else if constexpr (D == 3) st_two_rows<T, TT, D, LV, 3>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
+  if (a == 0) st_two_rows<T, TT, D, LV, SYM, 0>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
+  else if (a == 1) st_two_rows<T, TT, D, LV, SYM, 1>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
+  else if (a == 2) st_two_rows<T, TT, D, LV, SYM, 2>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
+  else if constexpr (D == 3) st_two_rows<T, TT, D, LV, SYM, 3>(g, ts, c, i, x + vo, bv, y + vo, mode, colour);
 }
 
 // Update pass of one colour: the economic cell block (stored diagonal and
 // displacement-pressure couplings) is solved for every cell of the colour
 // from the residual r of the residual pass; xo receives the new iterate.
-template <typename T, typename TT, int D, int LV>
+// Coefficient (row A, column B, offset O) of the row at cell c from a full table
+// (slot of the layout at cell c) or a half table (compact slot at c, or its
+// mirror's at c + O; off = the linear cell offset of O), slots folded at
+// compile time.
+template <typename T, typename TT, int D, int LV, bool SYM, int A, int B, int OX, int OY, int OZ>
+__device__ __forceinline__ typename CT<T>::type tab_coef(const TT* ts, long long N, long long c, long long off) {
+  constexpr StencilLayout L = level_layout(D, LV);
+  constexpr int sl = st_slot(L, A, B, OX, OY, OZ);
+  static_assert(sl >= 0, "coefficient outside the stored box");
+  if constexpr (SYM) {
+    constexpr int q = L.pidx[A][B];
+    constexpr bool mir = half_mir_c(L, q, sl - L.p[q].base);
+    constexpr int hs = half_slot_c(L, q, sl - L.p[q].base);
+    return ldtab<T>(ts + (long long)hs * N + (mir ? c + off : c));
+  } else {
+    return ldtab<T>(ts + (long long)sl * N + c);
+  }
+}
+
+// the block coefficients of component K of the economic cell update: diagonals of the low
+// and high face, their couplings to the cell's pressure, and back
+template <typename T, typename TT, int D, int LV, bool SYM, int K>
+__device__ __forceinline__ void vupd_coefs(const TT* ts, long long N, long long c, long long sk, bool lo_ok,
+                                           bool hi_ok, typename CT<T>::type* dg, typename CT<T>::type* gr,
+                                           typename CT<T>::type* gc) {
+  constexpr int E0 = K == 0, E1 = K == 1, E2 = K == 2;
+  if (lo_ok) {
+    dg[K] = tab_coef<T, TT, D, LV, SYM, K, K, 0, 0, 0>(ts, N, c, 0);
+    gr[K] = tab_coef<T, TT, D, LV, SYM, K, D, 0, 0, 0>(ts, N, c, 0);
+    gc[K] = tab_coef<T, TT, D, LV, SYM, D, K, 0, 0, 0>(ts, N, c, 0);
+  }
+  if (hi_ok) {
+    dg[D + K] = tab_coef<T, TT, D, LV, SYM, K, K, 0, 0, 0>(ts, N, c + sk, 0);
+    gr[D + K] = tab_coef<T, TT, D, LV, SYM, K, D, -E0, -E1, -E2>(ts, N, c + sk, -sk);
+    gc[D + K] = tab_coef<T, TT, D, LV, SYM, D, K, E0, E1, E2>(ts, N, c, sk);
+  }
+}
+
+template <typename T, typename TT, int D, int LV, bool SYM>
 __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const TT* __restrict__ tab,
                                                  T wu, T wp, int colour,
                                                  const typename CT<T>::type* __restrict__ res,
@@ -361,7 +451,8 @@ __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const TT* __r
   if (t >= N / 2) return;
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   const long long vo = (long long)item * (D + 1) * N;
-  const TT* ts = tab + (long long)(item / nrhs) * L.nslot * N;
+  constexpr int nslot = SYM ? half_base(L, L.npair) : L.nslot;
+  const TT* ts = tab + (long long)(item / nrhs) * nslot * N;
   const Cx* x = xi + vo;
   const Cx* rr = res + vo;
   Cx* xout = xo + vo;
@@ -376,28 +467,16 @@ __global__ void __launch_bounds__(128) k_st_vupd(Grid g, int nrhs, const TT* __r
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const long long sk = stride_of(g, k);
-    const int sd = st_slot(L, k, k, 0, 0, 0);
-    const int sg0 = st_slot(L, k, D, 0, 0, 0);
-    const int sg1 = st_slot(L, k, D, k == 0 ? -1 : 0, k == 1 ? -1 : 0, k == 2 ? -1 : 0);
-    const int sc0 = st_slot(L, D, k, 0, 0, 0);
-    const int sc1 = st_slot(L, D, k, k == 0 ? 1 : 0, k == 1 ? 1 : 0, k == 2 ? 1 : 0);
     ok[k] = i[k] >= 1;
-    if (ok[k]) {
-      r[k] = __ldg(rr + (long long)k * N + c);
-      dg[k] = ldtab<T>(ts + (long long)sd * N + c);
-      gr[k] = ldtab<T>(ts + (long long)sg0 * N + c);
-      gc_[k] = ldtab<T>(ts + (long long)sc0 * N + c);
-    }
     ok[D + k] = i[k] + 1 < g.n[k];
-    if (ok[D + k]) {
-      r[D + k] = __ldg(rr + (long long)k * N + c + sk);
-      dg[D + k] = ldtab<T>(ts + (long long)sd * N + c + sk);
-      gr[D + k] = ldtab<T>(ts + (long long)sg1 * N + c + sk);
-      gc_[D + k] = ldtab<T>(ts + (long long)sc1 * N + c);
-    }
+    if (ok[k]) r[k] = __ldg(rr + (long long)k * N + c);
+    if (ok[D + k]) r[D + k] = __ldg(rr + (long long)k * N + c + sk);
   }
+  vupd_coefs<T, TT, D, LV, SYM, 0>(ts, N, c, stride_of(g, 0), ok[0], ok[D], dg, gr, gc_);
+  vupd_coefs<T, TT, D, LV, SYM, 1>(ts, N, c, stride_of(g, 1), ok[1], ok[D + 1], dg, gr, gc_);
+  if constexpr (D == 3) vupd_coefs<T, TT, D, LV, SYM, 2>(ts, N, c, stride_of(g, 2), ok[2], ok[D + 2], dg, gr, gc_);
   r[2 * D] = __ldg(rr + (long long)D * N + c);
-  Cx sch = ldtab<T>(ts + (long long)st_slot(L, D, D, 0, 0, 0) * N + c);
+  Cx sch = tab_coef<T, TT, D, LV, SYM, D, D, 0, 0, 0>(ts, N, c, 0);
   Cx rp = r[2 * D];
   Cx dinv[2 * D];
 #pragma unroll
@@ -544,7 +623,7 @@ __global__ void __launch_bounds__(128) k_st_vupd_full(Grid g, int nrhs, const TI
 // (= ((m * nsub) + s) * nrhs + r) receives (b - K_c x) at coarsest slot
 // map[s][e] of item m * nrhs + r, or 0 on padding (map -1); only the rows of
 // the colour's subdomains are evaluated.
-template <typename T, typename TT, int D, int LV>
+template <typename T, typename TT, int D, int LV, bool SYM>
 __global__ void __launch_bounds__(128) k_st_resid_gather(Grid g, int nrhs, int nsub, int nloc,
                                                          const int* __restrict__ map, const TT* __restrict__ tab,
                                                          const typename CT<T>::type* __restrict__ x,
@@ -564,13 +643,14 @@ __global__ void __launch_bounds__(128) k_st_resid_gather(Grid g, int nrhs, int n
     const int a = (int)(gs / N);
     const long long c = gs % N;
     const long long vo = (long long)(m * nrhs + r) * (D + 1) * N;
-    const TT* ts = tab + (long long)m * L.nslot * N;
+    constexpr int nslot = SYM ? half_base(L, L.npair) : L.nslot;
+    const TT* ts = tab + (long long)m * nslot * N;
     int i[3];
     cell_coords(g, c, i);
-    if (a == 0) v = st_row_ct<T, TT, D, LV, 0>(g, ts, c, i, x + vo);
-    else if (a == 1) v = st_row_ct<T, TT, D, LV, 1>(g, ts, c, i, x + vo);
-    else if (a == 2) v = st_row_ct<T, TT, D, LV, 2>(g, ts, c, i, x + vo);
-    else if constexpr (D == 3) v = st_row_ct<T, TT, D, LV, 3>(g, ts, c, i, x + vo);
+    if (a == 0) v = st_row_ct<T, TT, D, LV, SYM, 0>(g, ts, c, i, x + vo);
+    else if (a == 1) v = st_row_ct<T, TT, D, LV, SYM, 1>(g, ts, c, i, x + vo);
+    else if (a == 2) v = st_row_ct<T, TT, D, LV, SYM, 2>(g, ts, c, i, x + vo);
+    else if constexpr (D == 3) v = st_row_ct<T, TT, D, LV, SYM, 3>(g, ts, c, i, x + vo);
     v = csub(__ldg(b + vo + gs), v);
   }
   out[(long long)bl * nloc + e] = v;
@@ -618,7 +698,7 @@ static int layout_variant(const StencilLayout& L, int d) {
 static const int kRowsCpt[ST_ROWS_VARIANTS] = {1, 2, 1, 2};
 static const int kRowsBs[ST_ROWS_VARIANTS] = {128, 128, 256, 64};
 
-template <typename T, typename TT>
+template <typename T, typename TT, bool SYM>
 static void st_apply_t(const Grid& g, int items, int nrhs, int v, const TT* tab, const typename CT<T>::type* x,
                        const typename CT<T>::type* b, typename CT<T>::type* y, int mode, int colour,
                        int var, cudaStream_t s) {
@@ -627,56 +707,76 @@ static void st_apply_t(const Grid& g, int items, int nrhs, int v, const TT* tab,
   if (kRowsCpt[var] == 1) {
     const dim3 gr((unsigned)((g.ncell + bs - 1) / bs), sel_items(items), g.d + 1);
     if (g.d == 2) {
-      if (v == 1) k_st_rows<T, TT, 2, 1><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
-      else k_st_rows<T, TT, 2, 2><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
-    } else {
-      if (v == 1) k_st_rows<T, TT, 3, 1><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
-      else k_st_rows<T, TT, 3, 2><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+      if (v == 1) k_st_rows<T, TT, 2, 1, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+      else k_st_rows<T, TT, 2, 2, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+    } else if constexpr (!SYM) {
+      if (v == 1) k_st_rows<T, TT, 3, 1, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+      else k_st_rows<T, TT, 3, 2, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
     }
   } else {
     const dim3 gr((unsigned)((g.ncell / 2 + bs - 1) / bs), sel_items(items), g.d + 1);
     if (g.d == 2) {
-      if (v == 1) k_st_rows2<T, TT, 2, 1><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
-      else k_st_rows2<T, TT, 2, 2><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
-    } else {
-      if (v == 1) k_st_rows2<T, TT, 3, 1><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
-      else k_st_rows2<T, TT, 3, 2><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+      if (v == 1) k_st_rows2<T, TT, 2, 1, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+      else k_st_rows2<T, TT, 2, 2, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+    } else if constexpr (!SYM) {
+      if (v == 1) k_st_rows2<T, TT, 3, 1, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
+      else k_st_rows2<T, TT, 3, 2, SYM><<<gr, bs, 0, s>>>(g, nrhs, tab, x, b, y, mode, colour, g_sel.list);
     }
   }
 }
-template <typename T, typename TT>
+template <typename T, typename TT, bool SYM>
 static void st_vupd_t(const Grid& g, int items, int nrhs, int v, const TT* tab, T wu, T wp, int colour,
                       const typename CT<T>::type* r, const typename CT<T>::type* xi, typename CT<T>::type* xo,
                       cudaStream_t s) {
   const dim3 gu((unsigned)((g.ncell / 2 + 127) / 128), sel_items(items), 1);
   if (g.d == 2) {
-    if (v == 1) k_st_vupd<T, TT, 2, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
-    else k_st_vupd<T, TT, 2, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
-  } else {
-    if (v == 1) k_st_vupd<T, TT, 3, 1><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
-    else k_st_vupd<T, TT, 3, 2><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+    if (v == 1) k_st_vupd<T, TT, 2, 1, SYM><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+    else k_st_vupd<T, TT, 2, 2, SYM><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+  } else if constexpr (!SYM) {
+    if (v == 1) k_st_vupd<T, TT, 3, 1, SYM><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
+    else k_st_vupd<T, TT, 3, 2, SYM><<<gu, 128, 0, s>>>(g, nrhs, tab, wu, wp, colour, r, xi, xo, g_sel.list);
   }
 }
-// dispatch on the table storage format (0: as T, 1: FP16 pairs, 2: BF16 pairs; T = float only)
+// dispatch on the table storage format (0: as T, full; 1: FP16 pairs, 2: BF16 pairs; T = float
+// only).  In 2D the half formats are stored half by symmetry (launch_table_half_sym); in 3D
+// they are full (the mirrored reads of the 3D boxes cost more registers than they save).
 template <typename T>
 static void st_apply_any(const Grid& g, int items, int nrhs, int v, const void* tab, int fmt,
                          const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y,
                          int mode, int colour, int var, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (fmt == 1) return st_apply_t<T, __half2>(g, items, nrhs, v, (const __half2*)tab, x, b, y, mode, colour, var, s);
-    if (fmt == 2) return st_apply_t<T, __nv_bfloat162>(g, items, nrhs, v, (const __nv_bfloat162*)tab, x, b, y, mode, colour, var, s);
+    if (fmt == 1 && g.d == 2)
+      return st_apply_t<T, __half2, true>(g, items, nrhs, v, (const __half2*)tab, x, b, y, mode, colour, var, s);
+    if (fmt == 2 && g.d == 2)
+      return st_apply_t<T, __nv_bfloat162, true>(g, items, nrhs, v, (const __nv_bfloat162*)tab, x, b, y, mode, colour,
+                                                 var, s);
+    if (fmt == 1)
+      return st_apply_t<T, __half2, false>(g, items, nrhs, v, (const __half2*)tab, x, b, y, mode, colour, var, s);
+    if (fmt == 2)
+      return st_apply_t<T, __nv_bfloat162, false>(g, items, nrhs, v, (const __nv_bfloat162*)tab, x, b, y, mode,
+                                                  colour, var, s);
   }
-  st_apply_t<T, typename CT<T>::type>(g, items, nrhs, v, (const typename CT<T>::type*)tab, x, b, y, mode, colour, var, s);
+  st_apply_t<T, typename CT<T>::type, false>(g, items, nrhs, v, (const typename CT<T>::type*)tab, x, b, y, mode,
+                                             colour, var, s);
 }
 template <typename T>
 static void st_vupd_any(const Grid& g, int items, int nrhs, int v, const void* tab, int fmt, T wu, T wp,
                         int colour, const typename CT<T>::type* r, const typename CT<T>::type* xi,
                         typename CT<T>::type* xo, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (fmt == 1) return st_vupd_t<T, __half2>(g, items, nrhs, v, (const __half2*)tab, wu, wp, colour, r, xi, xo, s);
-    if (fmt == 2) return st_vupd_t<T, __nv_bfloat162>(g, items, nrhs, v, (const __nv_bfloat162*)tab, wu, wp, colour, r, xi, xo, s);
+    if (fmt == 1 && g.d == 2)
+      return st_vupd_t<T, __half2, true>(g, items, nrhs, v, (const __half2*)tab, wu, wp, colour, r, xi, xo, s);
+    if (fmt == 2 && g.d == 2)
+      return st_vupd_t<T, __nv_bfloat162, true>(g, items, nrhs, v, (const __nv_bfloat162*)tab, wu, wp, colour, r, xi,
+                                                xo, s);
+    if (fmt == 1)
+      return st_vupd_t<T, __half2, false>(g, items, nrhs, v, (const __half2*)tab, wu, wp, colour, r, xi, xo, s);
+    if (fmt == 2)
+      return st_vupd_t<T, __nv_bfloat162, false>(g, items, nrhs, v, (const __nv_bfloat162*)tab, wu, wp, colour, r,
+                                                 xi, xo, s);
   }
-  st_vupd_t<T, typename CT<T>::type>(g, items, nrhs, v, (const typename CT<T>::type*)tab, wu, wp, colour, r, xi, xo, s);
+  st_vupd_t<T, typename CT<T>::type, false>(g, items, nrhs, v, (const typename CT<T>::type*)tab, wu, wp, colour, r,
+                                            xi, xo, s);
 }
 
 template <typename T>
@@ -705,17 +805,17 @@ __global__ void k_table_half(long long n, const double2* __restrict__ in, void* 
   if (fmt == 1) ((__half2*)out)[i] = __floats2half2_rn((float)v.x, (float)v.y);
   else ((__nv_bfloat162*)out)[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
 }
-template <typename T, typename TT>
+template <typename T, typename TT, bool SYM>
 static void resid_gather_t(const Grid& g, int items_l, int nrhs, int nsub, int nloc, const int* map, int v,
                            const TT* tab, const typename CT<T>::type* x, const typename CT<T>::type* b,
                            typename CT<T>::type* out, cudaStream_t s) {
   const dim3 gr((unsigned)((nloc + 127) / 128), sel_items(items_l));
   if (g.d == 2) {
-    if (v == 1) k_st_resid_gather<T, TT, 2, 1><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
-    else k_st_resid_gather<T, TT, 2, 2><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
-  } else {
-    if (v == 1) k_st_resid_gather<T, TT, 3, 1><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
-    else k_st_resid_gather<T, TT, 3, 2><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+    if (v == 1) k_st_resid_gather<T, TT, 2, 1, SYM><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+    else k_st_resid_gather<T, TT, 2, 2, SYM><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+  } else if constexpr (!SYM) {
+    if (v == 1) k_st_resid_gather<T, TT, 3, 1, SYM><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
+    else k_st_resid_gather<T, TT, 3, 2, SYM><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
   }
 }
 
@@ -725,18 +825,52 @@ void launch_st_resid_gather(const Grid& g, int items_l, int nrhs, int nsub, int 
                             const typename CT<T>::type* b, typename CT<T>::type* out, cudaStream_t s) {
   const int v = layout_variant(L, g.d);
   if constexpr (sizeof(T) == 4) {
+    if (fmt == 1 && g.d == 2)
+      return resid_gather_t<T, __half2, true>(g, items_l, nrhs, nsub, nloc, map, v, (const __half2*)tab, x, b, out, s);
+    if (fmt == 2 && g.d == 2)
+      return resid_gather_t<T, __nv_bfloat162, true>(g, items_l, nrhs, nsub, nloc, map, v,
+                                                     (const __nv_bfloat162*)tab, x, b, out, s);
     if (fmt == 1)
-      return resid_gather_t<T, __half2>(g, items_l, nrhs, nsub, nloc, map, v, (const __half2*)tab, x, b, out, s);
+      return resid_gather_t<T, __half2, false>(g, items_l, nrhs, nsub, nloc, map, v, (const __half2*)tab, x, b, out,
+                                               s);
     if (fmt == 2)
-      return resid_gather_t<T, __nv_bfloat162>(g, items_l, nrhs, nsub, nloc, map, v, (const __nv_bfloat162*)tab, x, b,
-                                               out, s);
+      return resid_gather_t<T, __nv_bfloat162, false>(g, items_l, nrhs, nsub, nloc, map, v,
+                                                      (const __nv_bfloat162*)tab, x, b, out, s);
   }
-  resid_gather_t<T, typename CT<T>::type>(g, items_l, nrhs, nsub, nloc, map, v, (const typename CT<T>::type*)tab, x,
-                                          b, out, s);
+  resid_gather_t<T, typename CT<T>::type, false>(g, items_l, nrhs, nsub, nloc, map, v,
+                                                 (const typename CT<T>::type*)tab, x, b, out, s);
 }
 
 void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaStream_t s) {
   k_table_half<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out, fmt);
+}
+
+// full FP64 table [set][full slot][cell] -> half-precision half table [set][compact slot][cell]
+#define EHS_MAXHALF 512
+struct HalfFull {
+  int full[EHS_MAXHALF];
+};
+__global__ void k_table_half_sym(long long ncell, int nfull, int nhalf, HalfFull hf, const double2* __restrict__ in,
+                                 void* out, int fmt) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int hs = blockIdx.y, set = blockIdx.z;
+  const double2 v = in[((long long)set * nfull + hf.full[hs]) * ncell + c];
+  const long long o = ((long long)set * nhalf + hs) * ncell + c;
+  if (fmt == 1) ((__half2*)out)[o] = __floats2half2_rn((float)v.x, (float)v.y);
+  else ((__nv_bfloat162*)out)[o] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+}
+
+int half_table_slots(const StencilLayout& L) { return make_half_map(L).nslot; }
+
+void launch_table_half_sym(const Grid& g, int nsets, const StencilLayout& L, const double2* in, void* out, int fmt,
+                           cudaStream_t s) {
+  const HalfMap H = make_half_map(L);
+  if (!H.ok || H.nslot > EHS_MAXHALF) throw std::runtime_error("half table map");
+  HalfFull hf{};
+  for (int k = 0; k < H.nslot; ++k) hf.full[k] = H.full[k];
+  const dim3 gr((unsigned)((g.ncell + 255) / 256), H.nslot, nsets);
+  k_table_half_sym<<<gr, 256, 0, s>>>(g.ncell, L.nslot, H.nslot, hf, in, out, fmt);
 }
 
 void launch_block_inv(const Grid& g, int nsets, const StencilLayout& L, const double2* tab, double2* out,

@@ -73,8 +73,9 @@ void launch_galerkin(const Grid& gf, const Grid& gc, int nsets, const StencilLay
                      cudaStream_t s);
 template <typename T>
 void launch_table_cast(long long n, const double2* in, typename CT<T>::type* out, cudaStream_t s);
-// tab: stencil table of level-layout L in format fmt (0: complex T, 1: FP16
-// pairs, 2: BF16 pairs; the half formats serve the complex64 cycle only)
+// tab: stencil table of level-layout L in format fmt (0: complex T, full; 1: FP16
+// pairs, 2: BF16 pairs, in half storage (launch_table_half_sym) in 2D and full in
+// 3D; the half formats serve the complex64 cycle only)
 // var: residual-pass launch shape, 0 .. ST_ROWS_VARIANTS-1 (chosen by the setup autotuner)
 #define ST_ROWS_VARIANTS 4
 template <typename T>
@@ -82,6 +83,12 @@ void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L,
                      const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y,
                      int mode, int var, cudaStream_t s);
 void launch_table_half(long long n, const double2* in, void* out, int fmt, cudaStream_t s);
+// Galerkin table in half storage (common.cuh HalfMap: one coefficient of every mirrored pair,
+// K_c = K_c^T) and FP16 (fmt 1) / BF16 (fmt 2) pairs: out [nsets][half_table_slots(L)][ncell];
+// the complex64 cycle reads its fmt 1 / 2 tables in this form
+int half_table_slots(const StencilLayout& L);
+void launch_table_half_sym(const Grid& g, int nsets, const StencilLayout& L, const double2* in, void* out, int fmt,
+                           cudaStream_t s);
 // one colour of red-black Vanka on a Galerkin level; rbuf: residual scratch of x's size
 template <typename T>
 void launch_st_vanka(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
