@@ -54,8 +54,10 @@ typedef enum {
   EHS_ERR_OOM = 3,        /* device allocation failed */
   EHS_ERR_NOCONV = 4,     /* maxit reached before tol */
   EHS_ERR_BREAKDOWN = 5,  /* Arnoldi breakdown before tol */
-  EHS_ERR_TIMEOUT = 6,    /* reserved for a bounded device wait that gives up; no kernel of this
-                             version waits on another, so no call returns it */
+  EHS_ERR_TIMEOUT = 6,    /* a bounded device wait gave up: the grid barrier of a persistent
+                             launch (the MG-DD coarsest solve of the 2D complex64 cycle) waited
+                             past about a second because other work held the SMs; returned by
+                             the solves and by ehs_sync, the outputs are then unspecified */
   EHS_ERR_NONFINITE = 7,  /* NaN / Inf in a residual norm or a pivot */
   EHS_ERR_UNSUPPORTED = 8 /* reserved for an option combination that is not built; this version
                              rejects unknown option values with EHS_ERR_ARG instead */
@@ -124,6 +126,11 @@ typedef struct {
                             cycle: 0 complex double-float (FP64-class), 1 complex64, 2 FP16
                             pairs, 3 BF16 pairs; products accumulate in FP32 (double-float
                             for 0); formed in FP64 at setup in every case */
+  int coarse_persist;    /* 1: the MG-DD coarsest solve of the 2D complex64 cycle (coarse_fmt 1..3)
+                            runs as one persistent launch per solve -- every colour's residual,
+                            local products and scatter, separated by bounded grid barriers --
+                            instead of graph-replayed per-colour launches; same results.  0 (the
+                            default): per-colour launches */
 } ehs_opts;
 
 typedef struct {

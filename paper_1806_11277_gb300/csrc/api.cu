@@ -89,6 +89,8 @@ struct Hier {
   CoarseDD cdd;
   bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
   bool fused0 = false;         // 2D complex64 cycle: fused fine-level sweep and residual + restriction
+  bool persist = false;        // complex64 MG-DD coarsest solve in one persistent launch
+  unsigned* pbar = nullptr;    // its grid-barrier state (2 words)
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
   void* cfdf = nullptr;        // df64 coefficients (outer-Krylov operator of the global problem)
@@ -109,6 +111,7 @@ struct DDGroup {          // subdomains of one colour that share one shape
 
 struct ehs_ctx {
   cudaStream_t s = nullptr;
+  int* derr = nullptr;       // device flag: a bounded grid barrier of a persistent launch gave up
   ehs_problem prob{};
   ehs_opts opt{};
   int d = 2;
@@ -126,6 +129,7 @@ struct ehs_ctx {
   float4 *Vq = nullptr, *wq = nullptr, *rq = nullptr, *qq = nullptr, *xq = nullptr, *partq = nullptr;
   float4 *hq = nullptr, *h2q = nullptr, *yq = nullptr;
   float2 *Zf = nullptr, *npq = nullptr, *invq = nullptr;
+  int* kcnt = nullptr;        // [3][items] last-block counters of the fused Krylov reductions
   double2* hhost = nullptr;   // device double copies of h for the host
   double* d_rho = nullptr;   // media kept for the gradient: rho and omega per set
   double* d_om = nullptr;
@@ -158,7 +162,8 @@ template <typename P> P* dalloc(ehs_ctx* c, size_t count) {
   cudaError_t e = cudaMalloc(&p, count * sizeof(P));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    throw std::bad_alloc();
+    if (e == cudaErrorMemoryAllocation) throw std::bad_alloc();
+    throw CudaError(std::string("cudaMalloc: ") + cudaGetErrorString(e));   // no device, driver, ...
   }
   c->allocs.push_back(p);
   CK(cudaMemsetAsync(p, 0, count * sizeof(P), c->s));
@@ -394,6 +399,9 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
   // their tiles; EHS_FINE_UNFUSED=1 selects the per-colour kernels instead (tests compare both)
   const char* uf = getenv("EHS_FINE_UNFUSED");
   H.fused0 = (precs & 2) && d == 2 && !H.full && fine_tiles_fit(H.g0) && !(uf && uf[0] == '1');
+  // opts.coarse_persist: the MG-DD coarsest solve of the 2D complex64 cycle as one persistent launch
+  H.persist = (precs & 2) && mgdd && c->opt.coarse_persist && coarse_persist_supported(C.g, H.coarse_fmt);
+  if (H.persist) H.pbar = dalloc<unsigned>(c, 2);
   if (const char* f = getenv("EHS_ROWS_VARIANT")) {   // fixed launch shape (tests)
     const int v = atoi(f);
     if (v >= 0 && v < ST_ROWS_VARIANTS)
@@ -529,6 +537,24 @@ void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typenam
   const Level& L = H.lv[l];
   CoarseDD& D = H.cdd;
   const int p = PT<T>::i;
+  if constexpr (sizeof(T) == 4) {
+    if (H.persist) {   // every colour in one persistent launch
+      int fmt = 0;
+      const void* tab = tabp<float>(H, L, &fmt);
+      const int ncol = (int)D.col_subs.size();
+      const int* cs[8] = {nullptr};
+      int ncs[8] = {0};
+      for (int k = 0; k < ncol && k < 8; ++k) {
+        cs[k] = D.d_col_subs[k];
+        ncs[k] = (int)D.col_subs[k].size();
+      }
+      launch_coarse_dd_persist(L.g, l >= 2 ? 2 : 1, fmt, H.coarse_fmt, H.nrhs, D.nsub, D.nloc, D.d_map, D.d_sizes, tab,
+                               L.invlp, (const float2*)b, (float2*)x, (float2*)D.loc[1][0], (float2*)D.loc[1][1],
+                               g_sel.list, (int)sel_items(H.items), cs, ncs, ncol, H.pbar, c->derr, c->s);
+      cnt(); post();
+      return;
+    }
+  }
   const long long NG = (long long)(L.g.d + 1) * L.g.ncell;
   C* rs = (C*)D.loc[p][0];
   C* zs = (C*)D.loc[p][1];
@@ -658,6 +684,7 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (O->coef_half < 0 || O->coef_half > 2) throw ArgError("coef_half must be 0, 1 (FP16) or 2 (BF16)");
   if (O->vanka_full != 0 && O->vanka_full != 1) throw ArgError("vanka_full must be 0 or 1");
   if (O->coarse_fmt < 0 || O->coarse_fmt > 3) throw ArgError("coarse_fmt must be 0..3");
+  if (O->coarse_persist != 0 && O->coarse_persist != 1) throw ArgError("coarse_persist must be 0 or 1");
   for (int k = 0; k < 3; ++k)
     if (O->coarse_dd[k] < 0) throw ArgError("coarse_dd must be >= 0");
   // MG-DD on the global hierarchy: the coarsest grid is known here (DD contexts split the
@@ -993,28 +1020,30 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
   while (!A.all_done() && !A.maxed()) {
     A.start_cycle();
     set_active(c, A.active);
-    {  // V_0 = r / beta (invq holds 1/||r|| from the last norm)
+    {  // V_0 = r / beta (invq holds 1/||r|| from the last norm) and its complex64 copy
       SelScope sel = global_sel(c);
-      launch_scale_df(n, items, c->rq, c->invq, c->Vq, s); cnt(); post();
+      launch_scale_cast_df(n, items, c->rq, c->invq, c->Vq, c->f_in, s); cnt(); post();
     }
     for (int j = 0; j < m; ++j) {
-      float4* Vj = c->Vq + (size_t)j * items * n;
       float2* Zj = c->Zf + (size_t)j * items * n;
       SelScope sel = global_sel(c);      // only the items still iterating
-      graphed(c, j, [&]() {
-        launch_df_to_f2(nall, Vj, c->f_in, c->s); cnt(); post();
+      graphed(c, j, [&]() {               // f_in holds V_j in complex64
         if (c->opt.precond == EHS_PRECOND_DD) dd_apply_t<float>(c, c->f_in, Zj);
         else cycle_rec<float>(c, c->H, 0, c->f_in, Zj, false);
       });
       launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, Zj, 1, nullptr, c->wq, 0, s);
+      // CGS2: h1 = V^H w; w -= V h1, h2 = V^H w; w -= V h2, ||w|| -- each reduction by the
+      // launch's last block
       const int nv = j + 1;
-      launch_mdot_df(n, items, nv, c->Vq, c->wq, c->partq, nblk, s);
-      launch_reduce_parts_df(items, nv, nblk, c->partq, c->hq, c->hhost, s);
-      launch_mupdate_df(n, items, nv, c->Vq, c->hq, c->wq, c->partq, nblk, 1, nullptr, s);
-      launch_reduce_parts_df(items, nv, nblk, c->partq, c->h2q, c->hhost + (size_t)items * 12, s);
-      launch_mupdate_df(n, items, nv, c->Vq, c->h2q, c->wq, nullptr, nblk, 0, c->npq, s);
-      launch_reduce_norm_df(items, nblk, c->npq, c->nrm, c->invq, s);
-      cnt(7); post();
+      int* k0 = c->kcnt;
+      int* k1 = c->kcnt + items;
+      int* k2 = c->kcnt + 2 * items;
+      launch_mdot_df(n, items, nv, c->Vq, c->wq, c->partq, nblk, s, k0, c->hq, c->hhost);
+      launch_mupdate_df(n, items, nv, c->Vq, c->hq, c->wq, c->partq, nblk, 1, nullptr, s, k1, c->h2q,
+                        c->hhost + (size_t)items * 12);
+      launch_mupdate_df(n, items, nv, c->Vq, c->h2q, c->wq, nullptr, nblk, 0, c->npq, s, k2, nullptr, nullptr,
+                        c->nrm, c->invq);
+      cnt(4); post();
       // one round trip into pinned memory: h1, h2 (the reduce kernels' double copies) and the norms
       double2* ph1 = c->hstep;
       double2* ph2 = c->hstep + (size_t)items * 12;
@@ -1024,7 +1053,7 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
       if (!A.step(j, ph1, ph2, phn)) break;
       set_active(c, A.active);
       SelScope sel2 = global_sel(c);
-      launch_scale_df(n, items, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n, s); cnt(); post();
+      launch_scale_cast_df(n, items, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n, c->f_in, s); cnt(); post();
     }
     A.solve_y(yh);
     // y to df64 on the device via the double2 -> df64 conversion
@@ -1043,8 +1072,22 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
   return A.finish(c, info);
 }
 
+// a persistent launch whose grid barrier gave up (EHS_ERR_TIMEOUT); clears the flag
+bool device_timeout(ehs_ctx* c) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  if (h) CK(cudaMemsetAsync(c->derr, 0, sizeof(int), c->s));
+  return h != 0;
+}
+
 ehs_status fgmres(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* info) {
-  return c->opt.prec == EHS_C64 ? fgmres_df(c, q, u, info) : fgmres_c128(c, q, u, info);
+  const ehs_status st = c->opt.prec == EHS_C64 ? fgmres_df(c, q, u, info) : fgmres_c128(c, q, u, info);
+  if (device_timeout(c)) {
+    c->err = "a persistent launch's grid barrier waited past its limit (the SMs were held by other work)";
+    return EHS_ERR_TIMEOUT;
+  }
+  return st;
 }
 
 __global__ void k_conj(long long n, double2* v) {
@@ -1144,6 +1187,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     H.cdd_overlap = opts->coarse_dd_overlap;
     H.coarse_fmt = opts->coarse_fmt;
     c->n0 = (long long)(c->d + 1) * H.g0.ncell;
+    c->derr = dalloc<int>(c, 1);
     const long long nc = (long long)H.nsets * H.g0.ncell;
     check_media(c, prob->lambda, prob->mu, prob->rho, nc);
     // media to the device (the caller's buffers are only read here)
@@ -1203,6 +1247,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
       c->npq = dalloc<float2>(c, (size_t)items * c->nblk);
       c->invq = dalloc<float2>(c, items);
       c->hhost = dalloc<double2>(c, (size_t)items * 24);
+      c->kcnt = dalloc<int>(c, (size_t)items * 3);
     }
     CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));
     CK(cudaMallocHost((void**)&c->hstep, (size_t)items * 25 * sizeof(double2)));
@@ -1461,7 +1506,13 @@ ehs_status ehs_sync(ehs_ctx* c) {
   if (!c) return EHS_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(c->s);
   if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return EHS_ERR_CUDA; }
-  return EHS_OK;
+  return guard(c, [&]() -> ehs_status {
+    if (device_timeout(c)) {
+      c->err = "a persistent launch's grid barrier waited past its limit (the SMs were held by other work)";
+      return EHS_ERR_TIMEOUT;
+    }
+    return EHS_OK;
+  });
 }
 long long ehs_kernel_launches(void) { return g_launches.load(); }
 const char* ehs_last_error(const ehs_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }

@@ -11,8 +11,7 @@
 // multiplies every subdomain's stored inverse (double-float, complex64, FP16
 // or BF16 pairs) with its local residuals, skipping the padding rows.
 #include "kernels.h"
-#include <cuda_fp16.h>
-#include <cuda_bf16.h>
+#include "dense_rows.cuh"
 
 namespace ehs {
 namespace {
@@ -200,9 +199,6 @@ __global__ void k_dense_assemble_sub(Grid g, StencilLayout L, const double2* __r
 
 // x = Ainv r with Ainv stored in complex64, FP16 or BF16 pairs (FP32
 // accumulation); one warp per row, four independent loads in flight per lane
-__device__ __forceinline__ float2 ldlp(const float2* p) { return *p; }
-__device__ __forceinline__ float2 ldlp(const __half2* p) { return __half22float2(*p); }
-__device__ __forceinline__ float2 ldlp(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
 
 template <typename TI>
 __global__ void k_dense_apply_lp(int N, int nrhs, const TI* __restrict__ inv, const float2* __restrict__ r,
@@ -235,64 +231,19 @@ __global__ void k_dense_apply_lp(int N, int nrhs, const TI* __restrict__ inv, co
   if (lane == 0) x[(long long)item * N + warp] = make_float2(sx, sy);
 }
 
-// The same product with 16-byte loads: each warp computes R = 4 consecutive
-// rows, so every lane keeps four 16-byte matrix loads in flight and reuses each
-// chunk of r for the four rows (E entries per 16-byte load; N a multiple of 4
-// and of E, so every row starts 16-byte aligned).  Matrix set (item / nrhs) has
-// n = sizes[set % nsub] live rows and columns (MG-DD subdomains smaller than
-// the padded N); columns beyond n hold the zero padding of the identity rows
-// and are skipped, and so are groups of rows at or beyond n (their outputs are
-// never read).
+// The same product with 16-byte loads (dense_rows4 in dense_rows.cuh): each warp
+// computes 4 consecutive rows of the matrix set (item / nrhs), whose live size is
+// sizes[set % nsub]; groups of rows at or beyond it are skipped.
 template <typename TI>
 __global__ void __launch_bounds__(256) k_dense_apply_v(int N, int nrhs, int nsub, const int* __restrict__ sizes,
                                                        const TI* __restrict__ inv, const float2* __restrict__ r,
                                                        float2* __restrict__ x, const int* __restrict__ il) {
-  constexpr int E = 16 / (int)sizeof(TI);
-  constexpr int R = 4;
-  const int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R;
-  const int lane = threadIdx.x & 31;
+  const int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4;
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   const int set = item / nrhs;
   const int n = sizes ? sizes[set % nsub] : N;
   if (row0 >= n) return;
-  const int nq = (n + E - 1) / E;                  // 16-byte chunks per live row
-  const uint4* m0 = (const uint4*)(inv + ((long long)set * N + row0) * N);
-  const int qs = N / E;                            // chunks per stored row
-  const float4* rv = (const float4*)(r + (long long)item * N);
-  union U { uint4 u; TI t[E]; };
-  float ax[R], ay[R];
-#pragma unroll
-  for (int k = 0; k < R; ++k) { ax[k] = 0.f; ay[k] = 0.f; }
-  for (int q = lane; q < nq; q += 32) {
-    U a[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) a[k].u = __ldg(m0 + (long long)k * qs + q);
-#pragma unroll
-    for (int e = 0; e < E; e += 2) {
-      const float4 b = __ldg(rv + (q * E + e) / 2);
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const float2 c0 = ldlp(&a[k].t[e]), c1 = ldlp(&a[k].t[e + 1]);
-        ax[k] = fmaf(c0.x, b.x, fmaf(-c0.y, b.y, ax[k]));
-        ay[k] = fmaf(c0.x, b.y, fmaf(c0.y, b.x, ay[k]));
-        ax[k] = fmaf(c1.x, b.z, fmaf(-c1.y, b.w, ax[k]));
-        ay[k] = fmaf(c1.x, b.w, fmaf(c1.y, b.z, ay[k]));
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < R; ++k)
-    for (int o = 16; o > 0; o >>= 1) {
-      ax[k] += __shfl_xor_sync(0xffffffffu, ax[k], o);
-      ay[k] += __shfl_xor_sync(0xffffffffu, ay[k], o);
-    }
-  if (lane < R) {
-    float vx = ax[0], vy = ay[0];
-#pragma unroll
-    for (int k = 1; k < R; ++k)
-      if (lane == k) { vx = ax[k]; vy = ay[k]; }
-    x[(long long)item * N + row0 + lane] = make_float2(vx, vy);
-  }
+  dense_rows4<TI>(N, n, row0, inv + (long long)set * N * N, r + (long long)item * N, x + (long long)item * N);
 }
 
 }  // namespace

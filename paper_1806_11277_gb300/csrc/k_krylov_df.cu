@@ -62,9 +62,64 @@ __device__ __forceinline__ void block_store_norm(dfr v, float2* part, int item, 
   }
 }
 
+// Last-block reduction.  Every block of an item has written its partials; the
+// block that finishes last for the item (counted in cnt[item], which it resets)
+// sums them.  The sum runs in a fixed order -- per output, lanes stride over
+// the blocks and a warp tree combines them, as k_reduce_parts_df does -- so the
+// result is the same whichever block finishes last.  Partials are read with
+// L1-bypassing loads (other blocks wrote them).
+__device__ __forceinline__ bool last_block(int* cnt, int item, int nblk) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt + item, 1) == nblk - 1;
+  __syncthreads();
+  return last;
+}
+__device__ __forceinline__ void reduce_dots_last(int item, int nv, int nblk, const float4* part, float4* out,
+                                                 double2* outd, int* cnt) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < nv; i += KB / 32) {
+    const long long o = (long long)item * nv + i;
+    dfc s = dfc_zero();
+    for (int b = lane; b < nblk; b += 32) {
+      const float4 v = __ldcg(part + o * nblk + b);
+      s = dfc_add(s, dfc{{v.x, v.y}, {v.z, v.w}});
+    }
+    s = warp_sum_df(s);
+    if (lane == 0) {
+      dfc_st(out + o, s);
+      outd[o] = dfc_to_d2(s);
+    }
+  }
+  if (threadIdx.x == 0) cnt[item] = 0;
+}
+__device__ __forceinline__ void reduce_norm_last(int item, int nblk, const float2* part, double* out, float2* inv,
+                                                 int* cnt) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    dfr s = df_zero();
+    for (int b = lane; b < nblk; b += 32) {
+      const float2 v = __ldcg(part + (long long)item * nblk + b);
+      s = df_add(s, {v.x, v.y});
+    }
+    s = warp_sum_df(s);
+    if (lane == 0) {
+      const double nrm = sqrt(df_to_d(s));   // one FP64 sqrt per item
+      out[item] = nrm;
+      const dfr iv = df_from_d(nrm > 0.0 ? 1.0 / nrm : 0.0);
+      inv[item] = make_float2(iv.hi, iv.lo);
+      cnt[item] = 0;
+    }
+  }
+}
+
+// partial dots conj(V_i) . w per block; with cnt, the last block of each item also forms
+// the sums (out: df64, outd: double copy for the host)
 template <int NV>
 __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const float4* __restrict__ V,
-                                                const float4* __restrict__ w, float4* part, int nblk, const int* __restrict__ il) {
+                                                const float4* __restrict__ w, float4* part, int nblk,
+                                                const int* __restrict__ il, int* cnt, float4* out, double2* outd) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   dcacc acc[NV];
 #pragma unroll
@@ -75,20 +130,24 @@ __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const fl
 #pragma unroll
     for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], dfc_ld(V + ((long long)i * items + item) * n + e), we);
   }
-  dfc out[NV];
+  dfc vals[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) out[i] = dcacc_val(acc[i]);
-  block_store_df(out, NV, part, item, nblk);
+  for (int i = 0; i < NV; ++i) vals[i] = dcacc_val(acc[i]);
+  block_store_df(vals, NV, part, item, nblk);
+  if (cnt && last_block(cnt, item, nblk)) reduce_dots_last(item, NV, nblk, part, out, outd, cnt);
 }
 
 // w -= sum_i V_i h_i; optional partial dots of V with the new w and |w|^2.
+// With cnt, the last block of each item also forms the dots' sums (out, outd)
+// or the norm (nrm, inv = 1/norm).
 // h sits in shared memory and the dot pass re-reads V_i (an L1 hit: the block
 // read it a moment earlier), which keeps the kernel at two blocks per SM.
 template <int NV>
 __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, const float4* __restrict__ V,
                                                       const float4* __restrict__ h, float4* __restrict__ w,
                                                       float4* part, int nblk, int dot, float2* nrm_part,
-                                                      const int* __restrict__ il) {
+                                                      const int* __restrict__ il, int* cnt, float4* out,
+                                                      double2* outd, double* nrm, float2* inv) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   __shared__ float4 hs[NV];
   if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
@@ -115,12 +174,16 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
     dacc_fma(nacc, we.im, we.im);
   }
   if (dot) {
-    dfc out[NV];
+    dfc vals[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) out[i] = dcacc_val(acc[i]);
-    block_store_df(out, NV, part, item, nblk);
+    for (int i = 0; i < NV; ++i) vals[i] = dcacc_val(acc[i]);
+    block_store_df(vals, NV, part, item, nblk);
   }
   if (nrm_part) block_store_norm(dacc_val(nacc), nrm_part, item, nblk);
+  if (cnt && (dot || nrm_part) && last_block(cnt, item, nblk)) {
+    if (dot) reduce_dots_last(item, NV, nblk, part, out, outd, cnt);
+    else reduce_norm_last(item, nblk, nrm_part, nrm, inv, cnt);
+  }
 }
 
 __global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2* part, int nblk, const int* __restrict__ il) {
@@ -178,6 +241,18 @@ __global__ void k_scale_df(long long n, const float4* __restrict__ w, const floa
   if (e >= n) return;
   const float2 s = inv[item];
   dfc_st(out + (long long)item * n + e, dfc_scale(dfc_ld(w + (long long)item * n + e), {s.x, s.y}));
+}
+
+// V_j = w / ||w|| (df64) and its complex64 copy, the input of the preconditioner
+__global__ void k_scale_cast_df(long long n, const float4* __restrict__ w, const float2* __restrict__ inv,
+                                float4* __restrict__ out, float2* __restrict__ out32, const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float2 s = inv[item];
+  const dfc v = dfc_scale(dfc_ld(w + (long long)item * n + e), {s.x, s.y});
+  dfc_st(out + (long long)item * n + e, v);
+  out32[(long long)item * n + e] = dfc_to_f2(v);
 }
 
 __global__ void k_xupdate_df(long long n, int items, int m, const float2* __restrict__ Z,
@@ -341,24 +416,30 @@ FinePdf mkPdf(double h, double alpha) {
 
 #define EHS_NV_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
 void launch_mdot_df(long long n, int items, int nv, const float4* V, const float4* w, float4* part,
-                    int nblk, cudaStream_t s) {
+                    int nblk, cudaStream_t s, int* cnt, float4* out, double2* outd) {
   const dim3 g(nblk, sel_items(items));
   switch (nv) {
-#define X(k) case k: k_mdot_df<k><<<g, KB, 0, s>>>(n, items, V, w, part, nblk, g_sel.list); break;
+#define X(k) case k: k_mdot_df<k><<<g, KB, 0, s>>>(n, items, V, w, part, nblk, g_sel.list, cnt, out, outd); break;
     EHS_NV_CASES(X)
 #undef X
     default: break;
   }
 }
 void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
-                       float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s) {
+                       float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s, int* cnt, float4* out,
+                       double2* outd, double* nrm, float2* inv) {
   const dim3 g(nblk, sel_items(items));
   switch (nv) {
-#define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part, g_sel.list); break;
+#define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part, g_sel.list, \
+                                                      cnt, out, outd, nrm, inv); break;
     EHS_NV_CASES(X)
 #undef X
     default: break;
   }
+}
+void launch_scale_cast_df(long long n, int items, const float4* w, const float2* inv, float4* out, float2* out32,
+                          cudaStream_t s) {
+  k_scale_cast_df<<<dim3(nb(n, 256), sel_items(items)), 256, 0, s>>>(n, w, inv, out, out32, g_sel.list);
 }
 void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s) {
   k_norm_part_df<<<dim3(nblk, sel_items(items)), KB, 0, s>>>(n, w, part, nblk, g_sel.list);

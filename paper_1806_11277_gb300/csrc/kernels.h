@@ -136,6 +136,17 @@ void launch_dense_assemble_sub(const Grid& g, int nsets, int nsub, int nloc, con
 // live size of matrix set s is sizes[s % nsub], the rest identity padding (skipped)
 void launch_dense_apply_lp(int N, int items, int nrhs, int nsub, const int* sizes, const void* inv, int fmt,
                            const float2* r, float2* x, cudaStream_t s);
+// The MG-DD coarsest solve of the 2D complex64 cycle in one persistent launch (every colour's
+// residual gather, local products and scatter, separated by bounded grid barriers; the result
+// of the per-colour launches).  lv: layout variant of the coarsest level (1, 2); tfmt: table
+// format (0 complex64, 1 FP16, 2 BF16 pairs); ifmt: coarse_fmt of the inverses (1..3); act/nact:
+// active items (act null: all nact items); col_subs[k] / ncs[k]: subdomains of colour k; bar: two
+// device words of barrier state (cleared by the launch); err: set to 1 if a barrier gave up.
+bool coarse_persist_supported(const Grid& g, int coarse_fmt);
+void launch_coarse_dd_persist(const Grid& g, int lv, int tfmt, int ifmt, int nrhs, int nsub, int nloc, const int* map,
+                              const int* sizes, const void* tab, const void* inv, const float2* b, float2* x,
+                              float2* rs, float2* zs, const int* act, int nact, const int* const* col_subs,
+                              const int* ncs, int ncol, unsigned* bar, int* err, cudaStream_t s);
 // sub-item list of MG-DD / DD: out[j * ncs + q] = ((m * nsub) + subs[q]) * nrhs + r for the
 // j-th active item b = m * nrhs + r (all items when list is null)
 void launch_expand_items(const int* list, int nact, int nrhs, int nsub, const int* subs, int ncs, int* out,
@@ -177,10 +188,18 @@ void launch_xupdate(long long n, int items, int m, const CZ* Z, const double2* y
 
 // ---- FP64-class (double-float) Krylov, operator and coarsest ----------------
 // complex df64 = float4 {re.hi, re.lo, im.hi, im.lo}; real df64 = float2 {hi, lo}
+// With cnt (device counters [items], zero, reset by the kernels), the last block of each item
+// also reduces the partials: dots into out (df64) and outd (double copy for the host), the norm
+// into nrm (double) and inv (df64 1/norm) -- the results of launch_reduce_parts_df /
+// launch_reduce_norm_df, summed in the same order, without their launches.
 void launch_mdot_df(long long n, int items, int nv, const float4* V, const float4* w, float4* part,
-                    int nblk, cudaStream_t s);
+                    int nblk, cudaStream_t s, int* cnt = nullptr, float4* out = nullptr, double2* outd = nullptr);
 void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
-                       float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s);
+                       float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s, int* cnt = nullptr,
+                       float4* out = nullptr, double2* outd = nullptr, double* nrm = nullptr, float2* inv = nullptr);
+// out = w / norm (inv per item) and out32 = its complex64 copy
+void launch_scale_cast_df(long long n, int items, const float4* w, const float2* inv, float4* out, float2* out32,
+                          cudaStream_t s);
 void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s);
 // out (df64, device use) and outd (double copy for the host)
 void launch_reduce_parts_df(int items, int nv, int nblk, const float4* part, float4* out, double2* outd,

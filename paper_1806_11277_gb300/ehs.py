@@ -39,7 +39,8 @@ class Opts(C.Structure):
                 ("vanka_full", C.c_int),
                 ("coarse_dd", C.c_int * 3),
                 ("coarse_dd_overlap", C.c_int),
-                ("coarse_fmt", C.c_int)]
+                ("coarse_fmt", C.c_int),
+                ("coarse_persist", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -585,15 +585,17 @@ def test_mgdd_cycle_matches_oracle(case, cyc):
     S.close()
 
 
-@pytest.mark.parametrize("prec_name,fmt", [("c128", 0), ("c64", 0), ("c64", 1), ("c64", 2), ("c64", 3)])
-def test_mgdd_fgmres_matches_oracle(prec_name, fmt):
+@pytest.mark.parametrize("prec_name,fmt,persist", [("c128", 0, 0), ("c64", 0, 0), ("c64", 1, 0), ("c64", 2, 0),
+                                                   ("c64", 3, 0), ("c64", 1, 1), ("c64", 2, 1), ("c64", 3, 1)])
+def test_mgdd_fgmres_matches_oracle(prec_name, fmt, persist):
     """MG-DD inside FGMRES; the local inverses in double-float, complex64, FP16 or
-    BF16 storage (FP32 accumulation) for the complex64 cycle."""
+    BF16 storage (FP32 accumulation) for the complex64 cycle; with persist the
+    complex64 coarsest solve runs as one persistent launch (opts.coarse_persist)."""
     ehs = _ehs()
     prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
     meds = _media_2d(64, 2)
     q, u, info = _solve_both(meds, 3, prec, alpha=0.4, cycle=2, coarse_dd=(2, 2, 1), coarse_dd_overlap=2,
-                             coarse_fmt=fmt)
+                             coarse_fmt=fmt, coarse_persist=persist)
     for it, med in enumerate(meds):
         K = _oracle_parts(med)
         H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 3, w=[0.75, 0.5], coarse_dd=((2, 2), 2))
@@ -833,3 +835,32 @@ def test_dd_uneven_split_fgmres_matches_oracle(case, form):
             else:
                 assert abs(info[it]["iters"] - io["iters"]) <= 1, (case, form, it, info[it], io["iters"])
             assert _err(ug, xo) <= 1e-5, (case, form, prec, it, _err(ug, xo))
+
+
+@pytest.mark.parametrize("fmt,tfmt", [(1, 0), (2, 1), (3, 2)])
+def test_coarse_persistent_equals_per_colour_launches(fmt, tfmt):
+    """The persistent MG-DD coarsest solve (one launch, grid barriers between the
+    colours' residual, local-product and scatter phases) gives the result of the
+    per-colour launches (the same arithmetic per element), with several sources
+    per medium so that sub-items of many media and sources share each phase; and
+    both match the oracle's CoarseDD within the storage rounding."""
+    ehs = _ehs()
+    meds = _media_2d(64, 2)
+    outs = {}
+    for persist in (1, 0):
+        S = ehs.solver_for(meds, levels=3, alpha=0.4, nrhs=3, coarse_dd=(2, 2, 1), coarse_dd_overlap=2,
+                           coarse_fmt=fmt, coef_half=tfmt, coarse_persist=persist)
+        cshape = tuple(S.level_shape(2)[2:])
+        b_ = _rand_slots(cshape, S.items, 91)
+        bd = torch.from_numpy(b_).to("cuda", torch.complex64)
+        xd = torch.full_like(bd, 5.0)
+        S.coarse_solve(bd, xd)
+        S.sync()
+        outs[persist] = xd.cpu().numpy()
+        S.close()
+    assert _err(outs[1], outs[0]) <= 1e-6, _err(outs[1], outs[0])
+    tol = {1: 2e-5, 2: 3e-3, 3: 2e-2}[fmt]
+    for it in range(6):
+        H = mg.Hierarchy(_oracle_parts(meds[it // 3], 0.4), meds[0].shape, 3, w=[0.75, 0.5], coarse_dd=((2, 2), 2))
+        xr = op.dofs_to_slots(H.coarse_solve(op.slots_to_dofs(b_[it], cshape)), cshape)
+        assert _err(outs[1][it], xr) <= tol, (it, _err(outs[1][it], xr))
