@@ -72,8 +72,9 @@ def default_kw():
 ROOF = "coarse"
 ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 16 subdomain inverses "
                "x 4 media)")
-# Galerkin level-1 apply (k_st_rows): 87 stencil coefficients (FP16 pairs, 4 B) + x 24 + y 24
-ST_ROWS_L1_BYTES_PER_CELL = 87 * 4 + 24 + 24
+# Galerkin level-1 apply (k_st_rows): 45 stored stencil coefficients of the half table (FP16 pairs,
+# 4 B; 87 per row set, the mirrored ones read at the neighbour cell) + x 24 + y 24
+ST_ROWS_L1_BYTES_PER_CELL = 45 * 4 + 24 + 24
 # DRAM read + write bytes of one roofline-kernel launch (one colour) of the default line, from an
 # ncu capture of the kernel as it stands (None whenever the kernel changes): mean of 7 warm launches
 ROOF_TRAFFIC_C2 = 450.84e6 + 5.88e6
@@ -83,12 +84,13 @@ ROOF_TRAFFIC_C2 = 450.84e6 + 5.88e6
 # input read once, each output written once; complex64 vectors 8 B per value, 3 values per cell).
 #  fine sweep: one launch of the fused red-black sweep, x 24 + b 24 + coefficients 16 + x' 24
 #  fine residual + restriction: one fused launch, x 24 + b 24 + coefficients 16 + coarse r 6
-#  level-1 rows: the Galerkin residual pass (FP16 table of 87 coefficients x 4 B) + x 24 + y 24
+#  level-1 rows: the Galerkin residual pass, the FP16 table in half storage (45 of the 87
+#    coefficients per cell kept, K_c = K_c^T) x 4 B + x 24 + y 24
 #  level-1 prolongation: x += P e, x 24 read + 24 written + e 6 (per level-1 cell)
 STENCIL = (
     ("k_fine_sweep_tile (fine level, whole red-black sweep)", "sweep", 0, 88),
     ("k_fine_resid_restrict_tile (fine residual + restriction)", "resid_restrict", 0, 70),
-    ("k_st_rows2<float,__half2,2,1> (Galerkin level 1, all rows, FP16 table)", "rows", 1, 87 * 4 + 48),
+    ("k_st_rows2<float,__half2,2,1,true> (Galerkin level 1, all rows, FP16 half table)", "rows", 1, 45 * 4 + 48),
     ("k_prolong_add<float,2> (level 2 -> level 1 correction)", "prolong", 1, 54),
 )
 
@@ -149,6 +151,10 @@ OTHER = {
                       "FP64-class (double-float) FGMRES", "FP64 FGMRES") + "; plain FP64 GPU form",
                   media=lambda: media(), kw=dict(prec=0, coarse_fmt=0, coef_half=0), rows_l1_bytes=87 * 16 + 48 + 48,
                   kernel="k_st_rows<double,double2,2,1> (Galerkin level 1, all rows)"),
+    # the default line with the MG-DD coarsest solve as one persistent launch per solve
+    "c2p": dict(workload=WORKLOAD + "; MG-DD coarsest solve as one persistent launch (bounded grid barriers "
+                "between the colours' residual and local-product phases) instead of graph-replayed per-colour "
+                "launches", media=lambda: media(), kw=dict(coarse_persist=1), roof="coarse", kernel=ROOF_KERNEL),
     # the default line with full cell-block Vanka
     "c2v": dict(workload=WORKLOAD + "; full (2d+1)^2 cell-block Vanka instead of the economic block",
                 media=lambda: media(), kw=dict(vanka_full=1), roof="coarse", kernel=ROOF_KERNEL),
@@ -302,6 +308,67 @@ _CPU_METER = {"wall": 0.0, "cpu": 0.0}
 def cores_used(meter):
     """Threads the timed oracle work kept busy on average: process CPU time / wall time."""
     return max(1, int(round(meter["cpu"] / meter["wall"]))) if meter["wall"] > 0 else 1
+
+
+def oracle_dd_sample(med, kw, gpu_iters):
+    """Bounded oracle sample of a 3D DD line (Algorithm DD with one shifted-Laplacian cycle per
+    subdomain).  Outside the timer: the global operator K and the hierarchy of the largest padded
+    subdomain.  Timed: ten oracle FGMRES iterations on K with the identity as preconditioner (the
+    Krylov work and the operator product of an iteration: CGS2 over the growing basis, x-update,
+    true residual), one global residual K x, and one cycle of that subdomain's shifted operator.
+    One DD-preconditioned iteration = Krylov part + one residual per colour + one cycle per
+    subdomain.  The oracle's own iteration count at this size is not available (its solve would
+    take hours), so the GPU line's mean count is used; in the parity tests of the same DD forms
+    (24^3 and 28 x 28 x 16) the counts are equal."""
+    import itertools
+    from oracle import dd as odd, krylov, multigrid as mg, operators as op
+    shape = med.lam.shape
+    d = len(shape)
+    nsub = tuple(kw["dd"][d - 1 - a] for a in range(d))          # per numpy axis
+    splits = [odd.split_axis(shape[a], nsub[a]) for a in range(d)]
+    align = 2 ** (kw["levels"] - 1)
+    subs = [odd.Subdomain(shape, si, splits, kw["dd_overlap"], kw["dd_pad"], align)
+            for si in itertools.product(*[range(n) for n in nsub])]
+    big = max(subs, key=lambda sd: int(np.prod(sd.shape)))
+    ncol = len({sd.colour for sd in subs})
+    parts = op.parts_for(med)
+    K = op.assemble_mixed(parts)
+    gamma = op.gamma_profile(shape, med.omega, med.abl_cells, 1.0, 0.01 * np.pi)
+    lm = big.local_medium(med.lam, med.mu, med.rho, gamma, med.omega, 1.0)
+    cdd = None
+    if max(kw.get("coarse_dd", (1, 1, 1))) > 1:
+        cdd = (tuple(kw["coarse_dd"][:d]), kw.get("coarse_dd_overlap", 2))
+    H = mg.Hierarchy(op.assemble_mixed(op.Parts(*lm, med.omega, med.h), kw["alpha"]), big.shape, kw["levels"],
+                     w=list(kw["w"])[:kw["levels"] - 1], coarse_dd=cdd)
+    q = op.slots_to_dofs(synth_rhs(med), shape)
+    rng = np.random.default_rng(0)
+    rl = rng.standard_normal(H.K[0].shape[0]) + 0j
+    meter = {"wall": 0.0, "cpu": 0.0}
+    t, c = time.perf_counter(), time.process_time()
+    krylov.fgmres(lambda v: K @ v, lambda v: v, q, m=10, maxit=10, tol=1e-30)
+    t_kry = (time.perf_counter() - t) / 10
+    t1 = time.perf_counter()
+    _ = q - K @ q
+    t_res = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    H.cycle(rl)
+    t_cyc = time.perf_counter() - t2
+    meter["wall"] = time.perf_counter() - t
+    meter["cpu"] = time.process_time() - c
+    t_iter = t_kry + ncol * t_res + len(subs) * t_cyc
+    mean_it = float(np.mean(gpu_iters))
+    return {"value": 1.0 / (t_iter * mean_it), "unit": "solves/s", "cores": cores_used(meter),
+            "threads_available": cpu_threads(), "kind": "oracle",
+            "sample": (f"oracle on one source, setup excluded: 10 identity-preconditioned FGMRES iterations on "
+                       f"the global K ({t_kry:.2f} s/iteration), one global residual ({t_res:.2f} s), one cycle of "
+                       f"the largest subdomain {big.shape} ({t_cyc:.2f} s); per DD iteration {t_iter:.1f} s = "
+                       f"Krylov + {ncol} residuals + {len(subs)} subdomain cycles; x the GPU line's mean count "
+                       f"{mean_it:.1f} (the oracle's own count at this size is not available)")}
+
+
+def synth_rhs(med):
+    from paper_1806_11277_gb300 import synth
+    return synth.point_rhs(med.shape, med.sources[:1])[0]
 
 
 def oracle_iteration_counts():
@@ -668,7 +735,7 @@ def run_gpu(args):
         q_src = torch.from_numpy(q_host).pin_memory()
         g_host = [torch.empty(g.shape, dtype=g.dtype).pin_memory() for g in grads]
         d2h = int(sum(g.numel() * 8 for g in grads))
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, min(args.steps, 5))):
         flush.fill_(1)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -683,7 +750,8 @@ def run_gpu(args):
         else:
             S.fgmres_solve(q_pin, u_pin)
         e2e_t.append(time.perf_counter() - t)
-    e2e_val = nsolve * world / (sum(e2e_t) / len(e2e_t))
+    # median over the calls: one call slowed by the host (page faults, scheduling) would pull a mean
+    e2e_val = nsolve * world / statistics.median(e2e_t)
 
     t_launch, alg, achieved = roofline()
     peak, peak_kind = peaks()
@@ -753,6 +821,9 @@ def run_gpu(args):
             "sample": (f"{args.cpu_iters} oracle FGMRES iterations (one whole restart cycle: Arnoldi steps, "
                        f"x-update and true residual) on each of the 4 media, setup excluded; seconds/iteration "
                        f"x mean iterations per solve ({mean_iters:.1f}, {src})")}
+    if rank == 0 and world == 1 and not args.no_cpu and cfg is not None and kw.get("precond", 0) == 1 \
+            and len(meds[0].shape) == 3:
+        line["cpu_baseline"] = oracle_dd_sample(meds[0], kw, its)
     if rank == 0 and world == 1 and not args.no_cpu and args.config == "c1":
         # the 64x64 case is small enough for whole oracle solves (3-level V(1,1), alpha 0.2)
         from oracle import krylov, multigrid as mg, operators as op

@@ -94,3 +94,17 @@ def test_every_bench_config_passes_host_validation():
         with pytest.raises(ehs.EhsError) as e:
             ehs.solver_for(mk(), **kw)
         assert e.value.status == 2, (name, str(e.value))
+
+
+def test_oracle_dd_sample_of_the_3d_lines():
+    """The CPU baseline of the 3D DD lines (one global residual, one cycle of the
+    largest subdomain and ten Krylov iterations of the oracle, extrapolated to a
+    DD-preconditioned iteration) runs on a small medium with the lines' DD-MG and
+    DD-MG-DD options and reports a positive rate with its sample description."""
+    import bench
+    from paper_1806_11277_gb300 import synth
+    med = synth.layered_3d(n=32, seed=0, corr=4.0, abl=4)
+    base = dict(levels=3, alpha=0.5, w=[0.5, 0.5], dd=(2, 2, 2), dd_overlap=2, dd_pad=4, coarse_dd=(1, 1, 1))
+    for kw in (base, dict(base, coarse_dd=(2, 2, 1), coarse_dd_overlap=1)):
+        r = bench.oracle_dd_sample(med, kw, [20, 22])
+        assert r["value"] > 0 and r["kind"] == "oracle" and "8 subdomain cycles" in r["sample"]
