@@ -77,7 +77,7 @@ ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one col
 ST_ROWS_L1_BYTES_PER_CELL = 45 * 4 + 24 + 24
 # DRAM read + write bytes of one roofline-kernel launch (one colour) of the default line, from an
 # ncu capture of the kernel as it stands (None whenever the kernel changes): mean of 7 warm launches
-ROOF_TRAFFIC_C2 = 450.84e6 + 5.88e6
+ROOF_TRAFFIC_C2 = 450.85e6 + 5.91e6
 
 # Stencil kernels of the default line (the metric's "stencil HBM GB/s"), each timed through the
 # C ABI call that launches it alone: algorithmic bytes per cell of the level it runs on (each
@@ -98,6 +98,18 @@ STENCIL = (
 def media(seed=0):
     from paper_1806_11277_gb300 import synth
     return [synth.random_2d(n=N_GRID, sigma=s, seed=seed) for s in SIGMAS]
+
+
+def small_case():
+    """The default line's solver on 4 media of 256x256 (the same Poisson ratios): every
+    kernel of the line with the same tile and subdomain shapes (coarsest 64x64 in 4x4
+    subdomains of 16x16 cells, as the 128x128 coarsest grid's 8x8), its vectors and
+    tables still larger than L2, a few GB on the device: the case ncu section captures
+    run on."""
+    from paper_1806_11277_gb300 import synth
+    kw = default_kw()
+    kw["coarse_dd"] = (4, 4, 1)
+    return [synth.random_2d(n=256, sigma=s, seed=0) for s in SIGMAS], kw
 
 
 _EXACT5W = dict(levels=5, alpha=0.4, w=[0.75, 0.5, 0.25, 0.25], cycle=2, coarse_dd=(1, 1, 1), coarse_fmt=0,
@@ -518,6 +530,10 @@ def run_gpu(args):
     kw = default_kw()
     if cfg is not None:
         kw.update(cfg["kw"])
+    if args.profile_small:
+        if cfg is not None:
+            raise SystemExit("--profile-small applies to the default line")
+        meds, kw = small_case()
     nsolve = len(meds) * (1 if cfg is None else cfg.get("nrhs", 1))
     fwi = cfg is not None and cfg.get("fwi", False)
     if fwi:
@@ -694,7 +710,7 @@ def run_gpu(args):
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize()
-    if args.profile_step:                 # one solve step between profiler start/stop
+    if args.profile_step or args.profile_small:   # one solve step between profiler start/stop
         torch.cuda.cudart().cudaProfilerStart()
         step()
         torch.cuda.synchronize()
@@ -874,6 +890,9 @@ def main():
                     help="skip the solves; only the roofline kernel timing loop (for ncu captures)")
     ap.add_argument("--profile-step", action="store_true",
                     help="run warm-up, then one step between cudaProfilerStart/Stop and exit")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="as --profile-step, on the small case of the default line's kernels (small_case(): "
+                         "4 media of 256x256, a few GB on the device) for ncu section captures")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -530,7 +530,28 @@ __global__ void __launch_bounds__(128) k_st_vupd_full(Grid g, int nrhs, const TI
 // MG-DD colour residual fused with its gather: local unknown e of sub-item bl
 // (= ((m * nsub) + s) * nrhs + r) receives (b - K_c x) at coarsest slot
 // map[s][e] of item m * nrhs + r, or 0 on padding (map -1); only the rows of
-// the colour's subdomains are evaluated.
+// the colour's subdomains are evaluated.  Two warps share 32 rows, each summing
+// the coefficients of one slot parity (a warp-uniform split: no divergence),
+// so that twice as many loads are in flight (the launch is small: the box
+// unknowns of one colour); the halves meet in shared memory.
+template <typename T, typename TT, int D, int LV, bool SYM>
+__device__ __forceinline__ typename CT<T>::type gather_row_half(const Grid& g, const TT* ts, long long c,
+                                                                const int i[3], const typename CT<T>::type* x,
+                                                                int a, int part) {
+  if (part == 0) {
+    if (a == 0) return st_row_ct<T, TT, D, LV, SYM, 0, false, 2, 0>(g, ts, c, i, x);
+    if (a == 1) return st_row_ct<T, TT, D, LV, SYM, 1, false, 2, 0>(g, ts, c, i, x);
+    if (a == 2) return st_row_ct<T, TT, D, LV, SYM, 2, false, 2, 0>(g, ts, c, i, x);
+    if constexpr (D == 3) return st_row_ct<T, TT, D, LV, SYM, 3, false, 2, 0>(g, ts, c, i, x);
+  } else {
+    if (a == 0) return st_row_ct<T, TT, D, LV, SYM, 0, false, 2, 1>(g, ts, c, i, x);
+    if (a == 1) return st_row_ct<T, TT, D, LV, SYM, 1, false, 2, 1>(g, ts, c, i, x);
+    if (a == 2) return st_row_ct<T, TT, D, LV, SYM, 2, false, 2, 1>(g, ts, c, i, x);
+    if constexpr (D == 3) return st_row_ct<T, TT, D, LV, SYM, 3, false, 2, 1>(g, ts, c, i, x);
+  }
+  return czero<typename CT<T>::type>();
+}
+
 template <typename T, typename TT, int D, int LV, bool SYM>
 __global__ void __launch_bounds__(128) k_st_resid_gather(Grid g, int nrhs, int nsub, int nloc,
                                                          const int* __restrict__ map, const TT* __restrict__ tab,
@@ -540,28 +561,34 @@ __global__ void __launch_bounds__(128) k_st_resid_gather(Grid g, int nrhs, int n
                                                          const int* __restrict__ il) {
   typedef typename CT<T>::type Cx;
   constexpr StencilLayout L = level_layout(D, LV);
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nloc) return;
+  __shared__ Cx half1[2][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int part = w & 1;                                  // slot parity this warp sums
+  const int e = blockIdx.x * 64 + (w >> 1) * 32 + lane;
   const int bl = il ? il[blockIdx.y] : blockIdx.y;
   const int r = bl % nrhs, s = (bl / nrhs) % nsub, m = bl / (nrhs * nsub);
   const long long N = g.ncell;
-  const int gs = map[(long long)s * nloc + e];
+  const int gs = e < nloc ? map[(long long)s * nloc + e] : -1;
   Cx v = czero<Cx>();
+  const long long vo = (long long)(m * nrhs + r) * (D + 1) * N;
   if (gs >= 0) {
     const int a = (int)(gs / N);
     const long long c = gs % N;
-    const long long vo = (long long)(m * nrhs + r) * (D + 1) * N;
     constexpr int nslot = SYM ? half_base(L, L.npair) : L.nslot;
     const TT* ts = tab + (long long)m * nslot * N;
     int i[3];
     cell_coords(g, c, i);
-    if (a == 0) v = st_row_ct<T, TT, D, LV, SYM, 0>(g, ts, c, i, x + vo);
-    else if (a == 1) v = st_row_ct<T, TT, D, LV, SYM, 1>(g, ts, c, i, x + vo);
-    else if (a == 2) v = st_row_ct<T, TT, D, LV, SYM, 2>(g, ts, c, i, x + vo);
-    else if constexpr (D == 3) v = st_row_ct<T, TT, D, LV, SYM, 3>(g, ts, c, i, x + vo);
-    v = csub(__ldg(b + vo + gs), v);
+    v = gather_row_half<T, TT, D, LV, SYM>(g, ts, c, i, x + vo, a, part);
   }
-  out[(long long)bl * nloc + e] = v;
+  if (part) half1[w >> 1][lane] = v;
+  __syncthreads();
+  if (!part && e < nloc) {
+    const Cx v1 = half1[w >> 1][lane];
+    v.x += v1.x;
+    v.y += v1.y;
+    if (gs >= 0) v = csub(__ldg(b + vo + gs), v);
+    out[(long long)bl * nloc + e] = v;
+  }
 }
 
 inline dim3 grid1(long long n, int items, int bs) { return dim3((unsigned)((n + bs - 1) / bs), items, 1); }
@@ -717,7 +744,7 @@ template <typename T, typename TT, bool SYM>
 static void resid_gather_t(const Grid& g, int items_l, int nrhs, int nsub, int nloc, const int* map, int v,
                            const TT* tab, const typename CT<T>::type* x, const typename CT<T>::type* b,
                            typename CT<T>::type* out, cudaStream_t s) {
-  const dim3 gr((unsigned)((nloc + 127) / 128), sel_items(items_l));
+  const dim3 gr((unsigned)((nloc + 63) / 64), sel_items(items_l));   // 64 unknowns per 128-thread block
   if (g.d == 2) {
     if (v == 1) k_st_resid_gather<T, TT, 2, 1, SYM><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);
     else k_st_resid_gather<T, TT, 2, 2, SYM><<<gr, 128, 0, s>>>(g, nrhs, nsub, nloc, map, tab, x, b, out, g_sel.list);

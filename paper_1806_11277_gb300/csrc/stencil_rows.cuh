@@ -52,8 +52,10 @@ __device__ __forceinline__ int half_slot_of(int ti, bool& mir) {
 // known at compile time so that every table and vector load of the row is
 // issued back to back.  SYM: the table is stored half (common.cuh HalfMap), an
 // unstored coefficient read from its mirror at the neighbour cell.
-// XCG: x is read through L2 only (x written earlier by the same launch on other SMs)
-template <typename T, typename TT, int D, int LV, bool SYM, int Q, int QE, bool XCG = false>
+// XCG: x is read through L2 only (x written earlier by the same launch on other SMs).
+// NS > 1: only the coefficients whose slot index is SI modulo NS (a share of the row, the
+// rest summed by NS - 1 other threads).
+template <typename T, typename TT, int D, int LV, bool SYM, int Q, int QE, bool XCG = false, int NS = 1, int SI = 0>
 __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
                                         const TT* __restrict__ tab,
                                         long long c, const int i[3],
@@ -76,7 +78,7 @@ __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
 #pragma unroll
         for (int ox = 0; ox < e0; ++ox) {
           const int jx = i[0] + lo0 + ox;
-          if (rin && jx >= 0 && jx < g.n[0]) {
+          if ((NS == 1 || (base + (oz * e1 + oy) * e0 + ox) % NS == SI) && rin && jx >= 0 && jx < g.n[0]) {
             const int ti = (oz * e1 + oy) * e0 + ox;
             const long long cj = c + (lo2 + oz) * sz + (lo1 + oy) * sy + (lo0 + ox);
             const TT* tp;
@@ -92,17 +94,17 @@ __device__ __forceinline__ void row_acc(typename CT<T>::type& y, const Grid& g,
         }
       }
     }
-    row_acc<T, TT, D, LV, SYM, Q + 1, QE, XCG>(y, g, tab, c, i, x);
+    row_acc<T, TT, D, LV, SYM, Q + 1, QE, XCG, NS, SI>(y, g, tab, c, i, x);
   }
 }
 
-template <typename T, typename TT, int D, int LV, bool SYM, int A, bool XCG = false>
+template <typename T, typename TT, int D, int LV, bool SYM, int A, bool XCG = false, int NS = 1, int SI = 0>
 __device__ __forceinline__ typename CT<T>::type st_row_ct(const Grid& g, const TT* tab,
                                                            long long c, const int i[3],
                                                            const typename CT<T>::type* x) {
   constexpr StencilLayout L = level_layout(D, LV);
   typename CT<T>::type y = czero<typename CT<T>::type>();
-  row_acc<T, TT, D, LV, SYM, L.row_first[A], L.row_first[A + 1], XCG>(y, g, tab, c, i, x);
+  row_acc<T, TT, D, LV, SYM, L.row_first[A], L.row_first[A + 1], XCG, NS, SI>(y, g, tab, c, i, x);
   return y;
 }
 

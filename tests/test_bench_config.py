@@ -72,7 +72,7 @@ def test_clock_sampler_parses_clocks_and_reasons(tmp_path, monkeypatch):
 
 
 def test_every_bench_config_passes_host_validation():
-    """Every bench workload (the default line and each --config) gets past
+    """Every bench workload (the default line, its small profiling case and each --config) gets past
     ehs_create's host-side checks of its options against its grid (levels,
     MG-DD split and overlap, formats): on a host without a GPU the create call
     then stops at its first CUDA call (EHS_ERR_CUDA), never at EHS_ERR_ARG."""
@@ -86,7 +86,7 @@ def test_every_bench_config_passes_host_validation():
         ehs.load(build.build())
     except FileNotFoundError:
         pytest.skip("nvcc not available")
-    cases = {"c2": (bench.media, {})}
+    cases = {"c2": (bench.media, {}), "small": (lambda: bench.small_case()[0], bench.small_case()[1])}
     cases.update({k: (v["media"], v["kw"]) for k, v in bench.OTHER.items()})
     for name, (mk, over) in cases.items():
         kw = bench.default_kw()
