@@ -138,6 +138,7 @@ struct ehs_ctx {
   int nblk = 1;
   double* hpin = nullptr;    // pinned host scratch
   double2* hstep = nullptr;  // pinned host copies of one Arnoldi step: h1 [items][12], h2 [items][12], norms
+  cudaEvent_t ev_step = nullptr;   // recorded after the copies of one Arnoldi step
   // CUDA graphs of the preconditioner application, one per Krylov direction j
   // (the input/output pointers differ per j), captured on a private stream
   bool use_graphs = true;
@@ -1032,28 +1033,29 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
         else cycle_rec<float>(c, c->H, 0, c->f_in, Zj, false);
       });
       launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, Zj, 1, nullptr, c->wq, 0, s);
-      // CGS2: h1 = V^H w; w -= V h1, h2 = V^H w; w -= V h2, ||w|| -- each reduction by the
-      // launch's last block
+      // CGS2: h1 = V^H w; w' = w - V h1 with h2 = V^H w' and ||w'||^2 in the same pass, whose
+      // last block also forms ||w' - V h2|| = sqrt(||w'||^2 - ||h2||^2); then one pass forms
+      // V_{j+1} = (w' - V h2) / ||.|| and its complex64 copy.  Each reduction is done by the
+      // launch's last block.
       const int nv = j + 1;
       int* k0 = c->kcnt;
       int* k1 = c->kcnt + items;
-      int* k2 = c->kcnt + 2 * items;
       launch_mdot_df(n, items, nv, c->Vq, c->wq, c->partq, nblk, s, k0, c->hq, c->hhost);
-      launch_mupdate_df(n, items, nv, c->Vq, c->hq, c->wq, c->partq, nblk, 1, nullptr, s, k1, c->h2q,
-                        c->hhost + (size_t)items * 12);
-      launch_mupdate_df(n, items, nv, c->Vq, c->h2q, c->wq, nullptr, nblk, 0, c->npq, s, k2, nullptr, nullptr,
-                        c->nrm, c->invq);
-      cnt(4); post();
-      // one round trip into pinned memory: h1, h2 (the reduce kernels' double copies) and the norms
+      launch_mupdate_df(n, items, nv, c->Vq, c->hq, c->wq, c->partq, nblk, 1, c->npq, s, k1, c->h2q,
+                        c->hhost + (size_t)items * 12, c->nrm, c->invq);
+      // one round trip into pinned memory (h1, h2 and the norms), overlapped with the last pass
       double2* ph1 = c->hstep;
       double2* ph2 = c->hstep + (size_t)items * 12;
       double* phn = (double*)(c->hstep + (size_t)items * 24);
       CK(cudaMemcpyAsync(ph1, c->hhost, (size_t)items * 24 * sizeof(double2), cudaMemcpyDeviceToHost, s));
-      sync_read(c, phn, c->nrm, items * sizeof(double));
+      CK(cudaMemcpyAsync(phn, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(c->ev_step, s));
+      launch_update_scale_cast_df(n, items, nv, c->Vq, c->h2q, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n,
+                                  c->f_in, nblk, s);
+      cnt(4); post();                        // with the operator launch above
+      CK(cudaEventSynchronize(c->ev_step));
       if (!A.step(j, ph1, ph2, phn)) break;
       set_active(c, A.active);
-      SelScope sel2 = global_sel(c);
-      launch_scale_cast_df(n, items, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n, c->f_in, s); cnt(); post();
     }
     A.solve_y(yh);
     // y to df64 on the device via the double2 -> df64 conversion
@@ -1252,6 +1254,7 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));
     CK(cudaMallocHost((void**)&c->hstep, (size_t)items * 25 * sizeof(double2)));
     CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_step, cudaEventDisableTiming));
     c->pg.assign(m, nullptr);
     c->pg_nodes.assign(m, 0);
     c->pg_ver.assign(m, -1);
@@ -1278,6 +1281,7 @@ ehs_status ehs_destroy(ehs_ctx* c) {
   for (cudaGraphExec_t g : c->pg)
     if (g) cudaGraphExecDestroy(g);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->ev_step) cudaEventDestroy(c->ev_step);
   for (void* p : c->allocs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);

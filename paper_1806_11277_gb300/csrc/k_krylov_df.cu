@@ -114,6 +114,36 @@ __device__ __forceinline__ void reduce_norm_last(int item, int nblk, const float
   }
 }
 
+// Norm of w'' = w' - V h2 without forming it: with h2 = V^H w' and V orthonormal,
+// ||w''||^2 = ||w'||^2 - ||h2||^2 (the neglected term is h2^H (V^H V - I) h2, of the
+// order of the basis' loss of orthogonality times ||h2||^2, itself the square of a
+// second-pass correction).  Sums the block partials of ||w'||^2 as reduce_norm_last
+// does, subtracts the squares of the nv coefficients this block just wrote to h
+// (df64), and stores the norm and its df64 inverse.
+__device__ __forceinline__ void reduce_norm_pythag_last(int item, int nv, int nblk, const float2* part,
+                                                        const float4* h, double* out, float2* inv) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    dfr s = df_zero();
+    for (int b = lane; b < nblk; b += 32) {
+      const float2 v = __ldcg(part + (long long)item * nblk + b);
+      s = df_add(s, {v.x, v.y});
+    }
+    s = warp_sum_df(s);
+    if (lane == 0) {
+      for (int i = 0; i < nv; ++i) {
+        const dfc hv = dfc_ldv(h + (long long)item * nv + i);   // written by this block
+        s = df_sub(s, df_add(df_mul(hv.re, hv.re), df_mul(hv.im, hv.im)));
+      }
+      const double n2 = df_to_d(s);
+      const double nrm = sqrt(n2 > 0.0 ? n2 : 0.0);   // one FP64 sqrt per item
+      out[item] = nrm;
+      const dfr iv = df_from_d(nrm > 0.0 ? 1.0 / nrm : 0.0);
+      inv[item] = make_float2(iv.hi, iv.lo);
+    }
+  }
+}
+
 // partial dots conj(V_i) . w per block; with cnt, the last block of each item also forms
 // the sums (out: df64, outd: double copy for the host)
 template <int NV>
@@ -139,7 +169,8 @@ __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const fl
 
 // w -= sum_i V_i h_i; optional partial dots of V with the new w and |w|^2.
 // With cnt, the last block of each item also forms the dots' sums (out, outd)
-// or the norm (nrm, inv = 1/norm).
+// and/or the norm (nrm, inv = 1/norm): with both, the norm of the vector that
+// removing V out from w would leave (reduce_norm_pythag_last).
 // h sits in shared memory and the dot pass re-reads V_i (an L1 hit: the block
 // read it a moment earlier), which keeps the kernel at two blocks per SM.
 template <int NV>
@@ -182,7 +213,41 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
   if (nrm_part) block_store_norm(dacc_val(nacc), nrm_part, item, nblk);
   if (cnt && (dot || nrm_part) && last_block(cnt, item, nblk)) {
     if (dot) reduce_dots_last(item, NV, nblk, part, out, outd, cnt);
-    else reduce_norm_last(item, nblk, nrm_part, nrm, inv, cnt);
+    if (dot && nrm_part) {
+      __syncthreads();                              // the dots' sums are in out
+      reduce_norm_pythag_last(item, NV, nblk, nrm_part, out, nrm, inv);
+    } else if (nrm_part) {
+      reduce_norm_last(item, nblk, nrm_part, nrm, inv, cnt);
+    }
+  }
+}
+
+// The last pass of an Arnoldi step: V_{j+1} = (w - sum_i V_i h_i) * inv (df64) and
+// its complex64 copy, the next preconditioner input; w itself is not written.
+template <int NV>
+__global__ void __launch_bounds__(KB, 3) k_update_scale_cast_df(long long n, int items, const float4* __restrict__ V,
+                                                                const float4* __restrict__ h,
+                                                                const float4* __restrict__ w,
+                                                                const float2* __restrict__ inv,
+                                                                float4* __restrict__ out, float2* __restrict__ out32,
+                                                                int nblk, const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  __shared__ float4 hs[NV];
+  if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
+  __syncthreads();
+  const float2 sc = inv[item];
+  const dfr iv = {sc.x, sc.y};
+  const float4* wv = w + (long long)item * n;
+  for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+    dcacc sv = dcacc_zero();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const float4 hv = hs[i];
+      dcacc_fma(sv, dfc_ld(V + ((long long)i * items + item) * n + e), dfc{{hv.x, hv.y}, {hv.z, hv.w}});
+    }
+    const dfc v = dfc_scale(dfc_sub(dfc_ld(wv + e), dcacc_val(sv)), iv);
+    dfc_st(out + (long long)item * n + e, v);
+    out32[(long long)item * n + e] = dfc_to_f2(v);
   }
 }
 
@@ -432,6 +497,17 @@ void launch_mupdate_df(long long n, int items, int nv, const float4* V, const fl
   switch (nv) {
 #define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part, g_sel.list, \
                                                       cnt, out, outd, nrm, inv); break;
+    EHS_NV_CASES(X)
+#undef X
+    default: break;
+  }
+}
+void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V, const float4* h, const float4* w,
+                                 const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s) {
+  const dim3 g(nblk, sel_items(items));
+  switch (nv) {
+#define X(k) case k: k_update_scale_cast_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, inv, out, out32, nblk, g_sel.list); \
+    break;
     EHS_NV_CASES(X)
 #undef X
     default: break;

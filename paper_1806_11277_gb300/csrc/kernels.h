@@ -198,6 +198,9 @@ void launch_mupdate_df(long long n, int items, int nv, const float4* V, const fl
                        float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s, int* cnt = nullptr,
                        float4* out = nullptr, double2* outd = nullptr, double* nrm = nullptr, float2* inv = nullptr);
 // out = w / norm (inv per item) and out32 = its complex64 copy
+// V_{j+1} = (w - V h) * inv and its complex64 copy (the last pass of an Arnoldi step)
+void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V, const float4* h, const float4* w,
+                                 const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s);
 void launch_scale_cast_df(long long n, int items, const float4* w, const float2* inv, float4* out, float2* out32,
                           cudaStream_t s);
 void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s);
