@@ -90,7 +90,8 @@ ROOF_TRAFFIC_C2 = 450.85e6 + 5.91e6
 STENCIL = (
     ("k_fine_sweep_tile (fine level, whole red-black sweep)", "sweep", 0, 88),
     ("k_fine_resid_restrict_tile (fine residual + restriction)", "resid_restrict", 0, 70),
-    ("k_st_rows2<float,__half2,2,1,true> (Galerkin level 1, all rows, FP16 half table)", "rows", 1, 45 * 4 + 48),
+    ("k_st_rows / k_st_rows2 <float,__half2,2,1,true> (Galerkin level 1, all rows, FP16 half table; the "
+     "setup autotuner's launch shape)", "rows", 1, 45 * 4 + 48),
     ("k_prolong_add<float,2> (level 2 -> level 1 correction)", "prolong", 1, 54),
 )
 

@@ -40,14 +40,17 @@ constexpr int SW_X = 32, SW_Y = 16, SW_H = 3;                 // sweep tile and 
 constexpr int SWS_X = SW_X + 2 * SW_H, SWS_Y = SW_Y + 2 * SW_H;
 constexpr int SW_RX = SW_X + 2, SW_RY = SW_Y + 2;             // red region: tile + one-cell ring
 constexpr int SW_NRED = SW_RX * SW_RY / 2;                    // 306 red cells
-constexpr int SW_T = SW_X * SW_Y / 2;                         // 256 threads: one cell pair each
-constexpr int SW_RPT = (SW_NRED + SW_T - 1) / SW_T;           // red cells per thread (2)
+constexpr int SW_TB = SW_X * SW_Y / 2;                        // 256 black cells: one per thread
+constexpr int SW_T = 320;                                     // 10 warps: every red cell in one round
+constexpr int SW_RPT = (SW_NRED + SW_T - 1) / SW_T;           // red cells per thread (1)
+static_assert(SW_T >= SW_TB && SW_T % 32 == 0, "sweep threads");
 
 constexpr int RR_X = 32, RR_Y = 16, RR_H = 2;                 // residual + restriction tile
 constexpr int RRS_X = RR_X + 2 * RR_H, RRS_Y = RR_Y + 2 * RR_H;
 constexpr int RR_RX = RR_X + 2, RR_RY = RR_Y + 2;             // fine residual region
-constexpr int RR_T = 256;
+constexpr int RR_T = 256;                                     // 8 warps (10 measured slower here)
 constexpr int RR_RPT = (RR_RX * RR_RY + RR_T - 1) / RR_T;     // residual cells per thread (3)
+static_assert(RR_T >= RR_X * RR_Y / 2, "one restriction output per thread");
 
 static_assert(SW_X % 2 == 0 && RR_X % 4 == 0 && RR_Y % 2 == 0, "tile shapes");
 
@@ -277,7 +280,7 @@ __device__ __forceinline__ void cell_update(const Tile<W, H>& S, int sx, int sy,
 typedef Tile<SWS_X, SWS_Y> SweepTile;
 typedef Tile<RRS_X, RRS_Y> ResTile;
 
-__global__ void __launch_bounds__(SW_T, 4) k_fine_sweep_tile(Grid g, Grid gc, int nrhs, const float4* __restrict__ cf,
+__global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, int nrhs, const float4* __restrict__ cf,
                                                              FP P, float wu, float wp,
                                                              const float2* __restrict__ b,
                                                              const float2* __restrict__ xi,
@@ -333,6 +336,7 @@ __global__ void __launch_bounds__(SW_T, 4) k_fine_sweep_tile(Grid g, Grid gc, in
   __syncthreads();
   // ---- black cells of the tile from the red-updated iterate; outputs
   const int t = threadIdx.x;
+  if (t >= SW_TB) return;                                          // no barrier follows
   const int ty = t / (SW_X / 2), kx = t % (SW_X / 2);
   const int gy = Y0 + ty;
   const int gxb = X0 + 2 * kx + ((gy + 1) & 1);                    // (gx + gy) odd: black
@@ -425,6 +429,7 @@ __global__ void __launch_bounds__(RR_T, 4) k_fine_resid_restrict_tile(Grid g, Gr
   __syncthreads();
   // restriction: thread t < 128 forms u_0 and u_1 of coarse cell t, thread t >= 128 its pressure
   constexpr int CX = RR_X / 2, CY = RR_Y / 2;
+  if (threadIdx.x >= 2 * CX * CY) return;                          // no barrier follows
   const int t = threadIdx.x % (CX * CY), half = threadIdx.x / (CX * CY);
   const int I = X0 / 2 + t % CX, J = Y0 / 2 + t / CX;
   if (I >= gc.n[0] || J >= gc.n[1]) return;

@@ -36,13 +36,40 @@ __device__ __forceinline__ dfr warp_sum_df(dfr v) {
   return v;
 }
 
-__device__ __forceinline__ void block_store_df(const dfc* acc, int nv, float4* part, int item, int nblk) {
+__device__ __forceinline__ dfc shfl_dfc(dfc v, int o) { return {shfl_df(v.re, o), shfl_df(v.im, o)}; }
+
+// Block partials of NV sums.  The warp stage halves the values per lane at each
+// exchange (reduce-scatter): at the exchange with lane ^ o a lane keeps one half
+// of its values, sends the other and adds what it receives, so that after
+// log2(P) exchanges (P = NV rounded up to a power of two) each value's sum over
+// 32 / P lanes sits in one lane, and the remaining exchanges add across those.
+// That moves P - 1 + log2(32 / P) values per lane instead of 5 NV.  The order of
+// every sum is fixed by the lane indices, so the result does not depend on timing.
+template <int NV>
+__device__ __forceinline__ void block_store_df(const dfc* acc, float4* part, int item, int nblk) {
+  constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : 16;
+  static_assert(NV <= MAXV && MAXV <= 16, "sums per block");
   __shared__ dfc sh[KB / 32][MAXV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = 0; i < nv; ++i) {
-    const dfc v = warp_sum_df(acc[i]);
-    if (lane == 0) sh[wid][i] = v;
+  dfc v[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) v[k] = k < NV ? acc[k] : dfc_zero();
+  int idx = 0;
+#pragma unroll
+  for (int cnt = P, o = 16; cnt > 1; cnt >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < cnt / 2; ++k) {
+      const dfc keep = up ? v[cnt / 2 + k] : v[k];
+      const dfc send = up ? v[k] : v[cnt / 2 + k];
+      v[k] = dfc_add(keep, shfl_dfc(send, o));
+    }
+    if (up) idx += cnt / 2;
   }
+#pragma unroll
+  for (int o = 16 / P; o > 0; o >>= 1) v[0] = dfc_add(v[0], shfl_dfc(v[0], o));
+  if ((lane & (32 / P - 1)) == 0 && idx < NV) sh[wid][idx] = v[0];
+  const int nv = NV;
   __syncthreads();
   if (threadIdx.x < nv) {
     dfc s = dfc_zero();
@@ -163,7 +190,7 @@ __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const fl
   dfc vals[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) vals[i] = dcacc_val(acc[i]);
-  block_store_df(vals, NV, part, item, nblk);
+  block_store_df<NV>(vals, part, item, nblk);
   if (cnt && last_block(cnt, item, nblk)) reduce_dots_last(item, NV, nblk, part, out, outd, cnt);
 }
 
@@ -208,7 +235,7 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
     dfc vals[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) vals[i] = dcacc_val(acc[i]);
-    block_store_df(vals, NV, part, item, nblk);
+    block_store_df<NV>(vals, part, item, nblk);
   }
   if (nrm_part) block_store_norm(dacc_val(nacc), nrm_part, item, nblk);
   if (cnt && (dot || nrm_part) && last_block(cnt, item, nblk)) {

@@ -78,6 +78,14 @@ void launch_table_cast(long long n, const double2* in, typename CT<T>::type* out
 // 3D; the half formats serve the complex64 cycle only)
 // var: residual-pass launch shape, 0 .. ST_ROWS_VARIANTS-1 (chosen by the setup autotuner)
 #define ST_ROWS_VARIANTS 4
+// layout variant of a Galerkin level: 1 = first coarse level, 2 = all coarser ones (throws otherwise)
+int layout_variant(const StencilLayout& L, int d);
+// residual pass on a Galerkin level of layout variant v (mode 0: y = K_c x, 1: y = b - K_c x;
+// colour >= 0: pressure rows of that colour only)
+template <typename T>
+void launch_st_rows(const Grid& g, int items, int nrhs, int v, const void* tab, int fmt,
+                    const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y, int mode,
+                    int colour, int var, cudaStream_t s);
 template <typename T>
 void launch_st_apply(const Grid& g, int items, int nrhs, const StencilLayout& L, const void* tab, int fmt,
                      const typename CT<T>::type* x, const typename CT<T>::type* b, typename CT<T>::type* y,
