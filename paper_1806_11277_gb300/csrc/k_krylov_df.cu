@@ -174,7 +174,7 @@ __device__ __forceinline__ void reduce_norm_pythag_last(int item, int nv, int nb
 // partial dots conj(V_i) . w per block; with cnt, the last block of each item also forms
 // the sums (out: df64, outd: double copy for the host)
 template <int NV>
-__global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const float4* __restrict__ V,
+__global__ void __launch_bounds__(KB, 2) k_mdot_df(long long n, int items, const float4* __restrict__ V,
                                                 const float4* __restrict__ w, float4* part, int nblk,
                                                 const int* __restrict__ il, int* cnt, float4* out, double2* outd) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
@@ -183,9 +183,13 @@ __global__ void __launch_bounds__(KB) k_mdot_df(long long n, int items, const fl
   for (int i = 0; i < NV; ++i) acc[i] = dcacc_zero();
   const float4* wv = w + (long long)item * n;
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+    // every load of the element first: NV + 1 independent 16-byte loads in flight per thread
+    dfc vv[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
     const dfc we = dfc_ld(wv + e);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], dfc_ld(V + ((long long)i * items + item) * n + e), we);
+    for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], vv[i], we);
   }
   dfc vals[NV];
 #pragma unroll
