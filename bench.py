@@ -46,7 +46,7 @@ N_GRID = 512
 # coarse local inverses (the paper's half-precision inverses, Sec. 4), FP32
 # arithmetic in the cycle, double-float FGMRES.
 LEVELS = 3
-ALPHA = 0.25
+ALPHA = 0.2
 W_LEVELS = (0.75, 0.5)
 CYCLE = 1                          # V(1,1)
 COARSE_DD = (8, 8, 1)

@@ -59,19 +59,21 @@ __device__ __forceinline__ dfr df_from_d(double a) {
 __device__ __forceinline__ double df_to_d(dfr a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ dfr df_zero() { return {0.0f, 0.0f}; }
 
-// complex df64
+// complex df64, stored as a float4 (re.hi, im.hi, re.lo, im.lo): the high parts and the low
+// parts of the two components each sit in one aligned register pair after a load, the
+// operand form of the paired FP32 instructions (dacc2 below)
 struct dfc {
   dfr re, im;
 };
 __device__ __forceinline__ dfc dfc_ld(const float4* p) {
   const float4 v = __ldg(p);
-  return {{v.x, v.y}, {v.z, v.w}};
+  return {{v.x, v.z}, {v.y, v.w}};
 }
 __device__ __forceinline__ dfc dfc_ldv(const float4* p) {   // plain (non-__ldg) load
   const float4 v = *p;
-  return {{v.x, v.y}, {v.z, v.w}};
+  return {{v.x, v.z}, {v.y, v.w}};
 }
-__device__ __forceinline__ void dfc_st(float4* p, dfc a) { *p = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ void dfc_st(float4* p, dfc a) { *p = make_float4(a.re.hi, a.im.hi, a.re.lo, a.im.lo); }
 __device__ __forceinline__ dfc dfc_zero() { return {df_zero(), df_zero()}; }
 __device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
 __device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
@@ -139,5 +141,47 @@ __device__ __forceinline__ void dcacc_fma(dcacc& a, dfc x, dfc y) {
   dacc_fma(a.im, x.im, y.re);
 }
 __device__ __forceinline__ dfc dcacc_val(dcacc a) { return {dacc_val(a.re), dacc_val(a.im)}; }
+
+// The same compensated accumulation for the two components of a complex sum at
+// once, lane 0 = real part, lane 1 = imaginary part, on the paired FP32
+// instructions (__fmul2_rn, __ffma2_rn, __fadd2_rn: per lane the rounding of
+// the scalar operation), so each lane performs dacc_fma's steps.  Operands come
+// as (high, low) pairs of lane vectors.
+struct dacc2 {
+  float2 s, c;
+};
+__device__ __forceinline__ dacc2 dacc2_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+// a += x * y lane-wise (x = xh + xl, y = yh + yl)
+__device__ __forceinline__ void dacc2_fma(dacc2& a, float2 xh, float2 xl, float2 yh, float2 yl) {
+  const float2 p = __fmul2_rn(xh, yh);
+  const float2 pe = __ffma2_rn(xh, yl, __ffma2_rn(xl, yh, __ffma2_rn(xh, yh, f2neg(p))));
+  const float2 t = __fadd2_rn(a.s, p);
+  const float2 bb = __fadd2_rn(t, f2neg(a.s));
+  const float2 sg = __fadd2_rn(__fadd2_rn(a.s, f2neg(__fadd2_rn(t, f2neg(bb)))), __fadd2_rn(p, f2neg(bb)));
+  a.s = t;
+  a.c = __fadd2_rn(a.c, __fadd2_rn(sg, pe));
+}
+__device__ __forceinline__ dfc dacc2_val(dacc2 a) { return {df_two_sum(a.s.x, a.c.x), df_two_sum(a.s.y, a.c.y)}; }
+// The lane vectors of one complex df64 value v: (re, im) and (im, re), high and low parts.
+struct dfc2 {
+  float2 h, l, sh, sl;
+};
+__device__ __forceinline__ dfc2 dfc2_of(dfc v) {
+  return {make_float2(v.re.hi, v.im.hi), make_float2(v.re.lo, v.im.lo), make_float2(v.im.hi, v.re.hi),
+          make_float2(v.im.lo, v.re.lo)};
+}
+// a += conj(x) * w, with wa = (w.re, -w.re) and wb = (w.im, w.im) (high, low parts) formed once
+// per element: lane 0 sums x.re w.re + x.im w.im, lane 1 -x.im w.re + x.re w.im
+__device__ __forceinline__ void dacc2_cfma(dacc2& a, const dfc2& x, float2 wah, float2 wal, float2 wbh, float2 wbl) {
+  dacc2_fma(a, x.h, x.l, wah, wal);
+  dacc2_fma(a, x.sh, x.sl, wbh, wbl);
+}
+// a += x * h, with ha = (h.re, h.re) and hb = (-h.im, h.im) (high, low parts): lane 0 sums
+// x.re h.re - x.im h.im, lane 1 x.im h.re + x.re h.im
+__device__ __forceinline__ void dacc2_mfma(dacc2& a, const dfc2& x, float2 hah, float2 hal, float2 hbh, float2 hbl) {
+  dacc2_fma(a, x.h, x.l, hah, hal);
+  dacc2_fma(a, x.sh, x.sl, hbh, hbl);
+}
 
 }  // namespace ehs

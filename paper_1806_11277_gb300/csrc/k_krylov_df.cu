@@ -111,7 +111,7 @@ __device__ __forceinline__ void reduce_dots_last(int item, int nv, int nblk, con
     dfc s = dfc_zero();
     for (int b = lane; b < nblk; b += 32) {
       const float4 v = __ldcg(part + o * nblk + b);
-      s = dfc_add(s, dfc{{v.x, v.y}, {v.z, v.w}});
+      s = dfc_add(s, dfc{{v.x, v.z}, {v.y, v.w}});      // the storage order of dfc_st
     }
     s = warp_sum_df(s);
     if (lane == 0) {
@@ -171,6 +171,14 @@ __device__ __forceinline__ void reduce_norm_pythag_last(int item, int nv, int nb
   }
 }
 
+// The lane vectors dacc2_mfma takes for a coefficient h (df64 complex): (h.re, h.re) and
+// (-h.im, h.im), high parts then low parts, as two float4.
+__device__ __forceinline__ void load_hpairs(const float4* hp, float4* out) {
+  const dfc hv = dfc_ldv(hp);
+  out[0] = make_float4(hv.re.hi, hv.re.hi, hv.re.lo, hv.re.lo);
+  out[1] = make_float4(-hv.im.hi, hv.im.hi, -hv.im.lo, hv.im.lo);
+}
+
 // partial dots conj(V_i) . w per block; with cnt, the last block of each item also forms
 // the sums (out: df64, outd: double copy for the host)
 template <int NV>
@@ -178,9 +186,9 @@ __global__ void __launch_bounds__(KB, 2) k_mdot_df(long long n, int items, const
                                                 const float4* __restrict__ w, float4* part, int nblk,
                                                 const int* __restrict__ il, int* cnt, float4* out, double2* outd) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
-  dcacc acc[NV];
+  dacc2 acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = dcacc_zero();
+  for (int i = 0; i < NV; ++i) acc[i] = dacc2_zero();
   const float4* wv = w + (long long)item * n;
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
     // every load of the element first: NV + 1 independent 16-byte loads in flight per thread
@@ -188,12 +196,14 @@ __global__ void __launch_bounds__(KB, 2) k_mdot_df(long long n, int items, const
 #pragma unroll
     for (int i = 0; i < NV; ++i) vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
     const dfc we = dfc_ld(wv + e);
+    const float2 wah = make_float2(we.re.hi, -we.re.hi), wal = make_float2(we.re.lo, -we.re.lo);
+    const float2 wbh = make_float2(we.im.hi, we.im.hi), wbl = make_float2(we.im.lo, we.im.lo);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], vv[i], we);
+    for (int i = 0; i < NV; ++i) dacc2_cfma(acc[i], dfc2_of(vv[i]), wah, wal, wbh, wbl);
   }
   dfc vals[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) vals[i] = dcacc_val(acc[i]);
+  for (int i = 0; i < NV; ++i) vals[i] = dacc2_val(acc[i]);
   block_store_df<NV>(vals, part, item, nblk);
   if (cnt && last_block(cnt, item, nblk)) reduce_dots_last(item, NV, nblk, part, out, outd, cnt);
 }
@@ -211,26 +221,30 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
                                                       const int* __restrict__ il, int* cnt, float4* out,
                                                       double2* outd, double* nrm, float2* inv) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
-  __shared__ float4 hs[NV];
-  if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
+  __shared__ float4 hs[NV][2];
+  if (threadIdx.x < NV) load_hpairs(h + (long long)item * NV + threadIdx.x, hs[threadIdx.x]);
   __syncthreads();
-  dcacc acc[NV];
+  dacc2 acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = dcacc_zero();
+  for (int i = 0; i < NV; ++i) acc[i] = dacc2_zero();
   dacc nacc = dacc_zero();
   float4* wv = w + (long long)item * n;
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
-    dcacc sv = dcacc_zero();
+    dacc2 sv = dacc2_zero();
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      const float4 hv = hs[i];
-      dcacc_fma(sv, dfc_ld(V + ((long long)i * items + item) * n + e), dfc{{hv.x, hv.y}, {hv.z, hv.w}});
+      const float4 a = hs[i][0], b = hs[i][1];
+      dacc2_mfma(sv, dfc2_of(dfc_ld(V + ((long long)i * items + item) * n + e)), make_float2(a.x, a.y),
+                 make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w));
     }
-    const dfc we = dfc_sub(dfc_ldv(wv + e), dcacc_val(sv));
+    const dfc we = dfc_sub(dfc_ldv(wv + e), dacc2_val(sv));
     dfc_st(wv + e, we);
     if (dot) {
+      const float2 wah = make_float2(we.re.hi, -we.re.hi), wal = make_float2(we.re.lo, -we.re.lo);
+      const float2 wbh = make_float2(we.im.hi, we.im.hi), wbl = make_float2(we.im.lo, we.im.lo);
 #pragma unroll
-      for (int i = 0; i < NV; ++i) dcacc_cfma(acc[i], dfc_ld(V + ((long long)i * items + item) * n + e), we);
+      for (int i = 0; i < NV; ++i)
+        dacc2_cfma(acc[i], dfc2_of(dfc_ld(V + ((long long)i * items + item) * n + e)), wah, wal, wbh, wbl);
     }
     dacc_fma(nacc, we.re, we.re);
     dacc_fma(nacc, we.im, we.im);
@@ -238,7 +252,7 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
   if (dot) {
     dfc vals[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) vals[i] = dcacc_val(acc[i]);
+    for (int i = 0; i < NV; ++i) vals[i] = dacc2_val(acc[i]);
     block_store_df<NV>(vals, part, item, nblk);
   }
   if (nrm_part) block_store_norm(dacc_val(nacc), nrm_part, item, nblk);
@@ -263,20 +277,21 @@ __global__ void __launch_bounds__(KB, 3) k_update_scale_cast_df(long long n, int
                                                                 float4* __restrict__ out, float2* __restrict__ out32,
                                                                 int nblk, const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
-  __shared__ float4 hs[NV];
-  if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
+  __shared__ float4 hs[NV][2];
+  if (threadIdx.x < NV) load_hpairs(h + (long long)item * NV + threadIdx.x, hs[threadIdx.x]);
   __syncthreads();
   const float2 sc = inv[item];
   const dfr iv = {sc.x, sc.y};
   const float4* wv = w + (long long)item * n;
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
-    dcacc sv = dcacc_zero();
+    dacc2 sv = dacc2_zero();
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      const float4 hv = hs[i];
-      dcacc_fma(sv, dfc_ld(V + ((long long)i * items + item) * n + e), dfc{{hv.x, hv.y}, {hv.z, hv.w}});
+      const float4 a = hs[i][0], b = hs[i][1];
+      dacc2_mfma(sv, dfc2_of(dfc_ld(V + ((long long)i * items + item) * n + e)), make_float2(a.x, a.y),
+                 make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w));
     }
-    const dfc v = dfc_scale(dfc_sub(dfc_ld(wv + e), dcacc_val(sv)), iv);
+    const dfc v = dfc_scale(dfc_sub(dfc_ld(wv + e), dacc2_val(sv)), iv);
     dfc_st(out + (long long)item * n + e, v);
     out32[(long long)item * n + e] = dfc_to_f2(v);
   }

@@ -1,6 +1,6 @@
 """Writes c2_oracle_iters.json: the CPU oracle's FGMRES(10) iteration counts
 (and final relative residuals) for the 512 x 512 four-Poisson-ratio workload
-of bench.py: 3-level V(1,1) cycle, alpha 0.25, damping 0.75/0.5, economic
+of bench.py: 3-level V(1,1) cycle, alpha 0.2, damping 0.75/0.5, economic
 red-black Vanka, MG-DD coarsest solve (128 x 128 coarsest grid split 8 x 8,
 overlap 3), tol 1e-6.  Also writes c2_oracle_samples.json: per medium the
 oracle's solution at a fixed seeded sample of DOFs (uniform over the whole
@@ -25,7 +25,7 @@ from oracle import krylov, multigrid as mg, operators as op  # noqa: E402
 from paper_1806_11277_gb300 import synth  # noqa: E402
 
 SIGMAS = (0.25, 0.4, 0.45, 0.49)
-LEVELS, ALPHA, W, GAMMA = 3, 0.25, [0.75, 0.5], 1
+LEVELS, ALPHA, W, GAMMA = 3, 0.2, [0.75, 0.5], 1
 COARSE_DD, COARSE_OVERLAP = (8, 8), 3
 N_UNIFORM, N_LARGEST, SAMPLE_SEED = 1024, 64, 2024
 
