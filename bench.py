@@ -66,18 +66,19 @@ def default_kw():
                 coarse_dd_overlap=COARSE_OVERLAP, coarse_fmt=COARSE_FMT, coef_half=COEF_HALF)
 
 
-# Roofline kernel of the default line: the MG-DD coarsest local products (k_dense_apply_v,
-# the largest share of the solve in the ncu launch list); per launch (one colour) the live
-# n_s x n_s entries of every subdomain inverse of the colour (4 B each, FP16 pairs) + r and z
+# Roofline kernel of the default line: the MG-DD coarsest local products with the scatter-add
+# (k_dense_apply_vs, the largest share of the solve in the ncu launch list); per launch (one
+# colour) the live n_s x n_s entries of every subdomain inverse of the colour (4 B each, FP16
+# pairs) + r read and the coarsest vector read and written at the live rows
 ROOF = "coarse"
-ROOF_KERNEL = ("k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 16 subdomain inverses "
-               "x 4 media)")
+ROOF_KERNEL = ("k_dense_apply_vs<__half2> (MG-DD coarsest local products with the scatter-add: one colour = "
+               "16 subdomain inverses x 4 media)")
 # Galerkin level-1 apply (k_st_rows): 45 stored stencil coefficients of the half table (FP16 pairs,
 # 4 B; 87 per row set, the mirrored ones read at the neighbour cell) + x 24 + y 24
 ST_ROWS_L1_BYTES_PER_CELL = 45 * 4 + 24 + 24
 # DRAM read + write bytes of one roofline-kernel launch (one colour) of the default line, from an
 # ncu capture of the kernel as it stands (None whenever the kernel changes): mean of 7 warm launches
-ROOF_TRAFFIC_C2 = 450.85e6 + 5.91e6
+ROOF_TRAFFIC_C2 = 447.13e6 + 0.59e6
 
 # Stencil kernels of the default line (the metric's "stencil HBM GB/s"), each timed through the
 # C ABI call that launches it alone: algorithmic bytes per cell of the level it runs on (each
@@ -157,7 +158,7 @@ OTHER = {
     "c2c64": dict(workload=WORKLOAD.replace("FP16 Galerkin tables and local inverses", "complex64 Galerkin "
                                             "tables and local inverses"),
                   media=lambda: media(), kw=dict(coarse_fmt=1, coef_half=0), roof="coarse",
-                  kernel="k_dense_apply_v<float2> (MG-DD coarsest local products, complex64 inverses)"),
+                  kernel="k_dense_apply_vs<float2> (MG-DD coarsest local products with the scatter-add, complex64 inverses)"),
     # the default line in the plain FP64 GPU form: complex128 cycle, FP64 inverses, FP64 Krylov
     "c2f64": dict(workload=WORKLOAD.replace("complex64 V(1,1)", "complex128 V(1,1)").replace(
                       "FP16 Galerkin tables and local inverses", "FP64 Galerkin tables and local inverses").replace(
@@ -176,7 +177,7 @@ OTHER = {
                   "coarsest 64x64 grid split 4x4 (overlap 2), complex64 local inverses; double-float FGMRES(10)",
                   media=lambda: media(), kw=dict(levels=4, alpha=0.4, w=[0.75, 0.5, 0.25], cycle=2,
                                                  coarse_dd=(4, 4, 1), coarse_dd_overlap=2, coarse_fmt=1, coef_half=0),
-                  roof="coarse", kernel="k_dense_apply_v<float2> (MG-DD coarsest local products, complex64 inverses)"),
+                  roof="coarse", kernel="k_dense_apply_vs<float2> (MG-DD coarsest local products with the scatter-add, complex64 inverses)"),
     # the 64x64 homogeneous case: 3-level V-cycle, alpha 0.2, complex128
     "c1": dict(
         workload=("2D homogeneous 64x64, Vp 2, Vs 1, rho 1, 10 points per S-wavelength, 10-cell ABL, centred "
@@ -210,7 +211,7 @@ OTHER["c5"] = dict(
     media=lambda: [__import__("paper_1806_11277_gb300.synth", fromlist=["x"]).fwi_2d()[0]],
     nrhs=16, fwi=True,
     kw=dict(nrhs=16, coarse_dd=(4, 4, 1)), roof="coarse",
-    kernel="k_dense_apply_v<__half2> (MG-DD coarsest local products: one colour = 4 subdomain inverses x 16 sources)")
+    kernel="k_dense_apply_vs<__half2> (MG-DD coarsest local products with the scatter-add: one colour = 4 subdomain inverses x 16 sources)")
 
 # DD-MG-DD (Sec. 4, the paper's 3D method): the same top-level DD, 4-level V(1,1) cycles per subdomain
 # whose coarsest grids are themselves split 2x2x1 (overlap 2, FP16 local inverses), alpha 0.5
@@ -552,9 +553,11 @@ def run_gpu(args):
     roof_note = []
 
     def roofline_coarse():
-        # roofline of the dominant kernel of the MG-DD line, the coarsest local products
-        # (k_dense_apply_v): one launch = ehs_coarse_local_apply of one colour (every
-        # subdomain of that colour, every item); events on the solver's stream
+        # roofline of the dominant kernel of the MG-DD line, the coarsest local products: one
+        # launch = one colour (every subdomain of that colour, every item), events on the
+        # solver's stream.  The complex64 form times ehs_coarse_local_add, the launch the solve
+        # makes (k_dense_apply_vs: products and scatter-add, r read, x read and written per
+        # live row); the FP64 form ehs_coarse_local_apply (k_dense_apply, r read, z written).
         ns, nloc, sizes = S.coarse_dims()
         c64 = kw["prec"] == ehs.EHS_C64
         eb = {0: 16, 1: 8, 2: 4, 3: 4}[kw.get("coarse_fmt", 0)] if c64 else 16
@@ -565,10 +568,11 @@ def run_gpu(args):
         for q, n in enumerate(sizes):
             r[:, q, n:] = 0
         z = torch.zeros_like(r)
+        xc = torch.zeros(tuple(S.level_shape(kw["levels"] - 1)), dtype=r.dtype, device=dev)
         cols = {}
         for q, n in enumerate(sizes):
             col = (q % nx) % 2 + 2 * ((q // nx) % 2)
-            cols[col] = cols.get(col, 0) + nsets * n * n * eb + S.items * n * 2 * vb
+            cols[col] = cols.get(col, 0) + nsets * n * n * eb + S.items * n * (3 if c64 else 2) * vb
         # Every launch reads more than L2 holds (the colour's inverses, ~445 MB), so no
         # flush is needed between them: per sample the four colours run back to back
         # between one pair of events, queued behind a read-only 512 MiB pass (which
@@ -581,7 +585,10 @@ def run_gpu(args):
                 flush.sum()
                 e0.record(stream)
                 for col in cols:
-                    S.coarse_local_apply(col, r, z)
+                    if c64:
+                        S.coarse_local_add(col, r, xc)
+                    else:
+                        S.coarse_local_apply(col, r, z)
                 e1.record(stream)
             e1.synchronize()
             kt.append(e0.elapsed_time(e1) / 1e3)

@@ -202,6 +202,13 @@ ehs_status ehs_coarse_dims(const ehs_ctx* ctx, int* nsub, int* nloc, int* sizes)
    complex of prec; entries of other colours' subdomains and of padding rows are left unspecified.
    The complex64 form reads the inverses in opts.coarse_fmt storage. */
 ehs_status ehs_coarse_local_apply(ehs_ctx* ctx, int prec, int colour, const void* r_loc, void* z_loc);
+/* The same local products added into a coarsest vector, as the MG-DD sweep applies them (steps 2
+   and 3 of Algorithm DD on the coarsest grid): x[item] += R_s^T A_s^{-1} r_loc[item][s] for every
+   subdomain s of colour `colour`, R_s^T placing the box unknowns at their coarsest slots (boxes of
+   one colour are disjoint).  r_loc as for ehs_coarse_local_apply; x: device [items][(d+1) *
+   ncell_c] complex of prec, read and written.  In the complex64 form one launch does both.  MG-DD
+   contexts only (EHS_ERR_ARG otherwise, or for a colour without subdomains). */
+ehs_status ehs_coarse_local_add(ehs_ctx* ctx, int prec, int colour, const void* r_loc, void* x);
 
 /* z := one sweep of Algorithm DD on K z = r (global residual recomputed
  * before each colour, subdomain corrections by one multigrid cycle of the

@@ -566,8 +566,12 @@ void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typenam
   for (int col = 0; col < (int)D.col_subs.size(); ++col) {
     const int ncs = (int)D.col_subs[col].size();
     if (!ncs) continue;
-    launch_expand_items(act, nact, H.nrhs, D.nsub, D.d_col_subs[col], ncs, D.d_list[col], c->s); cnt(); post();
-    SelScope sel(D.d_list[col], nact * ncs);
+    const int* lst = D.d_list_all[col];   // every item active: the list built at setup
+    if (act) {
+      launch_expand_items(act, nact, H.nrhs, D.nsub, D.d_col_subs[col], ncs, D.d_list[col], c->s); cnt(); post();
+      lst = D.d_list[col];
+    }
+    SelScope sel(lst, nact * ncs);
     const int items_l = H.items * D.nsub;
     if (first) {   // x = 0: the residual is b
       launch_dd_gather<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, b, rs, c->s);
@@ -578,6 +582,13 @@ void coarse_dd_solve(ehs_ctx* c, Hier& H, const typename CT<T>::type* b, typenam
     }
     cnt(); post();
     first = false;
+    if constexpr (sizeof(T) == 4) {   // local products with the scatter-add folded in
+      if (L.invlp && launch_dense_apply_scatter(D.nloc, items_l, H.nrhs, D.nsub, D.d_sizes, L.invlp, H.coarse_fmt,
+                                                (const float2*)rs, D.d_map, NG, (float2*)x, c->s)) {
+        cnt(); post();
+        continue;
+      }
+    }
     coarse_gemv<T>(c, H, L, D.nloc, items_l, rs, zs);
     launch_dd_scatter<T>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, zs, x, c->s); cnt(); post();
   }
@@ -1450,6 +1461,43 @@ ehs_status ehs_coarse_local_apply(ehs_ctx* c, int prec, int colour, const void* 
       coarse_gemv<double>(c, H, L, D.nloc, H.items * D.nsub, (const double2*)r, (double2*)z);
     else
       coarse_gemv<float>(c, H, L, D.nloc, H.items * D.nsub, (const float2*)r, (float2*)z);
+    return EHS_OK;
+  });
+}
+
+ehs_status ehs_coarse_local_add(ehs_ctx* c, int prec, int colour, const void* r, void* x) {
+  if (!c) return EHS_ERR_ARG;
+  return guard(c, [&]() -> ehs_status {
+    if (c->H.coef_only) throw ArgError("a DD context builds no global multigrid hierarchy");
+    if (prec != EHS_C64 && prec != EHS_C128) throw ArgError("bad prec");
+    if (!r || !x) throw ArgError("null vector");
+    Hier& H = c->H;
+    const Level& L = H.lv.back();
+    CoarseDD& D = H.cdd;
+    if (!D.nsub) throw ArgError("the coarsest grid is not split (opts.coarse_dd)");
+    if (colour < 0 || colour >= (int)D.col_subs.size() || D.col_subs[colour].empty())
+      throw ArgError("no coarsest subdomain has this colour");
+    if (!D.loc[prec == EHS_C128 ? 0 : 1][1]) throw ArgError("the context was not set up for this precision");
+    const long long NG = (long long)(L.g.d + 1) * L.g.ncell;
+    const int ncs = (int)D.col_subs[colour].size();
+    const int items_l = H.items * D.nsub;
+    SelScope sel(D.d_list_all[colour], H.items * ncs);
+    if (prec == EHS_C64 && L.invlp &&
+        launch_dense_apply_scatter(D.nloc, items_l, H.nrhs, D.nsub, D.d_sizes, L.invlp, H.coarse_fmt,
+                                   (const float2*)r, D.d_map, NG, (float2*)x, c->s)) {
+      cnt(); post();
+      return EHS_OK;
+    }
+    if (prec == EHS_C128) {
+      double2* zs = (double2*)D.loc[0][1];
+      coarse_gemv<double>(c, H, L, D.nloc, items_l, (const double2*)r, zs);
+      launch_dd_scatter<double>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, zs, (double2*)x, c->s);
+    } else {
+      float2* zs = (float2*)D.loc[1][1];
+      coarse_gemv<float>(c, H, L, D.nloc, items_l, (const float2*)r, zs);
+      launch_dd_scatter<float>(D.nloc, items_l, D.nsub, H.nrhs, NG, D.d_map, zs, (float2*)x, c->s);
+    }
+    cnt(); post();
     return EHS_OK;
   });
 }

@@ -246,7 +246,43 @@ __global__ void __launch_bounds__(256) k_dense_apply_v(int N, int nrhs, int nsub
   dense_rows4<TI>(N, n, row0, inv + (long long)set * N * N, r + (long long)item * N, x + (long long)item * N);
 }
 
+// The MG-DD form that also scatters: sub-item = ((m * nsub) + s) * nrhs + r, its four results
+// added to the coarsest vector xg of item m * nrhs + r at the subdomain's unknowns map[s][row]
+// (subdomains of one colour are disjoint, so no two threads add to the same entry).
+template <typename TI>
+__global__ void __launch_bounds__(256) k_dense_apply_vs(int N, int nrhs, int nsub, const int* __restrict__ sizes,
+                                                        const TI* __restrict__ inv, const float2* __restrict__ r,
+                                                        const int* __restrict__ map, long long NG, float2* xg,
+                                                        const int* __restrict__ il) {
+  const int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  const int set = item / nrhs, sub = set % nsub;
+  const int n = sizes[sub];
+  if (row0 >= n) return;
+  const long long gi = (long long)(set / nsub) * nrhs + item % nrhs;
+  dense_rows4<TI, false, true>(N, n, row0, inv + (long long)set * N * N, r + (long long)item * N, nullptr,
+                               map + (long long)sub * N, xg + gi * NG);
+}
+
 }  // namespace
+
+bool launch_dense_apply_scatter(int N, int items, int nrhs, int nsub, const int* sizes, const void* inv, int fmt,
+                                const float2* r, const int* map, long long NG, float2* xg, cudaStream_t s) {
+  const int wpb = 8;
+  const int E = fmt >= 2 ? 4 : 2;
+  if (N % 4 != 0 || N % E != 0 || !sizes) return false;
+  const dim3 gv((N / 4 + wpb - 1) / wpb, sel_items(items));   // a warp per 4 rows
+  if (fmt == 2)
+    k_dense_apply_vs<__half2><<<gv, 32 * wpb, 0, s>>>(N, nrhs, nsub, sizes, (const __half2*)inv, r, map, NG, xg,
+                                                       g_sel.list);
+  else if (fmt == 3)
+    k_dense_apply_vs<__nv_bfloat162><<<gv, 32 * wpb, 0, s>>>(N, nrhs, nsub, sizes, (const __nv_bfloat162*)inv, r, map,
+                                                              NG, xg, g_sel.list);
+  else
+    k_dense_apply_vs<float2><<<gv, 32 * wpb, 0, s>>>(N, nrhs, nsub, sizes, (const float2*)inv, r, map, NG, xg,
+                                                      g_sel.list);
+  return true;
+}
 
 void launch_dense_assemble(const Grid& g, int nsets, const StencilLayout& L, const double2* tab,
                            double2* A, cudaStream_t s) {

@@ -197,16 +197,26 @@ __device__ __forceinline__ void prep(Tile<W, H>& S, const FP& P, int ox, int oy,
   }
 }
 
+// Complex arithmetic on the paired FP32 instructions (one instruction for the
+// real and imaginary parts; per part the rounding of the scalar operation).
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+// a * x + y, a real
+__device__ __forceinline__ float2 rfma2(float a, float2 x, float2 y) { return __ffma2_rn(bc2(a), x, y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a * b complex: (a.x b.x - a.y b.y, a.x b.y + a.y b.x)
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+  return __ffma2_rn(bc2(a.y), make_float2(-b.y, b.x), __fmul2_rn(bc2(a.x), b));
+}
+
 // Off-diagonal part of a face row and its pressure coupling:
 // b - (K_s row - dg xc) = b + (wpn xn+ + wmn xn- + wtp xt+ + wtm xt-) - (p_high - p_low) / h
 __device__ __forceinline__ float2 face_rhs(float2 b, float wpn, float2 xnp, float wmn, float2 xnm, float wtp,
                                            float2 xtp, float wtm, float2 xtm, float2 phi, float2 plo, float hinv) {
-  float2 s;
-  s.x = fmaf(wpn, xnp.x, b.x); s.y = fmaf(wpn, xnp.y, b.y);
-  s.x = fmaf(wmn, xnm.x, s.x); s.y = fmaf(wmn, xnm.y, s.y);
-  s.x = fmaf(wtp, xtp.x, s.x); s.y = fmaf(wtp, xtp.y, s.y);
-  s.x = fmaf(wtm, xtm.x, s.x); s.y = fmaf(wtm, xtm.y, s.y);
-  return make_float2(fmaf(-hinv, phi.x - plo.x, s.x), fmaf(-hinv, phi.y - plo.y, s.y));
+  float2 s = rfma2(wpn, xnp, b);
+  s = rfma2(wmn, xnm, s);
+  s = rfma2(wtp, xtp, s);
+  s = rfma2(wtm, xtm, s);
+  return rfma2(-hinv, sub2(phi, plo), s);
 }
 
 // Economic cell update (eq. RelaxationMatrix: diagonal of the displacement block,
@@ -250,30 +260,29 @@ __device__ __forceinline__ void cell_update(const Tile<W, H>& S, int sx, int sy,
   dinv[2] = S.fx[sy][sx + 1];
   dinv[3] = S.fy[sy + 1][sx];
   float2 t[4];
-  t[0] = csub(cmul(dinv[0], face_rhs(b0, mc, u01, ml, u0m, w01, u0up, w00, u0dn, pc, pl, hinv)), u00);
-  t[1] = csub(cmul(dinv[1], face_rhs(b1, mc, v01, md, v0m, w10, v0r, w00, v0l, pc, pd, hinv)), v00);
-  t[2] = csub(cmul(dinv[2], face_rhs(b2, mr, u02, mc, u00, w11, u1up, w10, u1dn, pr, pc, hinv)), u01);
-  t[3] = csub(cmul(dinv[3], face_rhs(b3, mup, v02, mc, v00, w11, v1r, w01, v1l, pu, pc, hinv)), v01);
+  t[0] = sub2(cmul2(dinv[0], face_rhs(b0, mc, u01, ml, u0m, w01, u0up, w00, u0dn, pc, pl, hinv)), u00);
+  t[1] = sub2(cmul2(dinv[1], face_rhs(b1, mc, v01, md, v0m, w10, v0r, w00, v0l, pc, pd, hinv)), v00);
+  t[2] = sub2(cmul2(dinv[2], face_rhs(b2, mr, u02, mc, u00, w11, u1up, w10, u1dn, pr, pc, hinv)), u01);
+  t[3] = sub2(cmul2(dinv[3], face_rhs(b3, mup, v02, mc, v00, w11, v1r, w01, v1l, pu, pc, hinv)), v01);
   // pressure row residual: b - (-kap p + (div u) / h)
   const float kap = S.kap[sy][sx];
-  const float2 sdiv = make_float2((u00.x - u01.x) + (v00.x - v01.x), (u00.y - u01.y) + (v00.y - v01.y));
-  float2 rp = make_float2(b4.x - fmaf(-kap, pc.x, hinv * sdiv.x), b4.y - fmaf(-kap, pc.y, hinv * sdiv.y));
+  const float2 sdiv = __fadd2_rn(sub2(u00, u01), sub2(v00, v01));
+  float2 rp = sub2(b4, rfma2(-kap, pc, __fmul2_rn(bc2(hinv), sdiv)));
   const float gk[4] = {hinv, hinv, -hinv, -hinv};
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     if (!ok[a]) continue;
-    rp.x = fmaf(-gk[a], t[a].x, rp.x);
-    rp.y = fmaf(-gk[a], t[a].y, rp.y);
+    rp = rfma2(-gk[a], t[a], rp);
   }
-  const float2 dp = cmul(rp, S.mm[sy][sx]);
-  o[4] = make_float2(fmaf(wp, dp.x, pc.x), fmaf(wp, dp.y, pc.y));
+  const float2 dp = cmul2(rp, S.mm[sy][sx]);
+  o[4] = rfma2(wp, dp, pc);
   const float2 xv[4] = {u00, v00, u01, v01};
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     if (!ok[a]) { o[a] = xv[a]; continue; }
-    const float2 q = cmul(dp, dinv[a]);
-    const float2 du = make_float2(fmaf(-gk[a], q.x, t[a].x), fmaf(-gk[a], q.y, t[a].y));
-    o[a] = make_float2(fmaf(wu, du.x, xv[a].x), fmaf(wu, du.y, xv[a].y));
+    const float2 q = cmul2(dp, dinv[a]);
+    const float2 du = rfma2(-gk[a], q, t[a]);
+    o[a] = rfma2(wu, du, xv[a]);
   }
 }
 
@@ -408,11 +417,11 @@ __global__ void __launch_bounds__(RR_T, 4) k_fine_resid_restrict_tile(Grid g, Gr
     const float2 pc = S.x[2][sy][sx], pl = S.x[2][sy][sx - 1], pd = S.x[2][sy - 1][sx];
     const float mc = S.mu[sy][sx], ml = S.mu[sy][sx - 1], md = S.mu[sy - 1][sx];
     const float w00 = S.vm[sy][sx], w10 = S.vm[sy][sx + 1], w01 = S.vm[sy + 1][sx];
-    if (gx >= 1) rr[q][0] = csub(face_rhs(b0, mc, u01, ml, u0m, w01, u0up, w00, u0dn, pc, pl, hinv), cmul(S.fx[sy][sx], u00));
-    if (gy >= 1) rr[q][1] = csub(face_rhs(b1, mc, v01, md, v0m, w10, v0r, w00, v0l, pc, pd, hinv), cmul(S.fy[sy][sx], v00));
+    if (gx >= 1) rr[q][0] = sub2(face_rhs(b0, mc, u01, ml, u0m, w01, u0up, w00, u0dn, pc, pl, hinv), cmul2(S.fx[sy][sx], u00));
+    if (gy >= 1) rr[q][1] = sub2(face_rhs(b1, mc, v01, md, v0m, w10, v0r, w00, v0l, pc, pd, hinv), cmul2(S.fy[sy][sx], v00));
     const float kap = S.kap[sy][sx];
-    const float2 sdiv = make_float2((u00.x - u01.x) + (v00.x - v01.x), (u00.y - u01.y) + (v00.y - v01.y));
-    rr[q][2] = make_float2(b2.x - fmaf(-kap, pc.x, hinv * sdiv.x), b2.y - fmaf(-kap, pc.y, hinv * sdiv.y));
+    const float2 sdiv = __fadd2_rn(sub2(u00, u01), sub2(v00, v01));
+    rr[q][2] = sub2(b2, rfma2(-kap, pc, __fmul2_rn(bc2(hinv), sdiv)));
   }
   __syncthreads();                                                 // the staged x is no longer read
   float2(*rs)[RR_RY][RR_RX] = reinterpret_cast<float2(*)[RR_RY][RR_RX]>(&S.x[0][0][0]);   // [3][RY][RX]

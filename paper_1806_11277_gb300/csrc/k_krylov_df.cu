@@ -277,21 +277,22 @@ __global__ void __launch_bounds__(KB, 3) k_update_scale_cast_df(long long n, int
                                                                 float4* __restrict__ out, float2* __restrict__ out32,
                                                                 int nblk, const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
-  __shared__ float4 hs[NV][2];
-  if (threadIdx.x < NV) load_hpairs(h + (long long)item * NV + threadIdx.x, hs[threadIdx.x]);
+  __shared__ float4 hs[NV];
+  if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
   __syncthreads();
   const float2 sc = inv[item];
   const dfr iv = {sc.x, sc.y};
   const float4* wv = w + (long long)item * n;
+  // scalar Dot2 steps here: this pass is bound by memory, and the paired form's extra
+  // shared-memory operands measured slower at large nv
   for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
-    dacc2 sv = dacc2_zero();
+    dcacc sv = dcacc_zero();
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      const float4 a = hs[i][0], b = hs[i][1];
-      dacc2_mfma(sv, dfc2_of(dfc_ld(V + ((long long)i * items + item) * n + e)), make_float2(a.x, a.y),
-                 make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w));
+      const float4 hv = hs[i];   // the storage order of dfc_st
+      dcacc_fma(sv, dfc_ld(V + ((long long)i * items + item) * n + e), dfc{{hv.x, hv.z}, {hv.y, hv.w}});
     }
-    const dfc v = dfc_scale(dfc_sub(dfc_ld(wv + e), dacc2_val(sv)), iv);
+    const dfc v = dfc_scale(dfc_sub(dfc_ld(wv + e), dcacc_val(sv)), iv);
     dfc_st(out + (long long)item * n + e, v);
     out32[(long long)item * n + e] = dfc_to_f2(v);
   }

@@ -142,6 +142,11 @@ void launch_dense_assemble_sub(const Grid& g, int nsets, int nsub, int nloc, con
 // x = inv r with a low-precision inverse, FP32 accumulation; fmt 1 complex64, 2 FP16 pairs,
 // 3 BF16 pairs; matrix of item b: inv + (b / nrhs) N^2 entries.  sizes (device, optional):
 // live size of matrix set s is sizes[s % nsub], the rest identity padding (skipped)
+// MG-DD local products of one colour with the scatter-add folded in: x[item][map[sub][row]] +=
+// (A_sub^{-1} r_sub)[row] for every sub-item of the selection (complex64 r, x; inverses in format fmt
+// as launch_dense_apply_lp); false (nothing launched) where the 4-row form does not apply
+bool launch_dense_apply_scatter(int N, int items, int nrhs, int nsub, const int* sizes, const void* inv, int fmt,
+                                const float2* r, const int* map, long long NG, float2* xg, cudaStream_t s);
 void launch_dense_apply_lp(int N, int items, int nrhs, int nsub, const int* sizes, const void* inv, int fmt,
                            const float2* r, float2* x, cudaStream_t s);
 // The MG-DD coarsest solve of the 2D complex64 cycle in one persistent launch (every colour's

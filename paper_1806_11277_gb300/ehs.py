@@ -51,7 +51,7 @@ EXPORTS = ["ehs_default_opts", "ehs_create", "ehs_destroy", "ehs_op_apply", "ehs
            "ehs_vcycle", "ehs_dd_precond", "ehs_fgmres_solve", "ehs_adjoint_solve", "ehs_items",
            "ehs_level_len", "ehs_level_dims", "ehs_sync", "ehs_kernel_launches", "ehs_last_error",
            "ehs_fine_smooth_noalloc", "ehs_gradient", "ehs_coarse_solve", "ehs_coarse_dims",
-           "ehs_coarse_local_apply", "ehs_residual_restrict", "ehs_prolong_add"]
+           "ehs_coarse_local_apply", "ehs_coarse_local_add", "ehs_residual_restrict", "ehs_prolong_add"]
 
 _lib = None
 
@@ -90,6 +90,7 @@ def load(path=LIB_PATH):
     lib.ehs_coarse_solve.argtypes = [vp, i, vp, vp]
     lib.ehs_coarse_dims.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
     lib.ehs_coarse_local_apply.argtypes = [vp, i, i, vp, vp]
+    lib.ehs_coarse_local_add.argtypes = [vp, i, i, vp, vp]
     lib.ehs_residual_restrict.argtypes = [vp, i, i, vp, vp, vp]
     lib.ehs_prolong_add.argtypes = [vp, i, i, vp, vp]
     for name in EXPORTS:
@@ -230,6 +231,10 @@ class Solver:
     def coarse_local_apply(self, colour, r_loc, z_loc, prec=None):
         prec = _prec_of(z_loc) if prec is None else prec
         self._check(self.lib.ehs_coarse_local_apply(self.ctx, prec, colour, _ptr(r_loc), _ptr(z_loc)))
+
+    def coarse_local_add(self, colour, r_loc, x, prec=None):
+        prec = _prec_of(x) if prec is None else prec
+        self._check(self.lib.ehs_coarse_local_add(self.ctx, prec, colour, _ptr(r_loc), _ptr(x)))
 
     def dd_precond(self, r, z, prec=EHS_C64):
         self._check(self.lib.ehs_dd_precond(self.ctx, prec, _ptr(r), _ptr(z)))

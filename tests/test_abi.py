@@ -164,6 +164,7 @@ def test_null_context_is_an_argument_error_everywhere(lib_path):
     assert lib.ehs_vcycle(None, 1, buf, buf) == 1
     assert lib.ehs_coarse_solve(None, 1, buf, buf) == 1
     assert lib.ehs_coarse_local_apply(None, 1, 0, buf, buf) == 1
+    assert lib.ehs_coarse_local_add(None, 1, 0, buf, buf) == 1
     assert lib.ehs_residual_restrict(None, 0, 1, buf, buf, buf) == 1
     assert lib.ehs_prolong_add(None, 0, 1, buf, buf) == 1
     assert lib.ehs_dd_precond(None, 1, buf, buf) == 1

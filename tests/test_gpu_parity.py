@@ -658,9 +658,10 @@ def test_mgdd_rejects_bad_split():
                                            ((2, 2, 1), 2, 3e-3)])
 def test_coarse_solve_and_local_apply(split, fmt, tol):
     """ehs_coarse_solve against the oracle's coarsest solve (exact LU or the
-    CoarseDD sweep), and every colour's ehs_coarse_local_apply against the
+    CoarseDD sweep), every colour's ehs_coarse_local_apply against the
     oracle's dense solve of the subdomain matrix (the coarsest operator
-    restricted to the box unknowns)."""
+    restricted to the box unknowns), and ehs_coarse_local_add (the same
+    products added into a random coarsest vector at the boxes' unknowns)."""
     ehs = _ehs()
     meds = _media_2d(64, 2)
     cdd = split[0] * split[1] > 1
@@ -680,11 +681,16 @@ def test_coarse_solve_and_local_apply(split, fmt, tol):
     for s_, n in enumerate(sizes):
         rl[:, s_, n:] = 0
     rld = torch.from_numpy(rl).to("cuda", dt)
-    zs = {}
+    zs, xs = {}, {}
+    x0 = _rand_slots(cshape, S.items, 82)
     for col in (range(4) if cdd else [0]):
         zd = torch.zeros_like(rld)
         S.coarse_local_apply(col, rld, zd, prec=ehs.EHS_C128 if dt == torch.complex128 else ehs.EHS_C64)
         zs[col] = zd.cpu().numpy()
+        if cdd:   # the same products added into a coarsest vector at the boxes' unknowns
+            xa = torch.from_numpy(x0).to("cuda", dt)
+            S.coarse_local_add(col, rld, xa, prec=ehs.EHS_C128 if dt == torch.complex128 else ehs.EHS_C64)
+            xs[col] = xa.cpu().numpy()
     for it, med in enumerate(meds):
         H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 3, w=[0.75, 0.5],
                          coarse_dd=((split[0], split[1]), 2) if cdd else None)
@@ -694,6 +700,7 @@ def test_coarse_solve_and_local_apply(split, fmt, tol):
         if not cdd:
             continue
         nx = split[0]
+        xadd = {col: op.slots_to_dofs(x0[it].astype(np.complex128), cshape) for col in xs}
         for p_, (col, idx, _) in enumerate(H.cdd.subs):
             ix, iy = divmod(p_, split[1])          # oracle order: y index fastest
             s_ = iy * nx + ix                      # library order: x index fastest
@@ -701,6 +708,10 @@ def test_coarse_solve_and_local_apply(split, fmt, tol):
             ze = np.linalg.solve(Kc[idx][:, idx].toarray(), rl[it, s_, :idx.size])
             got = zs[col][it, s_, :idx.size]
             assert _err(got, ze) <= tol, (it, s_, _err(got, ze))
+            xadd[col][idx] += ze
+        for col, xe in xadd.items():
+            got = op.slots_to_dofs(xs[col][it], cshape)
+            assert _err(got, xe) <= tol, (it, col, _err(got, xe))
     S.close()
 
 
