@@ -89,6 +89,7 @@ struct Hier {
   CoarseDD cdd;
   bool coef_only = false;      // only the fine coefficients were built (global problem of a DD context)
   bool fused0 = false;         // 2D complex64 cycle: fused fine-level sweep and residual + restriction
+  SweepTab stab;               // setup-time tables of the fused sweep (fused0)
   bool persist = false;        // complex64 MG-DD coarsest solve in one persistent launch
   unsigned* pbar = nullptr;    // its grid-barrier state (2 words)
   Coef4<double>* cf64 = nullptr;
@@ -400,6 +401,14 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
   // their tiles; EHS_FINE_UNFUSED=1 selects the per-colour kernels instead (tests compare both)
   const char* uf = getenv("EHS_FINE_UNFUSED");
   H.fused0 = (precs & 2) && d == 2 && !H.full && fine_tiles_fit(H.g0) && !(uf && uf[0] == '1');
+  if (H.fused0) {
+    const size_t nc = (size_t)H.nsets * H.g0.ncell;
+    H.stab.dvx = dalloc<float2>(c, nc);
+    H.stab.dvy = dalloc<float2>(c, nc);
+    H.stab.sinv = dalloc<float2>(c, nc);
+    H.stab.vm = dalloc<float>(c, (size_t)H.nsets * sweep_table_vertices(H.g0));
+    launch_sweep_tables(H.g0, H.nsets, H.cf32, H.h, H.alpha, H.stab, c->s); cnt(2); post();
+  }
   // opts.coarse_persist: the MG-DD coarsest solve of the 2D complex64 cycle as one persistent launch
   H.persist = (precs & 2) && mgdd && c->opt.coarse_persist && coarse_persist_supported(C.g, H.coarse_fmt);
   if (H.persist) H.pbar = dalloc<unsigned>(c, 2);
@@ -614,7 +623,7 @@ void cycle_fine_fused(ehs_ctx* c, Hier& H, const float2* b, float2* x, bool gues
   const float2* cur = guess ? x : nullptr;            // nullptr: the zero iterate
   float2* out = guess ? t : (((H.nu1 + H.nu2) & 1) ? x : t);
   auto sweep = [&](const float2* ec) {
-    launch_fine_sweep_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.h, H.alpha, wu, wp, b, cur, ec, out, c->s);
+    launch_fine_sweep_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.stab, H.h, H.alpha, wu, wp, b, cur, ec, out, c->s);
     cnt(); post();
     cur = out;
     out = out == t ? x : t;
@@ -1330,8 +1339,8 @@ ehs_status ehs_smooth(ehs_ctx* c, int level, int nsweeps, int prec, const void* 
       const float2* cur = (const float2*)x;
       for (int s = 0; s < nsweeps; ++s) {
         float2* out = cur == (const float2*)x ? t : (float2*)x;
-        launch_fine_sweep_tile(L.g, H.lv[1].g, H.items, H.nrhs, H.cf32, H.h, H.alpha, wu, wp, (const float2*)b,
-                               cur, nullptr, out, c->s);
+        launch_fine_sweep_tile(L.g, H.lv[1].g, H.items, H.nrhs, H.cf32, H.stab, H.h, H.alpha, wu, wp,
+                               (const float2*)b, cur, nullptr, out, c->s);
         cnt(); post();
         cur = out;
       }

@@ -36,8 +36,8 @@
 namespace ehs {
 namespace {
 
-constexpr int SW_X = 32, SW_Y = 16, SW_H = 3;                 // sweep tile and staged halo
-constexpr int SWS_X = SW_X + 2 * SW_H, SWS_Y = SW_Y + 2 * SW_H;
+constexpr int SW_X = 32, SW_Y = 16, SW_H = 2;                 // sweep tile, staged halo below it
+constexpr int SWS_X = SW_X + 2 * SW_H + 1, SWS_Y = SW_Y + 2 * SW_H + 1;   // and one cell more above
 constexpr int SW_RX = SW_X + 2, SW_RY = SW_Y + 2;             // red region: tile + one-cell ring
 constexpr int SW_NRED = SW_RX * SW_RY / 2;                    // 306 red cells
 constexpr int SW_TB = SW_X * SW_Y / 2;                        // 256 black cells: one per thread
@@ -81,6 +81,10 @@ struct Tile {
 __device__ __forceinline__ void cpa8(void* dst, const void* src, int nbytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cpa_wait() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -148,52 +152,141 @@ __device__ __forceinline__ void stage(Tile<W, H>& S, const float4* __restrict__ 
   }
 }
 
+// The coefficient terms of the rows, shared by prep() and the setup-time tables:
+// the mean of mu / h^2 over the four cells around a vertex, and the diagonal of a
+// face row from the mu / h^2 of its two cells, the vertex means at its two ends and
+// the two cells' (omega^2 rho, omega rho gamma).
+__device__ __forceinline__ float vertex_mean(float m00, float m01, float m10, float m11) {
+  return 0.25f * ((m00 + m01) + m10 + m11);
+}
+__device__ __forceinline__ float2 face_diag(float mu0, float mu1, float vhi, float vlo, float2 m0, float2 m1,
+                                            float alpha) {
+  const float wsum = (mu0 + mu1) + vhi + vlo;
+  const float rf = 0.5f * (m0.x + m1.x), gf = 0.5f * (m0.y + m1.y);
+  return make_float2(wsum - rf, gf + alpha * rf);
+}
+
 // Coefficient terms of the rows of the cells in [RX0, RX1] x [RY0, RY1] (staged
-// coordinates) and of their faces: vertex means and face diagonals, or with INV
-// the inverse diagonals and the cells' inverse Schur complements (after stage()
-// and a barrier; ends with a barrier).  ox, oy: global coordinates of staged (0, 0).
-template <int W, int H, int NT, int RX0, int RX1, int RY0, int RY1, bool INV>
-__device__ __forceinline__ void prep(Tile<W, H>& S, const FP& P, int ox, int oy, int nx, int ny) {
+// coordinates) and of their faces: vertex means and face diagonals (after stage()
+// and a barrier; ends with a barrier).
+template <int W, int H, int NT, int RX0, int RX1, int RY0, int RY1>
+__device__ __forceinline__ void prep(Tile<W, H>& S, const FP& P) {
   static_assert(RX0 >= 1 && RY0 >= 1 && RX1 + 1 <= W - 1 && RY1 + 1 <= H - 1, "prep region inside the tile");
   constexpr int VX = RX1 - RX0 + 2, VY = RY1 - RY0 + 2;          // vertices and faces: one wider
   for (int idx = threadIdx.x; idx < VX * VY; idx += NT) {
     const int lx = RX0 + idx % VX, ly = RY0 + idx / VX;
-    S.vm[ly][lx] = 0.25f * ((S.mu[ly][lx] + S.mu[ly][lx - 1]) + S.mu[ly - 1][lx] + S.mu[ly - 1][lx - 1]);
+    S.vm[ly][lx] = vertex_mean(S.mu[ly][lx], S.mu[ly][lx - 1], S.mu[ly - 1][lx], S.mu[ly - 1][lx - 1]);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < VX * VY; idx += NT) {
     const int lx = RX0 + idx % VX, ly = RY0 + idx / VX;
     if (ly <= RY1) {     // u_0 face between cells (lx-1, ly) and (lx, ly)
-      const float wsum = (S.mu[ly][lx] + S.mu[ly][lx - 1]) + S.vm[ly + 1][lx] + S.vm[ly][lx];
-      const float2 m0 = S.mm[ly][lx], m1 = S.mm[ly][lx - 1];
-      const float rf = 0.5f * (m0.x + m1.x), gf = 0.5f * (m0.y + m1.y);
-      const float2 d = make_float2(wsum - rf, gf + P.alpha * rf);
-      S.fx[ly][lx] = INV ? cinv(d) : d;
+      const float2 d = face_diag(S.mu[ly][lx], S.mu[ly][lx - 1], S.vm[ly + 1][lx], S.vm[ly][lx], S.mm[ly][lx],
+                                 S.mm[ly][lx - 1], P.alpha);
+      S.fx[ly][lx] = d;
     }
     if (lx <= RX1) {     // u_1 face between cells (lx, ly-1) and (lx, ly)
-      const float wsum = (S.mu[ly][lx] + S.mu[ly - 1][lx]) + S.vm[ly][lx + 1] + S.vm[ly][lx];
-      const float2 m0 = S.mm[ly][lx], m1 = S.mm[ly - 1][lx];
-      const float rf = 0.5f * (m0.x + m1.x), gf = 0.5f * (m0.y + m1.y);
-      const float2 d = make_float2(wsum - rf, gf + P.alpha * rf);
-      S.fy[ly][lx] = INV ? cinv(d) : d;
+      const float2 d = face_diag(S.mu[ly][lx], S.mu[ly - 1][lx], S.vm[ly][lx + 1], S.vm[ly][lx], S.mm[ly][lx],
+                                 S.mm[ly - 1][lx], P.alpha);
+      S.fy[ly][lx] = d;
     }
   }
   __syncthreads();
-  if constexpr (INV) {   // Schur complements of the relaxed cells (mm is no longer read)
-    Tile<W, H>& T = S;
-    constexpr int CX = RX1 - RX0 + 1, CY = RY1 - RY0 + 1;
-    for (int idx = threadIdx.x; idx < CX * CY; idx += NT) {
-      const int lx = RX0 + idx % CX, ly = RY0 + idx / CX;
-      const int gx = ox + lx, gy = oy + ly;
-      float2 sd = make_float2(0.f, 0.f);                          // sum of the faces' 1/dg
-      if (gx >= 1) sd = cadd(sd, T.fx[ly][lx]);
-      if (gx + 1 < nx) sd = cadd(sd, T.fx[ly][lx + 1]);
-      if (gy >= 1) sd = cadd(sd, T.fy[ly][lx]);
-      if (gy + 1 < ny) sd = cadd(sd, T.fy[ly + 1][lx]);
-      const float2 sch = make_float2(-T.kap[ly][lx] - P.h2inv * sd.x, -P.h2inv * sd.y);
-      T.mm[ly][lx] = cinv(sch);
+}
+
+// Setup-time tables of the sweep, per medium: the inverse diagonals of each cell's
+// low u_0 and u_1 face rows (dvx, dvy, [ncell]), the inverse pressure Schur
+// complement of each cell's block (sinv, [ncell]) and the vertex means of mu / h^2
+// (vm, [(nx + 1) (ny + 1)], vertex (vx, vy) the low corner of cell (vx, vy)).  The
+// same formulas and clamped coefficients as prep(), formed once instead of in every
+// sweep; entries on Dirichlet faces are formed but never used.
+__device__ __forceinline__ float mu_cl(const float4* cfs, int gx, int gy, int nx, int ny, float h2inv) {
+  return __ldg(cfs + min(max(gy, 0), ny - 1) * nx + min(max(gx, 0), nx - 1)).x * h2inv;
+}
+__device__ __forceinline__ float2 mm_cl(const float4* cfs, int gx, int gy, int nx, int ny) {
+  const float4 c = __ldg(cfs + min(max(gy, 0), ny - 1) * nx + min(max(gx, 0), nx - 1));
+  return make_float2(c.z, c.w);
+}
+__device__ __forceinline__ float vm_cl(const float4* cfs, int vx, int vy, int nx, int ny, float h2inv) {
+  return vertex_mean(mu_cl(cfs, vx, vy, nx, ny, h2inv), mu_cl(cfs, vx - 1, vy, nx, ny, h2inv),
+                     mu_cl(cfs, vx, vy - 1, nx, ny, h2inv), mu_cl(cfs, vx - 1, vy - 1, nx, ny, h2inv));
+}
+__global__ void k_sweep_tables_faces(Grid g, const float4* __restrict__ cf, FP P, float2* __restrict__ dvx,
+                                     float2* __restrict__ dvy, float* __restrict__ vm) {
+  const int nx = g.n[0], ny = g.n[1];
+  const int nv = (nx + 1) * (ny + 1);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv) return;
+  const int set = blockIdx.y;
+  const float4* cfs = cf + (long long)set * g.ncell;
+  const int vx = t % (nx + 1), vy = t / (nx + 1);
+  const float h2 = P.h2inv;
+  vm[(long long)set * nv + t] = vm_cl(cfs, vx, vy, nx, ny, h2);
+  if (vx >= nx || vy >= ny) return;
+  const long long c = (long long)set * g.ncell + vy * nx + vx;
+  const float mc = mu_cl(cfs, vx, vy, nx, ny, h2), v00 = vm_cl(cfs, vx, vy, nx, ny, h2);
+  const float2 m0 = mm_cl(cfs, vx, vy, nx, ny);
+  dvx[c] = cinv(face_diag(mc, mu_cl(cfs, vx - 1, vy, nx, ny, h2), vm_cl(cfs, vx, vy + 1, nx, ny, h2), v00, m0,
+                          mm_cl(cfs, vx - 1, vy, nx, ny), P.alpha));
+  dvy[c] = cinv(face_diag(mc, mu_cl(cfs, vx, vy - 1, nx, ny, h2), vm_cl(cfs, vx + 1, vy, nx, ny, h2), v00, m0,
+                          mm_cl(cfs, vx, vy - 1, nx, ny), P.alpha));
+}
+__global__ void k_sweep_tables_schur(Grid g, const float4* __restrict__ cf, FP P, const float2* __restrict__ dvx,
+                                     const float2* __restrict__ dvy, float2* __restrict__ sinv) {
+  const int nx = g.n[0], ny = g.n[1];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.ncell) return;
+  const long long c = (long long)blockIdx.y * g.ncell + t;
+  const int gx = t % nx, gy = t / nx;
+  float2 sd = make_float2(0.f, 0.f);                               // sum of the faces' 1/dg
+  if (gx >= 1) sd = cadd(sd, dvx[c]);
+  if (gx + 1 < nx) sd = cadd(sd, dvx[c + 1]);
+  if (gy >= 1) sd = cadd(sd, dvy[c]);
+  if (gy + 1 < ny) sd = cadd(sd, dvy[c + nx]);
+  const float kap = __ldg(cf + c).y;
+  sinv[c] = cinv(make_float2(-kap - P.h2inv * sd.x, -P.h2inv * sd.y));
+}
+
+// Stage x as stage() does, with mu / h^2 and 1/(lambda+mu) of the cells and the
+// setup-time tables (fx, fy: inverse face diagonals, mm: inverse Schur complement,
+// vm: vertex means) in place of the coefficients prep() would combine.
+template <int W, int H, int NT>
+__device__ __forceinline__ void stage_tab(Tile<W, H>& S, const float4* __restrict__ cfs, const float2* __restrict__ tx,
+                                          const float2* __restrict__ ty, const float2* __restrict__ ts,
+                                          const float* __restrict__ tv, const float2* __restrict__ xv,
+                                          const float2* __restrict__ e, const Grid& gc, int N, int nx, int ny,
+                                          int x0, int y0, float h2inv) {
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < W * H; idx += NT) {
+    const int lx = idx % W, ly = idx / W;
+    const int gx = x0 + lx, gy = y0 + ly;
+    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    const int cx = min(max(gx, 0), nx - 1), cy = min(max(gy, 0), ny - 1);
+    const int gcl = cy * nx + cx;                                  // a valid address in every case
+    const bool v0 = in && gx >= 1, v1 = in && gy >= 1;            // u_k slot 0 is a boundary face
+    if (!e) {
+      if (xv) {
+        cpa8(&S.x[0][ly][lx], xv + gcl, v0 ? 8 : 0);
+        cpa8(&S.x[1][ly][lx], xv + N + gcl, v1 ? 8 : 0);
+        cpa8(&S.x[2][ly][lx], xv + 2 * N + gcl, in ? 8 : 0);
+      } else {
+        const float2 z = make_float2(0.f, 0.f);
+        S.x[0][ly][lx] = z; S.x[1][ly][lx] = z; S.x[2][ly][lx] = z;
+      }
+    } else {
+      float2 u0 = make_float2(0.f, 0.f), u1 = u0, pv = u0;
+      if (v0) u0 = cadd(xv ? __ldg(xv + gcl) : u0, prolong_at(e, 0, gx, gy, gc.n[0], gc.n[1]));
+      if (v1) u1 = cadd(xv ? __ldg(xv + N + gcl) : u1, prolong_at(e, 1, gx, gy, gc.n[0], gc.n[1]));
+      if (in) pv = cadd(xv ? __ldg(xv + 2 * N + gcl) : pv, prolong_at(e, 2, gx, gy, gc.n[0], gc.n[1]));
+      S.x[0][ly][lx] = u0; S.x[1][ly][lx] = u1; S.x[2][ly][lx] = pv;
     }
-    __syncthreads();
+    cpa8(&S.fx[ly][lx], tx + gcl, 8);
+    cpa8(&S.fy[ly][lx], ty + gcl, 8);
+    cpa8(&S.mm[ly][lx], ts + gcl, 8);
+    cpa4(&S.vm[ly][lx], tv + min(max(gy, 0), ny) * (nx + 1) + min(max(gx, 0), nx));
+    const float2 mk = __ldg(reinterpret_cast<const float2*>(cfs + gcl));   // mu, 1/(lambda+mu)
+    S.mu[ly][lx] = mk.x * h2inv;
+    S.kap[ly][lx] = mk.y;
   }
 }
 
@@ -290,6 +383,10 @@ typedef Tile<SWS_X, SWS_Y> SweepTile;
 typedef Tile<RRS_X, RRS_Y> ResTile;
 
 __global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, int nrhs, const float4* __restrict__ cf,
+                                                             const float2* __restrict__ tdx,
+                                                             const float2* __restrict__ tdy,
+                                                             const float2* __restrict__ tsi,
+                                                             const float* __restrict__ tvm,
                                                              FP P, float wu, float wp,
                                                              const float2* __restrict__ b,
                                                              const float2* __restrict__ xi,
@@ -306,11 +403,12 @@ __global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, in
   const float2* e = ec ? ec + (long long)item * 3 * gc.ncell : nullptr;
   const int X0 = blockIdx.x * SW_X, Y0 = blockIdx.y * SW_Y;
   const int x0 = X0 - SW_H, y0 = Y0 - SW_H;
-  stage<SWS_X, SWS_Y, SW_T>(S, cfs, x, e, gc, N, nx, ny, x0, y0, P.h2inv);
+  const int set = item / nrhs;
+  const long long nvt = (long long)(nx + 1) * (ny + 1);
+  stage_tab<SWS_X, SWS_Y, SW_T>(S, cfs, tdx + (long long)set * N, tdy + (long long)set * N, tsi + (long long)set * N,
+                                tvm + set * nvt, x, e, gc, N, nx, ny, x0, y0, P.h2inv);
   cpa_wait();
   __syncthreads();
-  // the red region (tile + one-cell ring) spans staged [SW_H - 1, SW_H + SW_X] x [SW_H - 1, SW_H + SW_Y]
-  prep<SWS_X, SWS_Y, SW_T, SW_H - 1, SW_H + SW_X, SW_H - 1, SW_H + SW_Y, true>(S, P, x0, y0, nx, ny);
   const float2* bb = b + vo;
   float2* xout = xo + vo;
   // ---- red cells of the tile and its one-cell ring, all from the staged iterate
@@ -390,7 +488,7 @@ __global__ void __launch_bounds__(RR_T, 4) k_fine_resid_restrict_tile(Grid g, Gr
   cpa_wait();
   __syncthreads();
   // the residual region (tile + one-cell ring) spans staged [RR_H - 1, RR_H + RR_X] x [RR_H - 1, RR_H + RR_Y]
-  prep<RRS_X, RRS_Y, RR_T, RR_H - 1, RR_H + RR_X, RR_H - 1, RR_H + RR_Y, false>(S, P, x0, y0, nx, ny);
+  prep<RRS_X, RRS_Y, RR_T, RR_H - 1, RR_H + RR_X, RR_H - 1, RR_H + RR_Y>(S, P);
   const float2* bb = b + vo;
   const float hinv = P.hinv;
   // fine residual b - K_s x on the tile and its one-cell ring (zero outside the grid and on
@@ -489,26 +587,40 @@ bool fine_tiles_fit(const Grid& g) {
   return g.d == 2 && g.n[0] % SW_X == 0 && g.n[1] % SW_Y == 0 && g.n[0] % RR_X == 0 && g.n[1] % RR_Y == 0;
 }
 
-void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf, double h,
-                            double alpha, float wu, float wp, const float2* b, const float2* xi,
-                            const float2* ec, float2* xo, cudaStream_t s) {
+static FP make_fp(double h, double alpha) {
   FP P;
   P.h2inv = (float)(1.0 / (h * h));
   P.hinv = (float)(1.0 / h);
   P.alpha = (float)alpha;
+  return P;
+}
+
+long long sweep_table_vertices(const Grid& g) { return (long long)(g.n[0] + 1) * (g.n[1] + 1); }
+
+void launch_sweep_tables(const Grid& g, int nsets, const Coef4<float>* cf, double h, double alpha,
+                         const SweepTab& T, cudaStream_t s) {
+  const FP P = make_fp(h, alpha);
+  const float4* c4 = reinterpret_cast<const float4*>(cf);
+  const long long nv = sweep_table_vertices(g);
+  k_sweep_tables_faces<<<dim3((unsigned)((nv + 255) / 256), nsets), 256, 0, s>>>(g, c4, P, T.dvx, T.dvy, T.vm);
+  k_sweep_tables_schur<<<dim3((unsigned)((g.ncell + 255) / 256), nsets), 256, 0, s>>>(g, c4, P, T.dvx, T.dvy,
+                                                                                       T.sinv);
+}
+
+void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
+                            const SweepTab& T, double h, double alpha, float wu, float wp, const float2* b,
+                            const float2* xi, const float2* ec, float2* xo, cudaStream_t s) {
+  const FP P = make_fp(h, alpha);
   smem_attr(k_fine_sweep_tile, sizeof(SweepTile));
   const dim3 gr(g.n[0] / SW_X, g.n[1] / SW_Y, sel_items(items));
-  k_fine_sweep_tile<<<gr, SW_T, sizeof(SweepTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf), P, wu, wp,
-                                                         b, xi, ec, xo, g_sel.list);
+  k_fine_sweep_tile<<<gr, SW_T, sizeof(SweepTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf), T.dvx,
+                                                         T.dvy, T.sinv, T.vm, P, wu, wp, b, xi, ec, xo, g_sel.list);
 }
 
 void launch_fine_resid_restrict_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
                                      double h, double alpha, const float2* x, const float2* b, float2* rc,
                                      cudaStream_t s) {
-  FP P;
-  P.h2inv = (float)(1.0 / (h * h));
-  P.hinv = (float)(1.0 / h);
-  P.alpha = (float)alpha;
+  const FP P = make_fp(h, alpha);
   smem_attr(k_fine_resid_restrict_tile, sizeof(ResTile));
   const dim3 gr(g.n[0] / RR_X, g.n[1] / RR_Y, sel_items(items));
   k_fine_resid_restrict_tile<<<gr, RR_T, sizeof(ResTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf), P,

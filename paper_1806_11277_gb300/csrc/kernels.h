@@ -55,9 +55,21 @@ void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
 // xo = sweep(x_in), x_in = (xi or 0) + (P ec if ec), xo != xi; ec: coarse
 // vector of grid gc (ignored when null).  And r_c = P^T (b - K_s x) in one pass.
 bool fine_tiles_fit(const Grid& g);
-void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf, double h,
-                            double alpha, float wu, float wp, const float2* b, const float2* xi,
-                            const float2* ec, float2* xo, cudaStream_t s);
+// Setup-time tables of the fused sweep, per medium (k_fine_fused.cu): inverse diagonals of each
+// cell's low u_0 / u_1 face rows and the inverse pressure Schur complement of its block
+// ([nsets][ncell] each), vertex means of mu / h^2 ([nsets][sweep_table_vertices(g)])
+struct SweepTab {
+  float2* dvx = nullptr;
+  float2* dvy = nullptr;
+  float2* sinv = nullptr;
+  float* vm = nullptr;
+};
+long long sweep_table_vertices(const Grid& g);
+void launch_sweep_tables(const Grid& g, int nsets, const Coef4<float>* cf, double h, double alpha,
+                         const SweepTab& T, cudaStream_t s);
+void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
+                            const SweepTab& T, double h, double alpha, float wu, float wp, const float2* b,
+                            const float2* xi, const float2* ec, float2* xo, cudaStream_t s);
 void launch_fine_resid_restrict_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
                                      double h, double alpha, const float2* x, const float2* b, float2* rc,
                                      cudaStream_t s);
