@@ -86,13 +86,14 @@ ROOF_TRAFFIC_C2 = 447.13e6 + 0.59e6
 #  fine sweep: one launch of the fused red-black sweep, x 24 + b 24 + x' 24 + mu and 1/(lambda+mu) 8
 #    + the setup-time tables 28 (inverse diagonals of the two low faces 16, inverse Schur complement
 #    8, vertex mean 4)
-#  fine residual + restriction: one fused launch, x 24 + b 24 + coefficients 16 + coarse r 6
+#  fine residual + restriction: one fused launch, x 24 + b 24 + mu and 1/(lambda+mu) 8 + the
+#    setup-time tables 20 (face diagonals 16, vertex mean 4) + coarse r 6
 #  level-1 rows: the Galerkin residual pass, the FP16 table in half storage (45 of the 87
 #    coefficients per cell kept, K_c = K_c^T) x 4 B + x 24 + y 24
 #  level-1 prolongation: x += P e, x 24 read + 24 written + e 6 (per level-1 cell)
 STENCIL = (
     ("k_fine_sweep_tile (fine level, whole red-black sweep)", "sweep", 0, 108),
-    ("k_fine_resid_restrict_tile (fine residual + restriction)", "resid_restrict", 0, 70),
+    ("k_fine_resid_restrict_tile (fine residual + restriction)", "resid_restrict", 0, 82),
     ("k_st_rows / k_st_rows2 <float,__half2,2,1,true> (Galerkin level 1, all rows, FP16 half table; the "
      "setup autotuner's launch shape)", "rows", 1, 45 * 4 + 48),
     ("k_prolong_add<float,2> (level 2 -> level 1 correction)", "prolong", 1, 54),

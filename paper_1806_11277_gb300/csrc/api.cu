@@ -403,6 +403,8 @@ void build_hier(ehs_ctx* c, Hier& H, int precs, bool coef_only) {
   H.fused0 = (precs & 2) && d == 2 && !H.full && fine_tiles_fit(H.g0) && !(uf && uf[0] == '1');
   if (H.fused0) {
     const size_t nc = (size_t)H.nsets * H.g0.ncell;
+    H.stab.gdx = dalloc<float2>(c, nc);
+    H.stab.gdy = dalloc<float2>(c, nc);
     H.stab.dvx = dalloc<float2>(c, nc);
     H.stab.dvy = dalloc<float2>(c, nc);
     H.stab.sinv = dalloc<float2>(c, nc);
@@ -629,7 +631,7 @@ void cycle_fine_fused(ehs_ctx* c, Hier& H, const float2* b, float2* x, bool gues
     out = out == t ? x : t;
   };
   for (int s = 0; s < H.nu1; ++s) sweep(nullptr);
-  launch_fine_resid_restrict_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.h, H.alpha, cur, b, bc, c->s);
+  launch_fine_resid_restrict_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.stab, H.h, H.alpha, cur, b, bc, c->s);
   cnt(); post();
   const int reps = (1 == H.nlev - 1) ? 1 : H.cyc;
   for (int k = 0; k < reps; ++k) cycle_rec<float>(c, H, 1, bc, xc, k > 0);
@@ -1382,7 +1384,7 @@ ehs_status ehs_residual_restrict(ehs_ctx* c, int level, int prec, const void* b,
     const Level& L = H.lv[level];
     const Level& Lc = H.lv[level + 1];
     if (prec == EHS_C64 && level == 0 && H.fused0) {
-      launch_fine_resid_restrict_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.h, H.alpha, (const float2*)x,
+      launch_fine_resid_restrict_tile(L.g, Lc.g, H.items, H.nrhs, H.cf32, H.stab, H.h, H.alpha, (const float2*)x,
                                       (const float2*)b, (float2*)rc, c->s);
       cnt(); post();
     } else if (prec == EHS_C64) {

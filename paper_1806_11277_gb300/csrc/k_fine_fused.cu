@@ -3,7 +3,8 @@
 //
 // k_fine_sweep_tile: one whole red-black sweep in one launch.  A CTA owns a
 //   SW_X x SW_Y tile of fine cells of one item and stages x (u_0, u_1, p) and
-//   the cell coefficients of the tile plus a 3-cell halo in shared memory.  It
+//   the coefficient terms of the tile plus a halo (2 cells below, 3 above) in
+//   shared memory.  It
 //   relaxes every red cell of the tile and of the one-cell ring around it from
 //   the staged iterate (all red updates from the same old iterate, as in the
 //   red half-sweep), applies them in shared memory, then relaxes the black
@@ -21,12 +22,13 @@
 //   the fine residual is never written to memory.
 //
 // The row arithmetic is that of k_fine_apply / k_fine_vanka, with the
-// quantities that depend on the coefficients alone formed once per staged tile
-// instead of once per use: the mean of mu over the 4 cells around each vertex
-// (the tangential weight of the two face rows that meet there), the diagonal
-// of each face row and its inverse, and the inverse pressure Schur complement
-// of each relaxed cell's arrowhead block (eq. RelaxationMatrix); weights carry
-// the 1/h^2 factor.  Outside the
+// quantities that depend on the coefficients alone formed once instead of once
+// per use: the mean of mu over the 4 cells around each vertex (the tangential
+// weight of the two face rows that meet there), the diagonal of each face row
+// (residual kernel: per staged tile) or its inverse, and the inverse pressure
+// Schur complement of each relaxed cell's arrowhead block (eq.
+// RelaxationMatrix; sweep: setup-time tables); weights carry the 1/h^2
+// factor.  Outside the
 // grid the displacements read zero (Dirichlet slots and the implicit high
 // boundary faces) and the coefficients repeat the nearest cell (the clamped
 // edge averages), so the rows need no per-load bounds checks.  Each cell update
@@ -37,7 +39,13 @@ namespace ehs {
 namespace {
 
 constexpr int SW_X = 32, SW_Y = 16, SW_H = 2;                 // sweep tile, staged halo below it
-constexpr int SWS_X = SW_X + 2 * SW_H + 1, SWS_Y = SW_Y + 2 * SW_H + 1;   // and one cell more above
+constexpr int SWS_X = SW_X + 2 * SW_H + 2, SWS_Y = SW_Y + 2 * SW_H + 1;   // and one (x: two) more above
+// A warp relaxes the cells of one colour in a pair of rows, lane j the cell of column j (in
+// the row of the pair where it has that colour).  With an even row pitch the staged words
+// the 32 lanes read at any one offset then fall in 32 different banks (16 different 8-byte
+// bank pairs per half warp for the complex values), where lanes two columns apart in one row
+// would meet in pairs.
+static_assert(SWS_X % 2 == 0, "even staged row pitch");
 constexpr int SW_RX = SW_X + 2, SW_RY = SW_Y + 2;             // red region: tile + one-cell ring
 constexpr int SW_NRED = SW_RX * SW_RY / 2;                    // 306 red cells
 constexpr int SW_TB = SW_X * SW_Y / 2;                        // 256 black cells: one per thread
@@ -61,15 +69,14 @@ struct FP {
 // Staged tile of W x H cells (local (lx, ly) = global (x0 + lx, y0 + ly)).
 //   x:   u_0, u_1, p (zero outside the grid and on Dirichlet slots)
 //   mu:  cell mu / h^2 (clamped outside the grid); kap: cell 1/(lambda+mu)
-//   mm:  cell (omega^2 rho, omega rho gamma) (clamped) while staging; in the
-//        sweep, afterwards, the inverse Schur complement
-//        1/(-kap - sum_faces (1/h^2) / dg) of the cells that are relaxed
+//   mm:  (sweep tile) the inverse Schur complement 1/(-kap - sum_faces (1/h^2) / dg)
+//        of the cell's block
 //   vm:  vm[ly][lx] = mean of mu / h^2 over cells (lx-1..lx, ly-1..ly), the
 //        vertex at the low corner of cell (lx, ly)
 //   fx / fy: per face of u_0 (between cells lx-1 and lx) / u_1 (between cells
 //        ly-1 and ly) the diagonal dg of its row (residual tile) or its inverse
-//        (sweep tile: the cell solve needs only 1/dg).  Formed by prep() on the
-//        faces the kernel's rows use.
+//        (sweep tile: the cell solve needs only 1/dg).  mm, vm, fx and fy come
+//        from the setup-time tables.
 template <int W, int H>
 struct Tile {
   float2 x[3][H][W];
@@ -115,45 +122,8 @@ __device__ __forceinline__ float2 prolong_at(const float2* __restrict__ ec, int 
   return acc;
 }
 
-// Stage the clamped coefficients of the tile (x0, y0) and x: from xv (null:
-// the zero iterate), plus P e when e is given, with the zero fill.
-template <int W, int H, int NT>
-__device__ __forceinline__ void stage(Tile<W, H>& S, const float4* __restrict__ cfs, const float2* __restrict__ xv,
-                                      const float2* __restrict__ e, const Grid& gc, int N, int nx, int ny,
-                                      int x0, int y0, float h2inv) {
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < W * H; idx += NT) {
-    const int lx = idx % W, ly = idx / W;
-    const int gx = x0 + lx, gy = y0 + ly;
-    const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-    const int cx = min(max(gx, 0), nx - 1), cy = min(max(gy, 0), ny - 1);
-    const int gcl = cy * nx + cx;                                  // a valid address in every case
-    const bool v0 = in && gx >= 1, v1 = in && gy >= 1;            // u_k slot 0 is a boundary face
-    if (!e) {
-      if (xv) {
-        cpa8(&S.x[0][ly][lx], xv + gcl, v0 ? 8 : 0);
-        cpa8(&S.x[1][ly][lx], xv + N + gcl, v1 ? 8 : 0);
-        cpa8(&S.x[2][ly][lx], xv + 2 * N + gcl, in ? 8 : 0);
-      } else {
-        const float2 z = make_float2(0.f, 0.f);
-        S.x[0][ly][lx] = z; S.x[1][ly][lx] = z; S.x[2][ly][lx] = z;
-      }
-    } else {
-      float2 u0 = make_float2(0.f, 0.f), u1 = u0, pv = u0;
-      if (v0) u0 = cadd(xv ? __ldg(xv + gcl) : u0, prolong_at(e, 0, gx, gy, gc.n[0], gc.n[1]));
-      if (v1) u1 = cadd(xv ? __ldg(xv + N + gcl) : u1, prolong_at(e, 1, gx, gy, gc.n[0], gc.n[1]));
-      if (in) pv = cadd(xv ? __ldg(xv + 2 * N + gcl) : pv, prolong_at(e, 2, gx, gy, gc.n[0], gc.n[1]));
-      S.x[0][ly][lx] = u0; S.x[1][ly][lx] = u1; S.x[2][ly][lx] = pv;
-    }
-    const float4 c = __ldg(cfs + gcl);
-    S.mu[ly][lx] = c.x * h2inv;
-    S.kap[ly][lx] = c.y;
-    S.mm[ly][lx] = make_float2(c.z, c.w);
-  }
-}
-
-// The coefficient terms of the rows, shared by prep() and the setup-time tables:
-// the mean of mu / h^2 over the four cells around a vertex, and the diagonal of a
+// The coefficient terms of the rows, formed into the setup-time tables below: the
+// mean of mu / h^2 over the four cells around a vertex, and the diagonal of a
 // face row from the mu / h^2 of its two cells, the vertex means at its two ends and
 // the two cells' (omega^2 rho, omega rho gamma).
 __device__ __forceinline__ float vertex_mean(float m00, float m01, float m10, float m11) {
@@ -166,40 +136,13 @@ __device__ __forceinline__ float2 face_diag(float mu0, float mu1, float vhi, flo
   return make_float2(wsum - rf, gf + alpha * rf);
 }
 
-// Coefficient terms of the rows of the cells in [RX0, RX1] x [RY0, RY1] (staged
-// coordinates) and of their faces: vertex means and face diagonals (after stage()
-// and a barrier; ends with a barrier).
-template <int W, int H, int NT, int RX0, int RX1, int RY0, int RY1>
-__device__ __forceinline__ void prep(Tile<W, H>& S, const FP& P) {
-  static_assert(RX0 >= 1 && RY0 >= 1 && RX1 + 1 <= W - 1 && RY1 + 1 <= H - 1, "prep region inside the tile");
-  constexpr int VX = RX1 - RX0 + 2, VY = RY1 - RY0 + 2;          // vertices and faces: one wider
-  for (int idx = threadIdx.x; idx < VX * VY; idx += NT) {
-    const int lx = RX0 + idx % VX, ly = RY0 + idx / VX;
-    S.vm[ly][lx] = vertex_mean(S.mu[ly][lx], S.mu[ly][lx - 1], S.mu[ly - 1][lx], S.mu[ly - 1][lx - 1]);
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < VX * VY; idx += NT) {
-    const int lx = RX0 + idx % VX, ly = RY0 + idx / VX;
-    if (ly <= RY1) {     // u_0 face between cells (lx-1, ly) and (lx, ly)
-      const float2 d = face_diag(S.mu[ly][lx], S.mu[ly][lx - 1], S.vm[ly + 1][lx], S.vm[ly][lx], S.mm[ly][lx],
-                                 S.mm[ly][lx - 1], P.alpha);
-      S.fx[ly][lx] = d;
-    }
-    if (lx <= RX1) {     // u_1 face between cells (lx, ly-1) and (lx, ly)
-      const float2 d = face_diag(S.mu[ly][lx], S.mu[ly - 1][lx], S.vm[ly][lx + 1], S.vm[ly][lx], S.mm[ly][lx],
-                                 S.mm[ly - 1][lx], P.alpha);
-      S.fy[ly][lx] = d;
-    }
-  }
-  __syncthreads();
-}
-
-// Setup-time tables of the sweep, per medium: the inverse diagonals of each cell's
-// low u_0 and u_1 face rows (dvx, dvy, [ncell]), the inverse pressure Schur
+// Setup-time tables of the fused kernels, per medium: the diagonals of each cell's
+// low u_0 and u_1 face rows (gdx, gdy, [ncell]) and their inverses (dvx, dvy), the
+// inverse pressure Schur
 // complement of each cell's block (sinv, [ncell]) and the vertex means of mu / h^2
 // (vm, [(nx + 1) (ny + 1)], vertex (vx, vy) the low corner of cell (vx, vy)).  The
-// same formulas and clamped coefficients as prep(), formed once instead of in every
-// sweep; entries on Dirichlet faces are formed but never used.
+// clamped coefficients outside the grid (the clamped edge averages), formed once
+// instead of in every sweep; entries on Dirichlet faces are formed but never used.
 __device__ __forceinline__ float mu_cl(const float4* cfs, int gx, int gy, int nx, int ny, float h2inv) {
   return __ldg(cfs + min(max(gy, 0), ny - 1) * nx + min(max(gx, 0), nx - 1)).x * h2inv;
 }
@@ -212,7 +155,8 @@ __device__ __forceinline__ float vm_cl(const float4* cfs, int vx, int vy, int nx
                      mu_cl(cfs, vx, vy - 1, nx, ny, h2inv), mu_cl(cfs, vx - 1, vy - 1, nx, ny, h2inv));
 }
 __global__ void k_sweep_tables_faces(Grid g, const float4* __restrict__ cf, FP P, float2* __restrict__ dvx,
-                                     float2* __restrict__ dvy, float* __restrict__ vm) {
+                                     float2* __restrict__ dvy, float2* __restrict__ gdx, float2* __restrict__ gdy,
+                                     float* __restrict__ vm) {
   const int nx = g.n[0], ny = g.n[1];
   const int nv = (nx + 1) * (ny + 1);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,10 +170,14 @@ __global__ void k_sweep_tables_faces(Grid g, const float4* __restrict__ cf, FP P
   const long long c = (long long)set * g.ncell + vy * nx + vx;
   const float mc = mu_cl(cfs, vx, vy, nx, ny, h2), v00 = vm_cl(cfs, vx, vy, nx, ny, h2);
   const float2 m0 = mm_cl(cfs, vx, vy, nx, ny);
-  dvx[c] = cinv(face_diag(mc, mu_cl(cfs, vx - 1, vy, nx, ny, h2), vm_cl(cfs, vx, vy + 1, nx, ny, h2), v00, m0,
-                          mm_cl(cfs, vx - 1, vy, nx, ny), P.alpha));
-  dvy[c] = cinv(face_diag(mc, mu_cl(cfs, vx, vy - 1, nx, ny, h2), vm_cl(cfs, vx + 1, vy, nx, ny, h2), v00, m0,
-                          mm_cl(cfs, vx, vy - 1, nx, ny), P.alpha));
+  const float2 dx = face_diag(mc, mu_cl(cfs, vx - 1, vy, nx, ny, h2), vm_cl(cfs, vx, vy + 1, nx, ny, h2), v00, m0,
+                              mm_cl(cfs, vx - 1, vy, nx, ny), P.alpha);
+  const float2 dy = face_diag(mc, mu_cl(cfs, vx, vy - 1, nx, ny, h2), vm_cl(cfs, vx + 1, vy, nx, ny, h2), v00, m0,
+                              mm_cl(cfs, vx, vy - 1, nx, ny), P.alpha);
+  gdx[c] = dx;
+  gdy[c] = dy;
+  dvx[c] = cinv(dx);
+  dvy[c] = cinv(dy);
 }
 __global__ void k_sweep_tables_schur(Grid g, const float4* __restrict__ cf, FP P, const float2* __restrict__ dvx,
                                      const float2* __restrict__ dvy, float2* __restrict__ sinv) {
@@ -247,9 +195,11 @@ __global__ void k_sweep_tables_schur(Grid g, const float4* __restrict__ cf, FP P
   sinv[c] = cinv(make_float2(-kap - P.h2inv * sd.x, -P.h2inv * sd.y));
 }
 
-// Stage x as stage() does, with mu / h^2 and 1/(lambda+mu) of the cells and the
-// setup-time tables (fx, fy: inverse face diagonals, mm: inverse Schur complement,
-// vm: vertex means) in place of the coefficients prep() would combine.
+// Stage the tile (x0, y0) of x: from xv (null: the zero iterate), plus P e when e is
+// given, zero outside the grid and on Dirichlet slots; with mu / h^2 and
+// 1/(lambda+mu) of the (clamped) cells and the setup-time tables: fx, fy the
+// face diagonals or their inverses (tx, ty), mm the inverse Schur complements (ts;
+// not staged when null), vm the vertex means (tv).
 template <int W, int H, int NT>
 __device__ __forceinline__ void stage_tab(Tile<W, H>& S, const float4* __restrict__ cfs, const float2* __restrict__ tx,
                                           const float2* __restrict__ ty, const float2* __restrict__ ts,
@@ -282,7 +232,7 @@ __device__ __forceinline__ void stage_tab(Tile<W, H>& S, const float4* __restric
     }
     cpa8(&S.fx[ly][lx], tx + gcl, 8);
     cpa8(&S.fy[ly][lx], ty + gcl, 8);
-    cpa8(&S.mm[ly][lx], ts + gcl, 8);
+    if (ts) cpa8(&S.mm[ly][lx], ts + gcl, 8);
     cpa4(&S.vm[ly][lx], tv + min(max(gy, 0), ny) * (nx + 1) + min(max(gx, 0), nx));
     const float2 mk = __ldg(reinterpret_cast<const float2*>(cfs + gcl));   // mu, 1/(lambda+mu)
     S.mu[ly][lx] = mk.x * h2inv;
@@ -420,10 +370,9 @@ __global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, in
     rsx[q] = -1;
     const int id = threadIdx.x + q * SW_T;
     if (id >= SW_NRED) continue;
-    const int ry = id / (SW_RX / 2), kx = id % (SW_RX / 2);
-    const int gy = Y0 - 1 + ry;
-    const int gxs = X0 - 1;
-    const int gx = gxs + 2 * kx + ((gxs + gy) & 1);                 // (gx + gy) even: red
+    const int pr = id / SW_RX, j = id % SW_RX;                     // row pair, column
+    const int gx = X0 - 1 + j, gy0 = Y0 - 1 + 2 * pr;
+    const int gy = gy0 + ((gx + gy0) & 1);                         // (gx + gy) even: red
     if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
     const int sx = gx - x0, sy = gy - y0;
     cell_update<SWS_X, SWS_Y>(S, sx, sy, gx, gy, nx, ny, N, gy * nx + gx, bb, P, wu, wp, ro[q], rok[q]);
@@ -444,21 +393,19 @@ __global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, in
   // ---- black cells of the tile from the red-updated iterate; outputs
   const int t = threadIdx.x;
   if (t >= SW_TB) return;                                          // no barrier follows
-  const int ty = t / (SW_X / 2), kx = t % (SW_X / 2);
-  const int gy = Y0 + ty;
-  const int gxb = X0 + 2 * kx + ((gy + 1) & 1);                    // (gx + gy) odd: black
-  const int gxr = gxb ^ 1;                                         // the red cell of the pair
-  const int cb = gy * nx + gxb, cr = gy * nx + gxr;
-  const int sy = gy - y0;
-  // red pressure of the pair: the red update
-  xout[2 * N + cr] = S.x[2][sy][gxr - x0];
-  // Dirichlet slots of the pair's two cells (never written by any update)
-  if (gxb == 0) xout[cb] = make_float2(0.f, 0.f);
-  if (gxr == 0) xout[cr] = make_float2(0.f, 0.f);
-  if (gy == 0) { xout[N + cb] = make_float2(0.f, 0.f); xout[N + cr] = make_float2(0.f, 0.f); }
+  const int gx = X0 + t % SW_X, gy0 = Y0 + 2 * (t / SW_X);         // column, row pair
+  const int gyb = gy0 + ((gx + gy0 + 1) & 1), gyr = gyb ^ 1;       // (gx + gy) odd: black; the red one
+  const int cb = gyb * nx + gx, cr = gyr * nx + gx;
+  const int sx = gx - x0, sy = gyb - y0;
+  // red pressure of the column's red cell: the red update
+  xout[2 * N + cr] = S.x[2][gyr - y0][sx];
+  // Dirichlet slots of the column's two cells (never written by any update)
+  if (gx == 0) { xout[cb] = make_float2(0.f, 0.f); xout[cr] = make_float2(0.f, 0.f); }
+  if (gyb == 0) xout[N + cb] = make_float2(0.f, 0.f);
+  if (gyr == 0) xout[N + cr] = make_float2(0.f, 0.f);
   float2 o[5];
   bool ok[4];
-  cell_update<SWS_X, SWS_Y>(S, gxb - x0, sy, gxb, gy, nx, ny, N, cb, bb, P, wu, wp, o, ok);
+  cell_update<SWS_X, SWS_Y>(S, sx, sy, gx, gyb, nx, ny, N, cb, bb, P, wu, wp, o, ok);
   xout[2 * N + cb] = o[4];
   if (ok[0]) xout[cb] = o[0];
   if (ok[1]) xout[N + cb] = o[1];
@@ -470,7 +417,10 @@ __global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, in
 __device__ __forceinline__ float rw(int kind, int j, int J, int nc) { return 0.25f * (float)pw4(kind, j, J, nc); }
 
 __global__ void __launch_bounds__(RR_T, 4) k_fine_resid_restrict_tile(Grid g, Grid gc, int nrhs,
-                                                                      const float4* __restrict__ cf, FP P,
+                                                                      const float4* __restrict__ cf,
+                                                                      const float2* __restrict__ tgx,
+                                                                      const float2* __restrict__ tgy,
+                                                                      const float* __restrict__ tvm, FP P,
                                                                       const float2* __restrict__ x,
                                                                       const float2* __restrict__ b,
                                                                       float2* __restrict__ rc,
@@ -484,11 +434,12 @@ __global__ void __launch_bounds__(RR_T, 4) k_fine_resid_restrict_tile(Grid g, Gr
   const float4* cfs = cf + (long long)(item / nrhs) * N;
   const int X0 = blockIdx.x * RR_X, Y0 = blockIdx.y * RR_Y;
   const int x0 = X0 - RR_H, y0 = Y0 - RR_H;
-  stage<RRS_X, RRS_Y, RR_T>(S, cfs, x + vo, nullptr, gc, N, nx, ny, x0, y0, P.h2inv);
+  const int set = item / nrhs;
+  const long long nvt = (long long)(nx + 1) * (ny + 1);
+  stage_tab<RRS_X, RRS_Y, RR_T>(S, cfs, tgx + (long long)set * N, tgy + (long long)set * N, nullptr, tvm + set * nvt,
+                                x + vo, nullptr, gc, N, nx, ny, x0, y0, P.h2inv);
   cpa_wait();
   __syncthreads();
-  // the residual region (tile + one-cell ring) spans staged [RR_H - 1, RR_H + RR_X] x [RR_H - 1, RR_H + RR_Y]
-  prep<RRS_X, RRS_Y, RR_T, RR_H - 1, RR_H + RR_X, RR_H - 1, RR_H + RR_Y>(S, P);
   const float2* bb = b + vo;
   const float hinv = P.hinv;
   // fine residual b - K_s x on the tile and its one-cell ring (zero outside the grid and on
@@ -602,7 +553,8 @@ void launch_sweep_tables(const Grid& g, int nsets, const Coef4<float>* cf, doubl
   const FP P = make_fp(h, alpha);
   const float4* c4 = reinterpret_cast<const float4*>(cf);
   const long long nv = sweep_table_vertices(g);
-  k_sweep_tables_faces<<<dim3((unsigned)((nv + 255) / 256), nsets), 256, 0, s>>>(g, c4, P, T.dvx, T.dvy, T.vm);
+  k_sweep_tables_faces<<<dim3((unsigned)((nv + 255) / 256), nsets), 256, 0, s>>>(g, c4, P, T.dvx, T.dvy, T.gdx,
+                                                                                    T.gdy, T.vm);
   k_sweep_tables_schur<<<dim3((unsigned)((g.ncell + 255) / 256), nsets), 256, 0, s>>>(g, c4, P, T.dvx, T.dvy,
                                                                                        T.sinv);
 }
@@ -618,13 +570,13 @@ void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, 
 }
 
 void launch_fine_resid_restrict_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
-                                     double h, double alpha, const float2* x, const float2* b, float2* rc,
-                                     cudaStream_t s) {
+                                     const SweepTab& T, double h, double alpha, const float2* x, const float2* b,
+                                     float2* rc, cudaStream_t s) {
   const FP P = make_fp(h, alpha);
   smem_attr(k_fine_resid_restrict_tile, sizeof(ResTile));
   const dim3 gr(g.n[0] / RR_X, g.n[1] / RR_Y, sel_items(items));
-  k_fine_resid_restrict_tile<<<gr, RR_T, sizeof(ResTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf), P,
-                                                                x, b, rc, g_sel.list);
+  k_fine_resid_restrict_tile<<<gr, RR_T, sizeof(ResTile), s>>>(g, gc, nrhs, reinterpret_cast<const float4*>(cf),
+                                                                T.gdx, T.gdy, T.vm, P, x, b, rc, g_sel.list);
 }
 
 }  // namespace ehs

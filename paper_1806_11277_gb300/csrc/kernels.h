@@ -55,10 +55,12 @@ void launch_fine_vanka(const Grid& g, int items, int nrhs, const Coef4<T>* cf, d
 // xo = sweep(x_in), x_in = (xi or 0) + (P ec if ec), xo != xi; ec: coarse
 // vector of grid gc (ignored when null).  And r_c = P^T (b - K_s x) in one pass.
 bool fine_tiles_fit(const Grid& g);
-// Setup-time tables of the fused sweep, per medium (k_fine_fused.cu): inverse diagonals of each
-// cell's low u_0 / u_1 face rows and the inverse pressure Schur complement of its block
-// ([nsets][ncell] each), vertex means of mu / h^2 ([nsets][sweep_table_vertices(g)])
+// Setup-time tables of the fused fine kernels, per medium (k_fine_fused.cu): the diagonals of
+// each cell's low u_0 / u_1 face rows, their inverses and the inverse pressure Schur complement
+// of its block ([nsets][ncell] each), vertex means of mu / h^2 ([nsets][sweep_table_vertices(g)])
 struct SweepTab {
+  float2* gdx = nullptr;
+  float2* gdy = nullptr;
   float2* dvx = nullptr;
   float2* dvy = nullptr;
   float2* sinv = nullptr;
@@ -71,8 +73,8 @@ void launch_fine_sweep_tile(const Grid& g, const Grid& gc, int items, int nrhs, 
                             const SweepTab& T, double h, double alpha, float wu, float wp, const float2* b,
                             const float2* xi, const float2* ec, float2* xo, cudaStream_t s);
 void launch_fine_resid_restrict_tile(const Grid& g, const Grid& gc, int items, int nrhs, const Coef4<float>* cf,
-                                     double h, double alpha, const float2* x, const float2* b, float2* rc,
-                                     cudaStream_t s);
+                                     const SweepTab& T, double h, double alpha, const float2* x, const float2* b,
+                                     float2* rc, cudaStream_t s);
 // level-0 stencil table (double) of K_s for the Galerkin setup
 void fine_table_layout(int d, StencilLayout* L);
 void launch_fine_table(const Grid& g, int nsets, const Coef4<double>* cf, double h,
