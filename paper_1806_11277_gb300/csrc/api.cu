@@ -95,6 +95,8 @@ struct Hier {
   Coef4<double>* cf64 = nullptr;
   Coef4<float>* cf32 = nullptr;
   void* cfdf = nullptr;        // df64 coefficients (outer-Krylov operator of the global problem)
+  float4* kdg = nullptr;       // 2D: df64 tables of that operator (face-row diagonals, vertex means)
+  float2* kvm = nullptr;
   std::vector<Level> lv;
 };
 
@@ -1054,17 +1056,18 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
         if (c->opt.precond == EHS_PRECOND_DD) dd_apply_t<float>(c, c->f_in, Zj);
         else cycle_rec<float>(c, c->H, 0, c->f_in, Zj, false);
       });
-      launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, Zj, 1, nullptr, c->wq, 0, s);
-      // CGS2: h1 = V^H w; w' = w - V h1 with h2 = V^H w' and ||w'||^2 in the same pass, whose
-      // last block also forms ||w' - V h2|| = sqrt(||w'||^2 - ||h2||^2); then one pass forms
-      // V_{j+1} = (w' - V h2) / ||.|| and its complex64 copy.  Each reduction is done by the
-      // launch's last block.
+      launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, Zj, 1, nullptr, c->wq, 0, s, c->H.kdg,
+                           c->H.kvm);
+      // CGS2: h1 = V^H w; w' = w - V h1 (not stored) with h2 = V^H w' and ||w'||^2 in the same
+      // pass, whose last block also forms ||w' - V h2|| = sqrt(||w'||^2 - ||h2||^2); then one pass
+      // forms V_{j+1} = (w - V (h1 + h2)) / ||.|| and its complex64 copy.  Each reduction is done
+      // by the launch's last block.
       const int nv = j + 1;
       int* k0 = c->kcnt;
       int* k1 = c->kcnt + items;
       launch_mdot_df(n, items, nv, c->Vq, c->wq, c->partq, nblk, s, k0, c->hq, c->hhost);
       launch_mupdate_df(n, items, nv, c->Vq, c->hq, c->wq, c->partq, nblk, 1, c->npq, s, k1, c->h2q,
-                        c->hhost + (size_t)items * 12, c->nrm, c->invq);
+                        c->hhost + (size_t)items * 12, c->nrm, c->invq, 0);
       // one round trip into pinned memory (h1, h2 and the norms), overlapped with the last pass
       double2* ph1 = c->hstep;
       double2* ph2 = c->hstep + (size_t)items * 12;
@@ -1073,7 +1076,7 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
       CK(cudaMemcpyAsync(phn, c->nrm, items * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaEventRecord(c->ev_step, s));
       launch_update_scale_cast_df(n, items, nv, c->Vq, c->h2q, c->wq, c->invq, c->Vq + (size_t)(j + 1) * items * n,
-                                  c->f_in, nblk, s);
+                                  c->f_in, nblk, s, c->hq);
       cnt(4); post();                        // with the operator launch above
       CK(cudaEventSynchronize(c->ev_step));
       if (!A.step(j, ph1, ph2, phn)) break;
@@ -1085,7 +1088,8 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
     launch_d2_to_df((long long)items * m, c->hhost, c->yq, s);
     CK(cudaMemcpyAsync(c->kused, A.kused.data(), items * sizeof(int), cudaMemcpyHostToDevice, s));
     launch_xupdate_df(n, items, m, c->Zf, c->yq, c->kused, c->xq, s);
-    launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, c->xq, 0, c->qq, c->rq, 1, s);
+    launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, c->xq, 0, c->qq, c->rq, 1, s, c->H.kdg,
+                         c->H.kvm);
     launch_norm_part_df(n, items, c->rq, c->npq, nblk, s);
     launch_reduce_norm_df(items, nblk, c->npq, c->nrm, c->invq, s); cnt(5); post();
     sync_read(c, c->hpin, c->nrm, items * sizeof(double));
@@ -1258,6 +1262,11 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
     if (opts->prec == EHS_C64) {   // df64 Krylov workspace of the mixed form
       H.cfdf = dalloc<float4>(c, (size_t)2 * H.nsets * H.g0.ncell);
       launch_coef_df((long long)H.nsets * H.g0.ncell, H.cf64, H.cfdf, c->s); cnt(); post();
+      if (H.g0.d == 2) {
+        H.kdg = dalloc<float4>(c, (size_t)2 * H.nsets * H.g0.ncell);
+        H.kvm = dalloc<float2>(c, (size_t)H.nsets * (H.g0.n[0] + 1) * (H.g0.n[1] + 1));
+        launch_apply_df_tables(H.g0, H.nsets, H.cf64, H.h, H.kdg, H.kvm, c->s); cnt(); post();
+      }
       c->Vq = dalloc<float4>(c, (size_t)(m + 1) * items * n);
       c->Zf = dalloc<float2>(c, (size_t)m * items * n);
       c->wq = dalloc<float4>(c, (size_t)items * n);

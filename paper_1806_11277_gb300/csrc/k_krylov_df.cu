@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(KB, 2) k_mdot_df(long long n, int items, const
   if (cnt && last_block(cnt, item, nblk)) reduce_dots_last(item, NV, nblk, part, out, outd, cnt);
 }
 
-// w -= sum_i V_i h_i; optional partial dots of V with the new w and |w|^2.
+// w -= sum_i V_i h_i (stored unless store = 0); optional partial dots of V with the new w and |w|^2.
 // With cnt, the last block of each item also forms the dots' sums (out, outd)
 // and/or the norm (nrm, inv = 1/norm): with both, the norm of the vector that
 // removing V out from w would leave (reduce_norm_pythag_last).
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
                                                       const float4* __restrict__ h, float4* __restrict__ w,
                                                       float4* part, int nblk, int dot, float2* nrm_part,
                                                       const int* __restrict__ il, int* cnt, float4* out,
-                                                      double2* outd, double* nrm, float2* inv) {
+                                                      double2* outd, double* nrm, float2* inv, int store) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   __shared__ float4 hs[NV][2];
   if (threadIdx.x < NV) load_hpairs(h + (long long)item * NV + threadIdx.x, hs[threadIdx.x]);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
                  make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w));
     }
     const dfc we = dfc_sub(dfc_ldv(wv + e), dacc2_val(sv));
-    dfc_st(wv + e, we);
+    if (store) dfc_st(wv + e, we);
     if (dot) {
       const float2 wah = make_float2(we.re.hi, -we.re.hi), wal = make_float2(we.re.lo, -we.re.lo);
       const float2 wbh = make_float2(we.im.hi, we.im.hi), wbl = make_float2(we.im.lo, we.im.lo);
@@ -267,10 +267,11 @@ __global__ void __launch_bounds__(KB, 2) k_mupdate_df(long long n, int items, co
   }
 }
 
-// The last pass of an Arnoldi step: V_{j+1} = (w - sum_i V_i h_i) * inv (df64) and
-// its complex64 copy, the next preconditioner input; w itself is not written.
+// The last pass of an Arnoldi step: V_{j+1} = (w - sum_i V_i (h0_i + h_i)) * inv (df64)
+// and its complex64 copy, the next preconditioner input; w itself is not written.
 template <int NV>
 __global__ void __launch_bounds__(KB, 3) k_update_scale_cast_df(long long n, int items, const float4* __restrict__ V,
+                                                                const float4* __restrict__ h0,
                                                                 const float4* __restrict__ h,
                                                                 const float4* __restrict__ w,
                                                                 const float2* __restrict__ inv,
@@ -278,7 +279,11 @@ __global__ void __launch_bounds__(KB, 3) k_update_scale_cast_df(long long n, int
                                                                 int nblk, const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   __shared__ float4 hs[NV];
-  if (threadIdx.x < NV) hs[threadIdx.x] = h[(long long)item * NV + threadIdx.x];
+  if (threadIdx.x < NV) {   // the coefficients h0 + h (h0 may be null)
+    dfc hv = dfc_ldv(h + (long long)item * NV + threadIdx.x);
+    if (h0) hv = dfc_add(dfc_ldv(h0 + (long long)item * NV + threadIdx.x), hv);
+    dfc_st(hs + threadIdx.x, hv);
+  }
   __syncthreads();
   const float2 sc = inv[item];
   const dfr iv = {sc.x, sc.y};
@@ -464,6 +469,93 @@ __device__ __forceinline__ dfc row_p_df(const Grid& g, long long c, const int i[
   return dfc_sub(dfc_scale(s, P.hinv), dfc_scale(pc, c0.kap));
 }
 
+// Setup-time tables of the 2D operator K (unshifted): per cell the diagonals of its
+// low u_0 and u_1 face rows (complex df64, [set][2][ncell]; entries on Dirichlet
+// faces are formed but never used) and per vertex ((nx + 1) (ny + 1)) the mean of mu
+// over the four cells around it (df64, [set][vertex]; clamped at the edges, as the
+// rows' tangential weights clamp), formed in FP64 from the FP64 coefficients.
+__device__ __forceinline__ const Coef4<double>& cf_cl(const Coef4<double>* cf, int x, int y, int nx, int ny) {
+  return cf[min(max(y, 0), ny - 1) * nx + min(max(x, 0), nx - 1)];
+}
+__device__ __forceinline__ double vm_d(const Coef4<double>* cf, int vx, int vy, int nx, int ny) {
+  return 0.25 * ((cf_cl(cf, vx, vy, nx, ny).mu + cf_cl(cf, vx - 1, vy, nx, ny).mu) + cf_cl(cf, vx, vy - 1, nx, ny).mu +
+                 cf_cl(cf, vx - 1, vy - 1, nx, ny).mu);
+}
+__global__ void k_apply_df_tables(Grid g, const Coef4<double>* __restrict__ cf, double h2inv, float4* __restrict__ dg,
+                                  float2* __restrict__ vm) {
+  const int nx = g.n[0], ny = g.n[1];
+  const int nv = (nx + 1) * (ny + 1);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv) return;
+  const int set = blockIdx.y;
+  const Coef4<double>* cs = cf + (long long)set * g.ncell;
+  const int vx = t % (nx + 1), vy = t / (nx + 1);
+  const dfr v = df_from_d(vm_d(cs, vx, vy, nx, ny));
+  vm[(long long)set * nv + t] = make_float2(v.hi, v.lo);
+  if (vx >= nx || vy >= ny) return;
+  const Coef4<double>& c0 = cf_cl(cs, vx, vy, nx, ny);
+  // u_0 face between cells (vx-1, vy) and (vx, vy); u_1 face between (vx, vy-1) and (vx, vy)
+  for (int k = 0; k < 2; ++k) {
+    const Coef4<double>& c1 = k == 0 ? cf_cl(cs, vx - 1, vy, nx, ny) : cf_cl(cs, vx, vy - 1, nx, ny);
+    const double wp = k == 0 ? vm_d(cs, vx, vy + 1, nx, ny) : vm_d(cs, vx + 1, vy, nx, ny);
+    const double wsum = (c0.mu + c1.mu) + wp + vm_d(cs, vx, vy, nx, ny);
+    const double rf = 0.5 * (c0.mr + c1.mr), gf = 0.5 * (c0.mi + c1.mi);
+    dfc_st(dg + ((long long)set * 2 + k) * g.ncell + (long long)vy * nx + vx,
+           dfc_from_d2(make_double2(wsum * h2inv - rf, gf)));
+  }
+}
+
+// The 2D rows of K (alpha = 0) with the tables above: a u_k row at cell c is
+// dg_k(c) x_c - (mu_c x_{c+e_k} + mu_{c-e_k} x_{c-e_k} + vm+ x_{c+e_j} + vm- x_{c-e_j}) / h^2
+// + (p_c - p_{c-e_k}) / h, the same terms k_fine_apply_df forms from the cells'
+// coefficients.  y = K x (mode 0) or b - K x (mode 1).
+template <typename V>
+__global__ void k_fine_apply_df2t(Grid g, int nrhs, const Coef4df* __restrict__ cf, const float4* __restrict__ dg,
+                                  const float2* __restrict__ vmt, FinePdf P, const V* __restrict__ x,
+                                  const float4* __restrict__ b, float4* __restrict__ y, int mode,
+                                  const int* __restrict__ il) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  const long long N = g.ncell;
+  const int nx = g.n[0], ny = g.n[1];
+  const long long vo = (long long)item * 3 * N;
+  const int set = item / nrhs;
+  const Coef4df* cs = cf + (long long)set * N;
+  const float2* vms = vmt + (long long)set * (nx + 1) * (ny + 1);
+  const V* xv = x + vo;
+  const V* pv = xv + 2 * N;
+  const int ix = (int)(c % nx), iy = (int)(c / nx);
+  const Coef4df c0 = ldcf_df(cs, c);
+  const float2 v00 = __ldg(vms + (long long)iy * (nx + 1) + ix);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    dfc r = dfc_zero();
+    const int ik = k == 0 ? ix : iy, nk = k == 0 ? nx : ny;
+    if (ik >= 1) {
+      const long long sk = k == 0 ? 1 : nx, sj = k == 0 ? nx : 1;
+      const int ij = k == 0 ? iy : ix, nj = k == 0 ? ny : nx;
+      const V* xk = xv + (long long)k * N;
+      const dfr mu1 = ldcf_df(cs, c - sk).mu;
+      const float2 vp = __ldg(vms + (k == 0 ? (long long)(iy + 1) * (nx + 1) + ix : (long long)iy * (nx + 1) + ix + 1));
+      dfc nb = dfc_zero();
+      if (ik + 1 < nk) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c + sk), c0.mu));
+      if (ik - 1 >= 1) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c - sk), mu1));
+      if (ij + 1 < nj) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c + sj), dfr{vp.x, vp.y}));
+      if (ij - 1 >= 0) nb = dfc_add(nb, dfc_scale(ldx<V>(xk, c - sj), dfr{v00.x, v00.y}));
+      const dfc d = dfc_ld(dg + ((long long)set * 2 + k) * N + c);
+      r = dfc_sub(dfc_mul(d, ldx<V>(xk, c)), dfc_scale(nb, P.h2inv));
+      r = dfc_add(r, dfc_scale(dfc_sub(ldx<V>(pv, c), ldx<V>(pv, c - sk)), P.hinv));
+      if (mode) r = dfc_sub(dfc_ld(b + vo + (long long)k * N + c), r);
+    }
+    dfc_st(y + vo + (long long)k * N + c, r);
+  }
+  const int i[3] = {ix, iy, 0};
+  dfc r = row_p_df<V, 2>(g, c, i, c0, xv, P);
+  if (mode) r = dfc_sub(dfc_ld(b + vo + 2 * N + c), r);
+  dfc_st(y + vo + 2 * N + c, r);
+}
+
 // y = K x (mode 0) or y = b - K x (mode 1); x of type V, b and y complex df64
 template <typename V, int D>
 __global__ void k_fine_apply_df(Grid g, int nrhs, const Coef4df* __restrict__ cf, FinePdf P,
@@ -539,21 +631,22 @@ void launch_mdot_df(long long n, int items, int nv, const float4* V, const float
 }
 void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
                        float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s, int* cnt, float4* out,
-                       double2* outd, double* nrm, float2* inv) {
+                       double2* outd, double* nrm, float2* inv, int store) {
   const dim3 g(nblk, sel_items(items));
   switch (nv) {
 #define X(k) case k: k_mupdate_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, part, nblk, dot, nrm_part, g_sel.list, \
-                                                      cnt, out, outd, nrm, inv); break;
+                                                      cnt, out, outd, nrm, inv, store); break;
     EHS_NV_CASES(X)
 #undef X
     default: break;
   }
 }
 void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V, const float4* h, const float4* w,
-                                 const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s) {
+                                 const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s,
+                                 const float4* h0) {
   const dim3 g(nblk, sel_items(items));
   switch (nv) {
-#define X(k) case k: k_update_scale_cast_df<k><<<g, KB, 0, s>>>(n, items, V, h, w, inv, out, out32, nblk, g_sel.list); \
+#define X(k) case k: k_update_scale_cast_df<k><<<g, KB, 0, s>>>(n, items, V, h0, h, w, inv, out, out32, nblk, g_sel.list); \
     break;
     EHS_NV_CASES(X)
 #undef X
@@ -595,11 +688,24 @@ void launch_df_to_f2(long long n, const float4* in, float2* out, cudaStream_t s)
 void launch_coef_df(long long n, const Coef4<double>* in, void* out, cudaStream_t s) {
   k_coef_df<<<nb(n, 256), 256, 0, s>>>(n, in, (Coef4df*)out);
 }
+void launch_apply_df_tables(const Grid& g, int nsets, const Coef4<double>* cf, double h, float4* dg, float2* vm,
+                            cudaStream_t s) {
+  const long long nv = (long long)(g.n[0] + 1) * (g.n[1] + 1);
+  k_apply_df_tables<<<dim3((unsigned)((nv + 255) / 256), nsets), 256, 0, s>>>(g, cf, 1.0 / (h * h), dg, vm);
+}
 void launch_fine_apply_df(const Grid& g, int items, int nrhs, const void* cf, double h, double alpha,
-                          const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s) {
+                          const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s,
+                          const float4* dg, const float2* vm) {
   const FinePdf P = mkPdf(h, alpha);
   const dim3 grid(nb(g.ncell, 128), sel_items(items));
   const Coef4df* c = (const Coef4df*)cf;
+  if (g.d == 2 && alpha == 0.0 && dg && vm) {   // the setup-time tables of K
+    if (x_is_c64) k_fine_apply_df2t<float2><<<grid, 128, 0, s>>>(g, nrhs, c, dg, vm, P, (const float2*)x, b, y, mode,
+                                                                 g_sel.list);
+    else k_fine_apply_df2t<float4><<<grid, 128, 0, s>>>(g, nrhs, c, dg, vm, P, (const float4*)x, b, y, mode,
+                                                        g_sel.list);
+    return;
+  }
   if (g.d == 2) {
     if (x_is_c64) k_fine_apply_df<float2, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float2*)x, b, y, mode, g_sel.list);
     else k_fine_apply_df<float4, 2><<<grid, 128, 0, s>>>(g, nrhs, c, P, (const float4*)x, b, y, mode, g_sel.list);

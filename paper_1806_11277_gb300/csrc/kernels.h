@@ -223,11 +223,13 @@ void launch_mdot_df(long long n, int items, int nv, const float4* V, const float
                     int nblk, cudaStream_t s, int* cnt = nullptr, float4* out = nullptr, double2* outd = nullptr);
 void launch_mupdate_df(long long n, int items, int nv, const float4* V, const float4* h, float4* w,
                        float4* part, int nblk, int dot, float2* nrm_part, cudaStream_t s, int* cnt = nullptr,
-                       float4* out = nullptr, double2* outd = nullptr, double* nrm = nullptr, float2* inv = nullptr);
+                       float4* out = nullptr, double2* outd = nullptr, double* nrm = nullptr, float2* inv = nullptr,
+                       int store = 1);
 // out = w / norm (inv per item) and out32 = its complex64 copy
-// V_{j+1} = (w - V h) * inv and its complex64 copy (the last pass of an Arnoldi step)
+// V_{j+1} = (w - V (h0 + h)) * inv and its complex64 copy (the last pass of an Arnoldi step; h0 may be null)
 void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V, const float4* h, const float4* w,
-                                 const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s);
+                                 const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s,
+                                 const float4* h0 = nullptr);
 void launch_scale_cast_df(long long n, int items, const float4* w, const float2* inv, float4* out, float2* out32,
                           cudaStream_t s);
 void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s);
@@ -244,8 +246,15 @@ void launch_df_to_d2(long long n, const float4* in, double2* out, cudaStream_t s
 void launch_df_to_f2(long long n, const float4* in, float2* out, cudaStream_t s);
 void launch_coef_df(long long n, const Coef4<double>* in, void* out /*Coef4df*/, cudaStream_t s);
 // y = K x (mode 0) or b - K x (mode 1); x complex64 (x_is_c64) or complex df64
+// Setup-time tables of the 2D operator K (alpha = 0) for launch_fine_apply_df: dg [nsets][2][ncell]
+// complex df64 (the low u_0 / u_1 face-row diagonals), vm [nsets][(nx + 1) (ny + 1)] df64 (vertex
+// means of mu)
+void launch_apply_df_tables(const Grid& g, int nsets, const Coef4<double>* cf, double h, float4* dg, float2* vm,
+                            cudaStream_t s);
+// with dg, vm (2D, alpha = 0) the rows read the tables above
 void launch_fine_apply_df(const Grid& g, int items, int nrhs, const void* cf, double h, double alpha,
-                          const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s);
+                          const void* x, int x_is_c64, const float4* b, float4* y, int mode, cudaStream_t s,
+                          const float4* dg = nullptr, const float2* vm = nullptr);
 void launch_dense_apply_df(int N, int items, int nrhs, const float4* inv, const float2* r, float2* x,
                            cudaStream_t s);
 
