@@ -332,7 +332,8 @@ __device__ __forceinline__ void cell_update(const Tile<W, H>& S, int sx, int sy,
 typedef Tile<SWS_X, SWS_Y> SweepTile;
 typedef Tile<RRS_X, RRS_Y> ResTile;
 
-__global__ void __launch_bounds__(SW_T, 3) k_fine_sweep_tile(Grid g, Grid gc, int nrhs, const float4* __restrict__ cf,
+// 4 CTAs per SM (48 registers; a few bytes of spill) measured faster than 3 (64 registers)
+__global__ void __launch_bounds__(SW_T, 4) k_fine_sweep_tile(Grid g, Grid gc, int nrhs, const float4* __restrict__ cf,
                                                              const float2* __restrict__ tdx,
                                                              const float2* __restrict__ tdy,
                                                              const float2* __restrict__ tsi,
