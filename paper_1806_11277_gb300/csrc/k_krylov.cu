@@ -195,7 +195,7 @@ inline unsigned nb(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 
 int krylov_nblk(long long n) {
   long long b = (n + KB - 1) / KB;
-  if (b > 3 * 152) b = 3 * 152;   // one wave per item at three blocks per SM (measured best of 228..1216)
+  if (b > 2 * 152) b = 2 * 152;   // one wave per item at the reduction passes' 2 CTAs per SM (measured)
   return (int)(b < 1 ? 1 : b);
 }
 

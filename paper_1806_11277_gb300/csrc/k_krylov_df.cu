@@ -644,9 +644,15 @@ void launch_mupdate_df(long long n, int items, int nv, const float4* V, const fl
 void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V, const float4* h, const float4* w,
                                  const float2* inv, float4* out, float2* out32, int nblk, cudaStream_t s,
                                  const float4* h0) {
-  const dim3 g(nblk, sel_items(items));
+  // no block partials here: the grid is sized for this kernel's 3 CTAs per SM (one wave per
+  // item), not by the reduction kernels' nblk
+  (void)nblk;
+  long long gb = (n + KB - 1) / KB;
+  if (gb > 3 * 152) gb = 3 * 152;
+  const int nb3 = (int)(gb < 1 ? 1 : gb);
+  const dim3 g(nb3, sel_items(items));
   switch (nv) {
-#define X(k) case k: k_update_scale_cast_df<k><<<g, KB, 0, s>>>(n, items, V, h0, h, w, inv, out, out32, nblk, g_sel.list); \
+#define X(k) case k: k_update_scale_cast_df<k><<<g, KB, 0, s>>>(n, items, V, h0, h, w, inv, out, out32, nb3, g_sel.list); \
     break;
     EHS_NV_CASES(X)
 #undef X
