@@ -172,6 +172,10 @@ OTHER = {
     "c2p": dict(workload=WORKLOAD + "; MG-DD coarsest solve as one persistent launch (bounded grid barriers "
                 "between the colours' residual and local-product phases) instead of graph-replayed per-colour "
                 "launches", media=lambda: media(), kw=dict(coarse_persist=1), roof="coarse", kernel=ROOF_KERNEL),
+    # the default line with the delayed CGS2 Arnoldi (two passes over the basis per step)
+    "c2d": dict(workload=WORKLOAD + "; delayed CGS2 Arnoldi (the second projection of a direction formed with "
+                "the first projection of the next: two passes over the basis per step instead of three)",
+                media=lambda: media(), kw=dict(ortho=1), roof="coarse", kernel=ROOF_KERNEL),
     # the default line with full cell-block Vanka
     "c2v": dict(workload=WORKLOAD + "; full (2d+1)^2 cell-block Vanka instead of the economic block",
                 media=lambda: media(), kw=dict(vanka_full=1), roof="coarse", kernel=ROOF_KERNEL),

@@ -131,6 +131,7 @@ struct ehs_ctx {
   // df64 Krylov workspace (complex64 preconditioner form)
   float4 *Vq = nullptr, *wq = nullptr, *rq = nullptr, *qq = nullptr, *xq = nullptr, *partq = nullptr;
   float4 *hq = nullptr, *h2q = nullptr, *yq = nullptr;
+  float4* dcoef = nullptr;    // [items][KDS] delayed-CGS2 update coefficients (df64)
   float2 *Zf = nullptr, *npq = nullptr, *invq = nullptr;
   int* kcnt = nullptr;        // [3][items] last-block counters of the fused Krylov reductions
   double2* hhost = nullptr;   // device double copies of h for the host
@@ -141,6 +142,7 @@ struct ehs_ctx {
   int nblk = 1;
   double* hpin = nullptr;    // pinned host scratch
   double2* hstep = nullptr;  // pinned host copies of one Arnoldi step: h1 [items][12], h2 [items][12], norms
+                             // (delayed CGS2: the step's FP64 coefficients, [items][KDS])
   cudaEvent_t ev_step = nullptr;   // recorded after the copies of one Arnoldi step
   // CUDA graphs of the preconditioner application, one per Krylov direction j
   // (the input/output pointers differ per j), captured on a private stream
@@ -710,6 +712,7 @@ void validate(const ehs_problem* P, const ehs_opts* O) {
   if (O->vanka_full != 0 && O->vanka_full != 1) throw ArgError("vanka_full must be 0 or 1");
   if (O->coarse_fmt < 0 || O->coarse_fmt > 3) throw ArgError("coarse_fmt must be 0..3");
   if (O->coarse_persist != 0 && O->coarse_persist != 1) throw ArgError("coarse_persist must be 0 or 1");
+  if (O->ortho != 0 && O->ortho != 1) throw ArgError("ortho must be 0 (CGS2) or 1 (delayed CGS2)");
   for (int k = 0; k < 3; ++k)
     if (O->coarse_dd[k] < 0) throw ArgError("coarse_dd must be >= 0");
   // MG-DD on the global hierarchy: the coarsest grid is known here (DD contexts split the
@@ -826,15 +829,16 @@ struct Arnoldi {
   int items, m, maxit;
   double tol;
   std::vector<zc> H, g, sn;
-  std::vector<double> cs, bnorm, beta;
+  std::vector<zc> Hr;          // unrotated Hessenberg matrix (delayed CGS2 corrects a column later)
+  std::vector<double> cs, bnorm, beta, rho;
   std::vector<int> iters, done, kused, active;
   bool breakdown = false, nonfinite = false;
 
   Arnoldi(int items_, int m_, int maxit_, double tol_)
       : items(items_), m(m_), maxit(maxit_), tol(tol_), H((size_t)items_ * (m_ + 1) * m_),
-        g((size_t)items_ * (m_ + 1)), sn((size_t)items_ * m_), cs((size_t)items_ * m_),
-        bnorm(items_), beta(items_), iters(items_, 0), done(items_, 0), kused(items_, 0),
-        active(items_, 0) {}
+        g((size_t)items_ * (m_ + 1)), sn((size_t)items_ * m_), Hr((size_t)items_ * (m_ + 1) * m_),
+        cs((size_t)items_ * m_), bnorm(items_), beta(items_), rho(items_, 0.0), iters(items_, 0),
+        done(items_, 0), kused(items_, 0), active(items_, 0) {}
 
   void set_b(const double* nrm) {
     for (int b = 0; b < items; ++b) {
@@ -852,12 +856,40 @@ struct Arnoldi {
   }
   void start_cycle() {
     std::fill(H.begin(), H.end(), zc(0));
+    std::fill(Hr.begin(), Hr.end(), zc(0));
     std::fill(g.begin(), g.end(), zc(0));
     for (int b = 0; b < items; ++b) {
       g[(size_t)b * (m + 1)] = beta[b];
       kused[b] = 0;
       active[b] = !done[b] && iters[b] < maxit;
     }
+  }
+  // applies the rotations of columns < j to column j of item b's H, forms the rotation of
+  // column j and applies it to g
+  void rotate(int b, int j) {
+    zc* Hb = &H[(size_t)b * (m + 1) * m];
+    zc* gb = &g[(size_t)b * (m + 1)];
+    for (int i = 0; i < j; ++i) {
+      const zc t = cs[b * m + i] * Hb[i * m + j] + sn[b * m + i] * Hb[(i + 1) * m + j];
+      Hb[(i + 1) * m + j] = -std::conj(sn[b * m + i]) * Hb[i * m + j] + cs[b * m + i] * Hb[(i + 1) * m + j];
+      Hb[i * m + j] = t;
+    }
+    zc rr;
+    givens(Hb[j * m + j], Hb[(j + 1) * m + j], &cs[b * m + j], &sn[b * m + j], &rr);
+    Hb[j * m + j] = rr;
+    Hb[(j + 1) * m + j] = 0.0;
+    gb[j + 1] = -std::conj(sn[b * m + j]) * gb[j];
+    gb[j] = cs[b * m + j] * gb[j];
+  }
+  // counts step j of item b and tests its residual estimate; false once the item stops
+  bool count(int b, int j, double hn) {
+    iters[b] += 1;
+    kused[b] = j + 1;
+    const double res = std::abs(g[(size_t)b * (m + 1) + j + 1]) / bnorm[b];
+    if (!std::isfinite(res)) { nonfinite = true; active[b] = 0; return false; }
+    if (hn == 0.0) { active[b] = 0; if (res > tol) breakdown = true; return false; }
+    if (res <= tol || iters[b] >= maxit) { active[b] = 0; return false; }
+    return true;
   }
   // column j of H from h = h1 + h2 ([items][j+1]) and hn; true if an item is still active
   bool step(int j, const double2* h1, const double2* h2, const double* hn) {
@@ -866,28 +898,42 @@ struct Arnoldi {
     for (int b = 0; b < items; ++b) {
       if (!active[b]) continue;
       zc* Hb = &H[(size_t)b * (m + 1) * m];
-      zc* gb = &g[(size_t)b * (m + 1)];
       for (int i = 0; i < nv; ++i)
         Hb[i * m + j] = zc(h1[b * nv + i].x + h2[b * nv + i].x, h1[b * nv + i].y + h2[b * nv + i].y);
       Hb[(j + 1) * m + j] = hn[b];
-      for (int i = 0; i < j; ++i) {
-        const zc t = cs[b * m + i] * Hb[i * m + j] + sn[b * m + i] * Hb[(i + 1) * m + j];
-        Hb[(i + 1) * m + j] = -std::conj(sn[b * m + i]) * Hb[i * m + j] + cs[b * m + i] * Hb[(i + 1) * m + j];
-        Hb[i * m + j] = t;
+      rotate(b, j);
+      any = count(b, j, hn[b]) || any;
+    }
+    return any;
+  }
+  // Delayed CGS2: p[b * stride ...] = a_0..a_{j-1}, sigma, b_0..b_{j-1}, h_j, rho of step j.
+  // Corrects column j - 1 of the unrotated matrix Hr (u_j = V_j a + sigma v_j, so its
+  // column gains rho_{j-1} a above the diagonal and its subdiagonal becomes
+  // rho_{j-1} sigma), sets column j to (b, h_j, rho), and redoes the Givens QR of
+  // columns 0..j from Hr (column j - 1 changed after its rotation was formed).
+  bool step_delayed(int j, const double2* p, int stride) {
+    bool any = false;
+    for (int b = 0; b < items; ++b) {
+      if (!active[b]) continue;
+      const double2* pa = p + (size_t)b * stride;
+      const double2* pb = pa + j + 1;
+      zc* R = &Hr[(size_t)b * (m + 1) * m];
+      if (j > 0) {
+        for (int i = 0; i < j; ++i) R[i * m + j - 1] += rho[b] * zc(pa[i].x, pa[i].y);
+        R[j * m + j - 1] = rho[b] * pa[j].x;
       }
-      zc rr;
-      givens(Hb[j * m + j], Hb[(j + 1) * m + j], &cs[b * m + j], &sn[b * m + j], &rr);
-      Hb[j * m + j] = rr;
-      Hb[(j + 1) * m + j] = 0.0;
-      gb[j + 1] = -std::conj(sn[b * m + j]) * gb[j];
-      gb[j] = cs[b * m + j] * gb[j];
-      iters[b] += 1;
-      kused[b] = j + 1;
-      const double res = std::abs(gb[j + 1]) / bnorm[b];
-      if (!std::isfinite(res)) { nonfinite = true; active[b] = 0; continue; }
-      if (hn[b] == 0.0) { active[b] = 0; if (res > tol) breakdown = true; continue; }
-      if (res <= tol || iters[b] >= maxit) { active[b] = 0; continue; }
-      any = true;
+      for (int i = 0; i <= j; ++i) R[i * m + j] = zc(pb[i].x, pb[i].y);
+      R[(j + 1) * m + j] = pb[j + 1].x;
+      rho[b] = pb[j + 1].x;
+      zc* Hb = &H[(size_t)b * (m + 1) * m];
+      zc* gb = &g[(size_t)b * (m + 1)];
+      std::fill(gb, gb + m + 1, zc(0));
+      gb[0] = beta[b];
+      for (int l = 0; l <= j; ++l) {
+        for (int i = 0; i <= l + 1; ++i) Hb[i * m + l] = R[i * m + l];
+        rotate(b, l);
+      }
+      any = count(b, j, rho[b]) || any;
     }
     return any;
   }
@@ -1058,6 +1104,19 @@ ehs_status fgmres_df(ehs_ctx* c, const double2* q, double2* u, ehs_solve_info* i
       });
       launch_fine_apply_df(c->H.g0, items, c->H.nrhs, c->H.cfdf, c->H.h, 0.0, Zj, 1, nullptr, c->wq, 0, s, c->H.kdg,
                            c->H.kvm);
+      if (c->opt.ortho == 1) {
+        // delayed CGS2: one pass for V^H u_j, V^H w and the norms, whose last block forms the
+        // coefficients; one pass for v_j and u_{j+1} (and its complex64 copy in f_in)
+        launch_mdot2_df(n, items, j, c->Vq, c->wq, c->partq, nblk, s, c->kcnt, c->dcoef, c->hhost);
+        CK(cudaMemcpyAsync(c->hstep, c->hhost, (size_t)items * KDS * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(c->ev_step, s));
+        launch_dupdate_df(n, items, j, c->Vq, c->wq, c->dcoef, c->f_in, s);
+        cnt(3); post();                      // with the operator launch above
+        CK(cudaEventSynchronize(c->ev_step));
+        if (!A.step_delayed(j, c->hstep, KDS)) break;
+        set_active(c, A.active);
+        continue;
+      }
       // CGS2: h1 = V^H w; w' = w - V h1 (not stored) with h2 = V^H w' and ||w'||^2 in the same
       // pass, whose last block also forms ||w' - V h2|| = sqrt(||w'||^2 - ||h2||^2); then one pass
       // forms V_{j+1} = (w - V (h1 + h2)) / ||.|| and its complex64 copy.  Each reduction is done
@@ -1273,13 +1332,14 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
       c->rq = dalloc<float4>(c, (size_t)items * n);
       c->qq = dalloc<float4>(c, (size_t)items * n);
       c->xq = dalloc<float4>(c, (size_t)items * n);
-      c->partq = dalloc<float4>(c, (size_t)items * 12 * c->nblk);
+      c->partq = dalloc<float4>(c, (size_t)items * 24 * c->nblk);   // 2 x 12 sums per item (delayed CGS2)
+      c->dcoef = dalloc<float4>(c, (size_t)items * KDS);
       c->hq = dalloc<float4>(c, (size_t)items * 12);
       c->h2q = dalloc<float4>(c, (size_t)items * 12);
       c->yq = dalloc<float4>(c, (size_t)items * 12);
       c->npq = dalloc<float2>(c, (size_t)items * c->nblk);
       c->invq = dalloc<float2>(c, items);
-      c->hhost = dalloc<double2>(c, (size_t)items * 24);
+      c->hhost = dalloc<double2>(c, (size_t)items * 24);            // >= KDS per item
       c->kcnt = dalloc<int>(c, (size_t)items * 3);
     }
     CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));

@@ -303,6 +303,168 @@ __global__ void __launch_bounds__(KB, 3) k_update_scale_cast_df(long long n, int
   }
 }
 
+// ---- delayed CGS2 (one dot pass and one update pass per Arnoldi step) --------
+// Step j starts with v_0..v_{j-1} orthonormal and, in slot j, u_j: the direction the
+// preconditioner was applied to, orthogonalised once and scaled by the norm that
+// assumed the first pass exact.  With z_j = M^{-1} u_j and w = K z_j, one pass over
+// the basis gives a = V^H u_j, b = V^H w, u_j^H w, ||u_j||^2 and ||w||^2; from them
+//   v_j     = (u_j - V a) / sigma,          sigma = sqrt(||u_j||^2 - ||a||^2),
+//   h_j     = v_j^H w = (u_j^H w - a^H b) / sigma,
+//   u_{j+1} = (w - V b - v_j h_j) / rho,    rho = sqrt(||w||^2 - ||b||^2 - |h_j|^2),
+// the second pass of Gram-Schmidt for u_j riding on the first pass for w.  Column j
+// of the Hessenberg matrix is (b, h_j, rho); the next step replaces its
+// subdiagonal by rho * sigma_{j+1} and adds rho * a_{j+1} above it (K z_j = w and
+// rho u_{j+1} = V_{j+1} a_{j+1} + rho sigma_{j+1} v_{j+1}).  In exact arithmetic
+// the basis and the Hessenberg matrix are those of CGS2; the preconditioner sees
+// u_j instead of v_j, which flexible GMRES allows (its space is spanned by the z_j
+// actually formed).
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zcmul(double2 a, double2 b) {   // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// First pass of step j = NS - 1 (slots 0..j of V, slot j holding u_j).  Blocks
+// 2k and 2k + 1 of an item cover the same elements: the even block forms
+// conj(V_i) u_j for i <= j (i = j: ||u_j||^2), the odd one conj(V_i) w (i = j:
+// u_j^H w) and ||w||^2; running side by side, the second read of the basis is an
+// L2 hit.  The last block of the item sums the partials (fixed order, as
+// reduce_dots_last) and forms the update coefficients in FP64:
+//   coef[item * KDS + ...]  (df64)  a_0..a_{j-1}, b_i - a_i h_j / sigma (i < j),
+//                                   h_j / sigma, 1 / sigma, 1 / rho
+//   outd[item * KDS + ...]  (FP64)  a_0..a_{j-1}, sigma, b_0..b_{j-1}, h_j, rho
+// (sigma = 1 and no a at j = 0: u_0 = r / ||r|| is normalised by the norm pass).
+template <int NS>
+__global__ void __launch_bounds__(KB, 2) k_mdot2_df(long long n, int items, const float4* __restrict__ V,
+                                                 const float4* __restrict__ w, float4* part, int nblk,
+                                                 const int* __restrict__ il, int* cnt, float4* coef, double2* outd) {
+  constexpr int NO = NS + 1;   // NS dots and one norm per half
+  static_assert(NO <= MAXV, "sums per half");
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  const int half = blockIdx.x & 1, blk = blockIdx.x >> 1;
+  const float4* xv = half ? w + (long long)item * n : V + ((long long)(NS - 1) * items + item) * n;
+  dacc2 acc[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) acc[i] = dacc2_zero();
+  dacc nacc = dacc_zero();
+  for (long long e = (long long)blk * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+    dfc vv[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
+    const dfc xe = half ? dfc_ld(xv + e) : vv[NS - 1];
+    const float2 wah = make_float2(xe.re.hi, -xe.re.hi), wal = make_float2(xe.re.lo, -xe.re.lo);
+    const float2 wbh = make_float2(xe.im.hi, xe.im.hi), wbl = make_float2(xe.im.lo, xe.im.lo);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) dacc2_cfma(acc[i], dfc2_of(vv[i]), wah, wal, wbh, wbl);
+    if (half) {
+      dacc_fma(nacc, xe.re, xe.re);
+      dacc_fma(nacc, xe.im, xe.im);
+    }
+  }
+  dfc vals[NO];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) vals[i] = dacc2_val(acc[i]);
+  vals[NS] = {dacc_val(nacc), df_zero()};
+  block_store_df<NO>(vals, part, item, 2 * nblk);
+  if (!cnt || !last_block(cnt, item, 2 * nblk)) return;
+  __shared__ double2 sd[2 * NO];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = wid; o < 2 * NO; o += KB / 32) {
+    const int hf = o / NO, oo = o - hf * NO;
+    const float4* p = part + ((long long)item * NO + oo) * (2 * nblk) + hf;
+    dfc s = dfc_zero();
+    for (int b = lane; b < nblk; b += 32) {
+      const float4 v = __ldcg(p + 2 * b);
+      s = dfc_add(s, dfc{{v.x, v.z}, {v.y, v.w}});   // the storage order of dfc_st
+    }
+    s = warp_sum_df(s);
+    if (lane == 0) sd[o] = dfc_to_d2(s);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  constexpr int j = NS - 1;
+  const double2* A = sd;        // A[i] = V_i^H u_j (i < j), A[j].x = ||u_j||^2
+  const double2* B = sd + NO;   // B[i] = V_i^H w (i < j), B[j] = u_j^H w, B[NS].x = ||w||^2
+  double sig = 1.0;
+  if (j > 0) {
+    double s2 = A[j].x;
+    for (int i = 0; i < j; ++i) s2 -= A[i].x * A[i].x + A[i].y * A[i].y;
+    sig = s2 > 0.0 ? sqrt(s2) : 0.0;
+  }
+  const double isig = sig > 0.0 ? 1.0 / sig : 0.0;
+  double2 hj = B[j];
+  for (int i = 0; i < j; ++i) {
+    const double2 t = zcmul(A[i], B[i]);
+    hj.x -= t.x;
+    hj.y -= t.y;
+  }
+  hj.x *= isig;
+  hj.y *= isig;
+  double r2 = B[NS].x - (hj.x * hj.x + hj.y * hj.y);
+  for (int i = 0; i < j; ++i) r2 -= B[i].x * B[i].x + B[i].y * B[i].y;
+  const double rho = r2 > 0.0 ? sqrt(r2) : 0.0;
+  const double2 cu = make_double2(hj.x * isig, hj.y * isig);
+  float4* cf = coef + (long long)item * KDS;
+  double2* od = outd + (long long)item * KDS;
+  for (int i = 0; i < j; ++i) {
+    const double2 t = zmul(A[i], cu);
+    dfc_st(cf + i, dfc_from_d2(A[i]));
+    dfc_st(cf + j + i, dfc_from_d2(make_double2(B[i].x - t.x, B[i].y - t.y)));
+    od[i] = A[i];
+    od[j + 1 + i] = B[i];
+  }
+  dfc_st(cf + 2 * j, dfc_from_d2(cu));
+  dfc_st(cf + 2 * j + 1, dfc_from_d2(make_double2(isig, 0.0)));
+  dfc_st(cf + 2 * j + 2, dfc_from_d2(make_double2(rho > 0.0 ? 1.0 / rho : 0.0, 0.0)));
+  od[j] = make_double2(sig, 0.0);
+  od[2 * j + 1] = hj;
+  od[2 * j + 2] = make_double2(rho, 0.0);
+  cnt[item] = 0;
+}
+
+// Second pass of step j = NJ: v_j = (u_j - sum_i V_i a_i) / sigma over slot j and
+// u_{j+1} = (w - sum_i V_i c_i - u_j h_j / sigma) / rho into slot j + 1 with its
+// complex64 copy (the next preconditioner input), c_i = b_i - a_i h_j / sigma;
+// coefficients as k_mdot2_df stores them.  Slots below j are only read.
+template <int NJ>
+__global__ void __launch_bounds__(KB, 3) k_dupdate_df(long long n, int items, const float4* V, float4* vj,
+                                                   float4* vn, const float4* __restrict__ w,
+                                                   const float4* __restrict__ coef, float2* __restrict__ out32,
+                                                   const int* __restrict__ il) {
+  const int item = il ? il[blockIdx.y] : blockIdx.y;
+  constexpr int NC = 2 * NJ + 3;
+  static_assert(NC <= KDS, "coefficients per item");
+  __shared__ float4 cs[NC];
+  if (threadIdx.x < NC) cs[threadIdx.x] = coef[(long long)item * KDS + threadIdx.x];
+  __syncthreads();
+  const float4 s4 = cs[2 * NJ + 1], r4 = cs[2 * NJ + 2];
+  const dfr isig = {s4.x, s4.z}, irho = {r4.x, r4.z};
+  const float4 u4 = cs[2 * NJ];
+  const dfc cu = {{u4.x, u4.z}, {u4.y, u4.w}};
+  const long long off = (long long)item * n;
+  const float4* wv = w + off;
+  float4* uv = vj + off;
+  float4* nv = vn + off;
+  for (long long e = (long long)blockIdx.x * KB + threadIdx.x; e < n; e += (long long)gridDim.x * KB) {
+    dcacc sv = dcacc_zero(), sw = dcacc_zero();
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) {
+      const dfc vi = dfc_ld(V + ((long long)i * items + item) * n + e);
+      const float4 a = cs[i], c = cs[NJ + i];   // the storage order of dfc_st
+      dcacc_fma(sv, vi, dfc{{a.x, a.z}, {a.y, a.w}});
+      dcacc_fma(sw, vi, dfc{{c.x, c.z}, {c.y, c.w}});
+    }
+    const dfc u = dfc_ldv(uv + e);      // rewritten below by this thread only
+    dcacc_fma(sw, u, cu);
+    if (NJ > 0) dfc_st(uv + e, dfc_scale(dfc_sub(u, dcacc_val(sv)), isig));
+    const dfc x = dfc_scale(dfc_sub(dfc_ld(wv + e), dcacc_val(sw)), irho);
+    dfc_st(nv + e, x);
+    out32[off + e] = dfc_to_f2(x);
+  }
+}
+
 __global__ void k_norm_part_df(long long n, const float4* __restrict__ w, float2* part, int nblk, const int* __restrict__ il) {
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   const float4* wv = w + (long long)item * n;
@@ -655,6 +817,30 @@ void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V
 #define X(k) case k: k_update_scale_cast_df<k><<<g, KB, 0, s>>>(n, items, V, h0, h, w, inv, out, out32, nb3, g_sel.list); \
     break;
     EHS_NV_CASES(X)
+#undef X
+    default: break;
+  }
+}
+void launch_mdot2_df(long long n, int items, int j, const float4* V, const float4* w, float4* part, int nblk,
+                     cudaStream_t s, int* cnt, float4* coef, double2* outd) {
+  const dim3 g(2 * nblk, sel_items(items));
+  switch (j + 1) {
+#define X(k) case k: k_mdot2_df<k><<<g, KB, 0, s>>>(n, items, V, w, part, nblk, g_sel.list, cnt, coef, outd); break;
+    EHS_NV_CASES(X)
+#undef X
+    default: break;
+  }
+}
+void launch_dupdate_df(long long n, int items, int j, float4* V, const float4* w, const float4* coef,
+                       float2* out32, cudaStream_t s) {
+  long long gb = (n + KB - 1) / KB;   // as launch_update_scale_cast_df: 3 CTAs per SM, one wave per item
+  if (gb > 3 * 152) gb = 3 * 152;
+  const dim3 g((unsigned)(gb < 1 ? 1 : gb), sel_items(items));
+  float4* vj = V + (size_t)j * items * n;
+  float4* vn = V + (size_t)(j + 1) * items * n;
+  switch (j) {
+#define X(k) case k: k_dupdate_df<k><<<g, KB, 0, s>>>(n, items, V, vj, vn, w, coef, out32, g_sel.list); break;
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)   // j <= 10: 2 j + 3 <= KDS
 #undef X
     default: break;
   }

@@ -232,6 +232,18 @@ void launch_update_scale_cast_df(long long n, int items, int nv, const float4* V
                                  const float4* h0 = nullptr);
 void launch_scale_cast_df(long long n, int items, const float4* w, const float2* inv, float4* out, float2* out32,
                           cudaStream_t s);
+// Delayed CGS2 (one dot pass and one update pass per Arnoldi step j; slot j of V holds u_j,
+// the direction the preconditioner was applied to).  launch_mdot2_df forms, with its last block
+// per item (cnt: device counters [items], zero, reset by the kernel), the FP64 coefficients:
+// coef[item * KDS ...] (df64) for launch_dupdate_df and outd[item * KDS ...] (double, for the
+// host) = a_0..a_{j-1}, sigma, b_0..b_{j-1}, h_j, rho; part: [items][2][j + 2][nblk] partials.
+// launch_dupdate_df rewrites slot j as v_j and writes u_{j+1} into slot j + 1 and its complex64
+// copy into out32.
+constexpr int KDS = 24;   // per-item stride of those arrays (2 j + 3 <= 23 for j <= 10)
+void launch_mdot2_df(long long n, int items, int j, const float4* V, const float4* w, float4* part, int nblk,
+                     cudaStream_t s, int* cnt, float4* coef, double2* outd);
+void launch_dupdate_df(long long n, int items, int j, float4* V, const float4* w, const float4* coef,
+                       float2* out32, cudaStream_t s);
 void launch_norm_part_df(long long n, int items, const float4* w, float2* part, int nblk, cudaStream_t s);
 // out (df64, device use) and outd (double copy for the host)
 void launch_reduce_parts_df(int items, int nv, int nblk, const float4* part, float4* out, double2* outd,

@@ -40,7 +40,8 @@ class Opts(C.Structure):
                 ("coarse_dd", C.c_int * 3),
                 ("coarse_dd_overlap", C.c_int),
                 ("coarse_fmt", C.c_int),
-                ("coarse_persist", C.c_int)]
+                ("coarse_persist", C.c_int),
+                ("ortho", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -67,7 +67,7 @@ def test_create_rejects_bad_arguments_before_any_launch(lib_path):
                                              ("cycle", 3, "cycle"), ("coef_half", 3, "coef_half"),
                                              ("vanka_full", 2, "vanka_full"), ("coarse_fmt", 7, "coarse_fmt"),
                                              ("prec", 5, "prec"), ("tol", 0.0, "tol"),
-                                             ("coarse_persist", 2, "coarse_persist")])
+                                             ("coarse_persist", 2, "coarse_persist"), ("ortho", 2, "ortho")])
 def test_create_rejects_bad_options_before_any_device_work(lib_path, field, value, msg):
     """ehs_create validates its arguments on the host first: a bad option is
     EHS_ERR_ARG with a message, whether or not a GPU is present."""

@@ -28,12 +28,15 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def test_bench_workload_iterations_and_residuals():
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_bench_workload_iterations_and_residuals(ortho):
+    """The bench workload with either Arnoldi orthogonalisation of the double-float
+    solve (CGS2, delayed CGS2)."""
     import bench
     from paper_1806_11277_gb300 import ehs
     gold = json.load(open(os.path.join(HERE, "golden", "c2_oracle_iters.json")))
     smp = json.load(open(os.path.join(HERE, "golden", "c2_oracle_samples.json")))["media"]
-    kw = bench.default_kw()
+    kw = dict(bench.default_kw(), ortho=ortho)
     assert gold["levels"] == kw["levels"] and gold["alpha"] == kw["alpha"] and gold["w"] == kw["w"]
     assert gold["cycle"] == ("W(1,1)" if kw["cycle"] == 2 else "V(1,1)")
     assert tuple(gold["coarse_dd"]) == tuple(kw["coarse_dd"][:2])

@@ -225,17 +225,20 @@ def _solve_both(meds, levels, prec, nrhs=1, host=False, **kw):
     return q, u, info
 
 
-@pytest.mark.parametrize("prec_name", ["c128", "c64"])
-def test_fgmres_matches_oracle_2d(prec_name):
+@pytest.mark.parametrize("prec_name,ortho,restart", [("c128", 0, 10), ("c64", 0, 10), ("c64", 1, 10), ("c64", 1, 3)])
+def test_fgmres_matches_oracle_2d(prec_name, ortho, restart):
+    """Four media in one batch against the oracle's FGMRES(restart); the double-float
+    solve with CGS2 (ortho 0) or delayed CGS2 (ortho 1), which the oracle's CGS2
+    equals in exact arithmetic; restart 3 runs several restart cycles."""
     ehs = _ehs()
     prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
     meds = _media_2d(64, 4)
-    q, u, info = _solve_both(meds, 3, prec)
+    q, u, info = _solve_both(meds, 3, prec, ortho=ortho, restart=restart)
     for it, med in enumerate(meds):
         K = _oracle_parts(med)
         H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, 3)
         qo = op.slots_to_dofs(q[it], med.shape)
-        xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+        xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=restart)
         ug = op.slots_to_dofs(u[it], med.shape)
         res = np.linalg.norm(qo - K @ ug) / np.linalg.norm(qo)
         assert info[it]["converged"] and res <= 1e-6
@@ -263,13 +266,15 @@ def test_fgmres_config1_host_buffers():
     assert _err(ug, xe) <= 1e-5
 
 
-def test_fgmres_multi_rhs_3d():
-    """Two sources of one 3D medium in one batch (complex64 cycle): each source's
-    iteration count within 1 of the oracle's, its true residual <= 1e-6 and its
-    solution within 1e-5 of the oracle's, element by element."""
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_fgmres_multi_rhs_3d(ortho):
+    """Two sources of one 3D medium in one batch (complex64 cycle; CGS2 or delayed
+    CGS2): each source's iteration count within 1 of the oracle's, its true
+    residual <= 1e-6 and its solution within 1e-5 of the oracle's, element by
+    element."""
     ehs = _ehs()
     meds = _media_3d(16, 1)
-    q, u, info = _solve_both(meds, 3, ehs.EHS_C64, nrhs=2)
+    q, u, info = _solve_both(meds, 3, ehs.EHS_C64, nrhs=2, ortho=ortho)
     K = _oracle_parts(meds[0])
     H = mg.Hierarchy(_oracle_parts(meds[0], 0.2), meds[0].shape, 3)
     for it in range(2):
@@ -344,10 +349,11 @@ def test_invalid_arguments_rejected():
         ehs.solver_for(bad, levels=3)
 
 
-def test_noconv_reports_best_iterate():
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_noconv_reports_best_iterate(ortho):
     ehs = _ehs()
     med = synth.homogeneous_2d()
-    S = ehs.solver_for(med, levels=3, maxit=3)
+    S = ehs.solver_for(med, levels=3, maxit=3, ortho=ortho)
     q = synth.point_rhs(med.shape, med.sources)[0][None]
     qd = torch.from_numpy(q).cuda()
     ud = torch.zeros_like(qd)
@@ -391,13 +397,14 @@ def test_fgmres_wcycle_iterations_match_oracle():
         assert _err(ug, xo) <= 1e-5
 
 
-def test_dd_fgmres_batched_media_compaction():
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_dd_fgmres_batched_media_compaction(ortho):
     """Two media converging at different iteration counts in one DD-MG batch:
     each item's count and solution must equal its own oracle solve."""
     ehs = _ehs()
     meds = _media_2d(64, 2)
     q, u, info = _solve_both(meds, 3, ehs.EHS_C64, precond=ehs.EHS_PRECOND_DD, dd=(2, 2, 1),
-                             dd_overlap=4, dd_pad=8)
+                             dd_overlap=4, dd_pad=8, ortho=ortho)
     for it, med in enumerate(meds):
         D = odd.DD(med, (2, 2), 4, 8, 3, 0.2)
         qo = op.slots_to_dofs(q[it], med.shape)
@@ -591,17 +598,20 @@ def test_mgdd_cycle_matches_oracle(case, cyc):
     S.close()
 
 
-@pytest.mark.parametrize("prec_name,fmt,persist", [("c128", 0, 0), ("c64", 0, 0), ("c64", 1, 0), ("c64", 2, 0),
-                                                   ("c64", 3, 0), ("c64", 1, 1), ("c64", 2, 1), ("c64", 3, 1)])
-def test_mgdd_fgmres_matches_oracle(prec_name, fmt, persist):
+@pytest.mark.parametrize("prec_name,fmt,persist,ortho", [("c128", 0, 0, 0), ("c64", 0, 0, 0), ("c64", 1, 0, 0),
+                                                         ("c64", 2, 0, 0), ("c64", 3, 0, 0), ("c64", 1, 1, 0),
+                                                         ("c64", 2, 1, 0), ("c64", 3, 1, 0), ("c64", 0, 0, 1),
+                                                         ("c64", 2, 0, 1)])
+def test_mgdd_fgmres_matches_oracle(prec_name, fmt, persist, ortho):
     """MG-DD inside FGMRES; the local inverses in double-float, complex64, FP16 or
     BF16 storage (FP32 accumulation) for the complex64 cycle; with persist the
-    complex64 coarsest solve runs as one persistent launch (opts.coarse_persist)."""
+    complex64 coarsest solve runs as one persistent launch (opts.coarse_persist); with
+    ortho the double-float solve uses delayed CGS2."""
     ehs = _ehs()
     prec = ehs.EHS_C128 if prec_name == "c128" else ehs.EHS_C64
     meds = _media_2d(64, 2)
     q, u, info = _solve_both(meds, 3, prec, alpha=0.4, cycle=2, coarse_dd=(2, 2, 1), coarse_dd_overlap=2,
-                             coarse_fmt=fmt, coarse_persist=persist)
+                             coarse_fmt=fmt, coarse_persist=persist, ortho=ortho)
     for it, med in enumerate(meds):
         K = _oracle_parts(med)
         H = mg.Hierarchy(_oracle_parts(med, 0.4), med.shape, 3, w=[0.75, 0.5], coarse_dd=((2, 2), 2))
