@@ -5,8 +5,8 @@ random fields, correlation 20 cells, Vp in [1.5, 4.5], rho in [1, 2.5]) with
 Poisson ratios 0.25 / 0.4 / 0.45 / 0.49, 8 points per shortest S-wavelength,
 20-cell absorbing layer, one x-force each; an MG-DD preconditioner (a
 complex64 3-level V-cycle whose coarsest grid is solved by one DD sweep over
-8 x 8 subdomains) inside an FP64-class (double-float) FGMRES(10) to 1e-6
-relative residual.  The four media are one batched context, so one step is
+8 x 8 subdomains) inside an FP64-class (double-float) FGMRES(10) with
+delayed CGS2 to 1e-6 relative residual.  The four media are one batched context, so one step is
 four solves.
 
 Timing: W warm-up steps, then K steps timed with CUDA events on the solver's
@@ -53,17 +53,18 @@ COARSE_DD = (8, 8, 1)
 COARSE_OVERLAP = 3
 COARSE_FMT = 2                     # FP16 pairs
 COEF_HALF = 1                      # FP16 pairs
+ORTHO = 1                          # delayed CGS2 Arnoldi
 WORKLOAD = ("2D heterogeneous media 512x512 (GRF corr 20, Vp 1.5-4.5, rho 1-2.5), Poisson "
             "0.25/0.4/0.45/0.49, 8 points per S-wavelength, 20-cell ABL; MG-DD preconditioner: complex64 "
             f"V(1,1) cycle ({LEVELS} levels, alpha {ALPHA}), coarsest 128x128 grid solved by one DD sweep over "
             f"8x8 subdomains (overlap {COARSE_OVERLAP}, dense local inverses), FP16 Galerkin tables and local "
-            "inverses; FP64-class (double-float) FGMRES(10) to 1e-6")
+            "inverses; FP64-class (double-float) FGMRES(10) with delayed CGS2 to 1e-6")
 
 
 def default_kw():
     """Solver options of the default 512x512 line (the C ABI's ehs_opts fields)."""
     return dict(levels=LEVELS, alpha=ALPHA, w=list(W_LEVELS), prec=1, cycle=CYCLE, coarse_dd=COARSE_DD,
-                coarse_dd_overlap=COARSE_OVERLAP, coarse_fmt=COARSE_FMT, coef_half=COEF_HALF)
+                coarse_dd_overlap=COARSE_OVERLAP, coarse_fmt=COARSE_FMT, coef_half=COEF_HALF, ortho=ORTHO)
 
 
 # Roofline kernel of the default line: the MG-DD coarsest local products with the scatter-add
@@ -172,10 +173,10 @@ OTHER = {
     "c2p": dict(workload=WORKLOAD + "; MG-DD coarsest solve as one persistent launch (bounded grid barriers "
                 "between the colours' residual and local-product phases) instead of graph-replayed per-colour "
                 "launches", media=lambda: media(), kw=dict(coarse_persist=1), roof="coarse", kernel=ROOF_KERNEL),
-    # the default line with the delayed CGS2 Arnoldi (two passes over the basis per step)
-    "c2d": dict(workload=WORKLOAD + "; delayed CGS2 Arnoldi (the second projection of a direction formed with "
-                "the first projection of the next: two passes over the basis per step instead of three)",
-                media=lambda: media(), kw=dict(ortho=1), roof="coarse", kernel=ROOF_KERNEL),
+    # the default line with the three-pass CGS2 Arnoldi instead of delayed CGS2
+    "c2cgs2": dict(workload=WORKLOAD.replace("with delayed CGS2", "with CGS2 (three passes over the basis per "
+                                            "Arnoldi step instead of two)"),
+                   media=lambda: media(), kw=dict(ortho=0), roof="coarse", kernel=ROOF_KERNEL),
     # the default line with full cell-block Vanka
     "c2v": dict(workload=WORKLOAD + "; full (2d+1)^2 cell-block Vanka instead of the economic block",
                 media=lambda: media(), kw=dict(vanka_full=1), roof="coarse", kernel=ROOF_KERNEL),
@@ -807,7 +808,8 @@ def run_gpu(args):
                    "sigmas": list(SIGMAS) if cfg is None else None, "levels": kw["levels"],
                    "alpha": kw["alpha"], "cycle": "W(1,1)" if kw["cycle"] == 2 else "V(1,1)",
                    "krylov": "FGMRES(10), " + ("double-float (FP64-class)" if kw["prec"] == 1 else "FP64")
-                   + " vectors and operator", "precond_dtype": "complex64" if kw["prec"] == 1 else "complex128",
+                   + " vectors and operator, " + ("delayed CGS2" if kw["prec"] == 1 and kw.get("ortho", 1)
+                                                  else "CGS2"), "precond_dtype": "complex64" if kw["prec"] == 1 else "complex128",
                    "coarsest": ("MG-DD %s subdomains, overlap %d" % ("x".join(map(str, kw["coarse_dd"][:2])),
                                                                    kw.get("coarse_dd_overlap", 2))
                                 if max(kw.get("coarse_dd", (1,))) > 1 else "exact dense inverse"),

@@ -134,7 +134,7 @@ typedef struct {
   int ortho;             /* Arnoldi orthogonalisation of the double-float solve (prec = EHS_C64; the
                             FP64 form always uses CGS2).  0: CGS2, three passes over the basis per
                             step (first projection, second projection with the norm, update).
-                            1: delayed CGS2, two passes per step: the second projection of a
+                            1 (the default): delayed CGS2, two passes per step: the second projection of a
                             direction is formed together with the first projection of the next
                             one (the preconditioner is applied to the once-orthogonalised
                             direction, which flexible GMRES allows); the same basis and

@@ -1247,6 +1247,7 @@ void ehs_default_opts(ehs_opts* o) {
   o->dd_abl_max = 1.0;
   o->coarse_dd[0] = o->coarse_dd[1] = o->coarse_dd[2] = 1;
   o->coarse_dd_overlap = 2;
+  o->ortho = 1;
 }
 
 ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* stream, ehs_ctx** out) {

@@ -47,6 +47,7 @@ def test_binding_loads_and_matches_header(lib_path):
     o = ehs.default_opts()
     assert o.levels == 3 and abs(o.alpha - 0.2) < 1e-15 and o.restart == 10
     assert abs(o.w[0] - 0.75) < 1e-15 and abs(o.w[1] - 0.5) < 1e-15 and abs(o.tol - 1e-6) < 1e-20
+    assert o.ortho == 1 and o.coarse_persist == 0
     assert lib.ehs_kernel_launches() >= 0
 
 
