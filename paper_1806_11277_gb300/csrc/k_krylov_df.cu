@@ -328,10 +328,16 @@ __device__ __forceinline__ double2 zcmul(double2 a, double2 b) {   // conj(a) * 
 
 // First pass of step j = NS - 1 (slots 0..j of V, slot j holding u_j).  Blocks
 // 2k and 2k + 1 of an item cover the same elements: the even block forms
-// conj(V_i) u_j for i <= j (i = j: ||u_j||^2), the odd one conj(V_i) w (i = j:
-// u_j^H w) and ||w||^2; running side by side, the second read of the basis is an
-// L2 hit.  The last block of the item sums the partials (fixed order, as
-// reduce_dots_last) and forms the update coefficients in FP64:
+// conj(V_i) u_j for i <= j (i = j: ||u_j||^2) as compensated Dot2 sums, the odd
+// one conj(V_i) w (i = j: u_j^H w) and ||w||^2 from FP32 products of the high
+// parts; running side by side, the second read of the basis is an L2 hit.  Only
+// the second projection (a, sigma) has to be exact to double-float: b, u_j^H w
+// and ||w||^2 fix what the update subtracts from w, the Hessenberg column records
+// exactly that, and the next step's a measures (and its update removes) whatever
+// their rounding left along the basis, as the second pass of CGS2 does for the
+// first; rho only scales u_{j+1} (sigma of the next step measures its norm) and
+// the step's residual estimate.  The last block of the item sums the partials
+// (fixed order, as reduce_dots_last) and forms the update coefficients in FP64:
 //   coef[item * KDS + ...]  (df64)  a_0..a_{j-1}, b_i - a_i h_j / sigma (i < j),
 //                                   h_j / sigma, 1 / sigma, 1 / rho
 //   outd[item * KDS + ...]  (FP64)  a_0..a_{j-1}, sigma, b_0..b_{j-1}, h_j, rho
@@ -344,29 +350,47 @@ __global__ void __launch_bounds__(KB, 2) k_mdot2_df(long long n, int items, cons
   static_assert(NO <= MAXV, "sums per half");
   const int item = il ? il[blockIdx.y] : blockIdx.y;
   const int half = blockIdx.x & 1, blk = blockIdx.x >> 1;
-  const float4* xv = half ? w + (long long)item * n : V + ((long long)(NS - 1) * items + item) * n;
-  dacc2 acc[NS];
-#pragma unroll
-  for (int i = 0; i < NS; ++i) acc[i] = dacc2_zero();
-  dacc nacc = dacc_zero();
-  for (long long e = (long long)blk * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
-    dfc vv[NS];
-#pragma unroll
-    for (int i = 0; i < NS; ++i) vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
-    const dfc xe = half ? dfc_ld(xv + e) : vv[NS - 1];
-    const float2 wah = make_float2(xe.re.hi, -xe.re.hi), wal = make_float2(xe.re.lo, -xe.re.lo);
-    const float2 wbh = make_float2(xe.im.hi, xe.im.hi), wbl = make_float2(xe.im.lo, xe.im.lo);
-#pragma unroll
-    for (int i = 0; i < NS; ++i) dacc2_cfma(acc[i], dfc2_of(vv[i]), wah, wal, wbh, wbl);
-    if (half) {
-      dacc_fma(nacc, xe.re, xe.re);
-      dacc_fma(nacc, xe.im, xe.im);
-    }
-  }
   dfc vals[NO];
+  if (half) {
+    // first projection of w: FP32 products of the high parts, FP32 sums over the thread's ~10
+    // elements, df64 from the block sums on
+    const float2* wv = (const float2*)(w + (long long)item * n);   // (re.hi, im.hi) of each value
+    float2 af[NS];
 #pragma unroll
-  for (int i = 0; i < NS; ++i) vals[i] = dacc2_val(acc[i]);
-  vals[NS] = {dacc_val(nacc), df_zero()};
+    for (int i = 0; i < NS; ++i) af[i] = make_float2(0.f, 0.f);
+    float nf = 0.f;
+    for (long long e = (long long)blk * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+      const float2 x = __ldg(wv + 2 * e);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        const float2 v = __ldg((const float2*)(V + ((long long)i * items + item) * n + e));
+        af[i].x = fmaf(v.x, x.x, fmaf(v.y, x.y, af[i].x));    // conj(v) * x
+        af[i].y = fmaf(v.x, x.y, fmaf(-v.y, x.x, af[i].y));
+      }
+      nf = fmaf(x.x, x.x, fmaf(x.y, x.y, nf));
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) vals[i] = {df_from_f(af[i].x), df_from_f(af[i].y)};
+    vals[NS] = {df_from_f(nf), df_zero()};
+  } else {
+    // second projection of u_j (and ||u_j||^2): compensated Dot2 sums of the df64 values
+    dacc2 acc[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) acc[i] = dacc2_zero();
+    for (long long e = (long long)blk * KB + threadIdx.x; e < n; e += (long long)nblk * KB) {
+      dfc vv[NS];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) vv[i] = dfc_ld(V + ((long long)i * items + item) * n + e);
+      const dfc xe = vv[NS - 1];
+      const float2 wah = make_float2(xe.re.hi, -xe.re.hi), wal = make_float2(xe.re.lo, -xe.re.lo);
+      const float2 wbh = make_float2(xe.im.hi, xe.im.hi), wbl = make_float2(xe.im.lo, xe.im.lo);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) dacc2_cfma(acc[i], dfc2_of(vv[i]), wah, wal, wbh, wbl);
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) vals[i] = dacc2_val(acc[i]);
+    vals[NS] = dfc_zero();
+  }
   block_store_df<NO>(vals, part, item, 2 * nblk);
   if (!cnt || !last_block(cnt, item, 2 * nblk)) return;
   __shared__ double2 sd[2 * NO];
@@ -404,7 +428,10 @@ __global__ void __launch_bounds__(KB, 2) k_mdot2_df(long long n, int items, cons
   hj.y *= isig;
   double r2 = B[NS].x - (hj.x * hj.x + hj.y * hj.y);
   for (int i = 0; i < j; ++i) r2 -= B[i].x * B[i].x + B[i].y * B[i].y;
-  const double rho = r2 > 0.0 ? sqrt(r2) : 0.0;
+  // r2 carries the first projection's FP32 rounding (about 1e-7 of ||w||^2): below 1e-12 ||w||^2 it
+  // says nothing, and any positive scale serves (sigma of the next step measures the true norm)
+  const double r2min = 1e-12 * B[NS].x;
+  const double rho = sqrt(r2 > r2min ? r2 : r2min);
   const double2 cu = make_double2(hj.x * isig, hj.y * isig);
   float4* cf = coef + (long long)item * KDS;
   double2* od = outd + (long long)item * KDS;
