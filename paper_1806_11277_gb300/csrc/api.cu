@@ -1340,7 +1340,8 @@ ehs_status ehs_create(const ehs_problem* prob, const ehs_opts* opts, void* strea
       c->yq = dalloc<float4>(c, (size_t)items * 12);
       c->npq = dalloc<float2>(c, (size_t)items * c->nblk);
       c->invq = dalloc<float2>(c, items);
-      c->hhost = dalloc<double2>(c, (size_t)items * 24);            // >= KDS per item
+      static_assert(KDS <= 24, "hhost and hstep hold 24 double2 per item");
+      c->hhost = dalloc<double2>(c, (size_t)items * 24);            // h1, h2 or the delayed-CGS2 coefficients
       c->kcnt = dalloc<int>(c, (size_t)items * 3);
     }
     CK(cudaMallocHost((void**)&c->hpin, 64 * sizeof(double) + items * sizeof(double)));
