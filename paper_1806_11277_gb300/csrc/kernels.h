@@ -214,7 +214,7 @@ void launch_xupdate(long long n, int items, int m, const CZ* Z, const double2* y
                     const int* kused, double2* x, cudaStream_t s);
 
 // ---- FP64-class (double-float) Krylov, operator and coarsest ----------------
-// complex df64 = float4 {re.hi, re.lo, im.hi, im.lo}; real df64 = float2 {hi, lo}
+// complex df64 = float4 {re.hi, im.hi, re.lo, im.lo} (dfc_st); real df64 = float2 {hi, lo}
 // With cnt (device counters [items], zero, reset by the kernels), the last block of each item
 // also reduces the partials: dots into out (df64) and outd (double copy for the host), the norm
 // into nrm (double) and inv (df64 1/norm) -- the results of launch_reduce_parts_df /
