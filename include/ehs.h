@@ -132,13 +132,16 @@ typedef struct {
                             instead of graph-replayed per-colour launches; same results.  0 (the
                             default): per-colour launches */
   int ortho;             /* Arnoldi orthogonalisation of the double-float solve (prec = EHS_C64; the
-                            FP64 form always uses CGS2).  0: CGS2, three passes over the basis per
-                            step (first projection, second projection with the norm, update).
-                            1 (the default): delayed CGS2, two passes per step: the second projection of a
-                            direction is formed together with the first projection of the next
-                            one (the preconditioner is applied to the once-orthogonalised
-                            direction, which flexible GMRES allows); the same basis and
-                            Hessenberg matrix in exact arithmetic */
+                            FP64 form always uses CGS2).  0: CGS2, three passes over the basis
+                            per step (first projection, second projection with the norm,
+                            update), compensated double-float sums throughout.  1 (the default):
+                            delayed CGS2, two passes per step: the second projection of a
+                            direction (compensated double-float sums) is formed together with
+                            the first projection of the next one (FP32 products: the next
+                            step's second projection removes their rounding, and the Hessenberg
+                            matrix records what was subtracted); the preconditioner is applied
+                            to the once-orthogonalised direction, which flexible GMRES allows.
+                            The same basis and Hessenberg matrix as CGS2 in exact arithmetic */
 } ehs_opts;
 
 typedef struct {
