@@ -433,7 +433,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_iter * args.ref_iters * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "media": len(SIGMAS)},
+        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "media": len(SIGMAS),
+                   "arithmetic": ("the oracle: FP64 throughout (scipy.sparse complex128 cycle and coarsest "
+                                  "local solves, FGMRES(10) with CGS2)")},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores_used(_CPU_METER),
                          "threads_available": cpu_threads(), "kind": "oracle",
                          "sample": (f"{args.ref_iters} oracle FGMRES iterations per step on one medium "
