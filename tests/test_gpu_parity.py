@@ -287,6 +287,33 @@ def test_fgmres_multi_rhs_3d(ortho):
         assert _err(ug, xo) <= 1e-5, (it, _err(ug, xo))
 
 
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_fgmres_zero_rhs_item(ortho):
+    """A zero right-hand side in a batch (the degenerate case of the solve): that item takes
+    no iteration and returns u = 0 with relative residual 0 (the convention for q = 0), while
+    the other item of the batch is solved as the oracle solves it alone."""
+    ehs = _ehs()
+    meds = _media_2d(64, 2)
+    q = np.stack([synth.point_rhs(m.shape, m.sources)[0] for m in meds])
+    q[0] = 0
+    S = ehs.solver_for(meds, levels=3, prec=ehs.EHS_C64, ortho=ortho)
+    qd = torch.from_numpy(q).cuda()
+    ud = torch.ones_like(qd)                      # the solve starts from zero whatever u holds
+    info = S.fgmres_solve(qd, ud)
+    u = ud.cpu().numpy()
+    S.close()
+    assert info[0]["iters"] == 0 and info[0]["converged"] and info[0]["relres"] == 0.0
+    assert not np.any(u[0])
+    med = meds[1]
+    K = _oracle_parts(med)
+    H = mg.Hierarchy(_oracle_parts(med, 0.2), med.shape, 3)
+    qo = op.slots_to_dofs(q[1], med.shape)
+    xo, io = krylov.fgmres(lambda v: K @ v, H.cycle, qo, m=10)
+    ug = op.slots_to_dofs(u[1], med.shape)
+    assert info[1]["converged"] and abs(info[1]["iters"] - io["iters"]) <= 1, (info[1], io["iters"])
+    assert _err(ug, xo) <= 1e-5
+
+
 def test_adjoint_solve():
     ehs = _ehs()
     med = _media_2d(32, 1)[0]
