@@ -1,7 +1,9 @@
 // FP64-class (double-float) kernels of the outer FGMRES solve, its operator
 // K (unshifted, Sec. 3 eq. elasticHelmReformulatedSystem), the true residual,
 // and the coarsest-level solve.  Same algorithms as k_krylov.cu / k_fine.cu /
-// k_dense.cu, carried out in df64 (see df64.cuh) on the FP32 pipe.
+// k_dense.cu, carried out in df64 (see df64.cuh) on the FP32 pipe; the Arnoldi
+// step is CGS2 (k_mdot_df, k_mupdate_df, k_update_scale_cast_df) or delayed
+// CGS2 (k_mdot2_df, k_dupdate_df).
 //
 // Layouts: Krylov basis V and solution x as complex df64 (float4 per value),
 // preconditioned directions Z as complex64 (the multigrid cycle's output
